@@ -1,0 +1,106 @@
+"""Seeded synthetic inputs shaped like the paper's merge workloads.
+
+This module only draws numbers: it holds none of the merge's arithmetic, and
+both the CUDA library's tests and the CPU oracle's tests take their inputs from
+it.  Every generator uses numpy's PCG64 with an explicit seed.
+
+The paper measures on RAND100K, SIFT, GIST, NYTimes and other sets (Sec. 5,
+Table "Overview of Datasets"); none of them is available here, so these
+generators copy only their shapes, dimensionality, value ranges and metric:
+
+* ``gaussian_mixture``: RAND-style clustered float vectors (means U[-lo, hi],
+  unit-variance noise), optionally L2-normalised for the cosine workloads.
+* ``sift_like``: non-negative integers 0..255 stored as float32, drawn around
+  256 sparse-ish centres (each centre coordinate is 0 with p=0.4, else
+  Gamma(2, 20)).  Each centre spreads its points in its own random 16-d
+  subspace (about 8 per coordinate), so the local intrinsic dimension is near
+  the 16.3 the paper lists for SIFT; values are rounded and clipped.
+* ``gist_like``: non-negative correlated vectors |M u| with M a random
+  d x d matrix (entries N(0, 1/d)) and u a 64-d latent padded with small noise.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def gaussian_mixture(n: int, d: int, n_comp: int = 16, seed: int = 0, normalize: bool = False,
+                     mean_range: float = 10.0, chunk: int = 1 << 18) -> np.ndarray:
+    rng = _rng(seed)
+    means = rng.uniform(-mean_range, mean_range, size=(n_comp, d))
+    comp = rng.integers(0, n_comp, size=n)
+    X = np.empty((n, d), np.float32)
+    for b in range(0, n, chunk):
+        e = min(n, b + chunk)
+        blk = means[comp[b:e]] + rng.standard_normal((e - b, d))
+        if normalize:
+            blk /= np.linalg.norm(blk, axis=1, keepdims=True)
+        X[b:e] = blk
+    return X
+
+
+def sift_like(n: int, d: int = 128, n_centres: int = 256, seed: int = 0, rank: int = 16,
+              spread: float = 8.0, chunk: int = 1 << 16) -> np.ndarray:
+    rng = _rng(seed)
+    zero = rng.random((n_centres, d)) < 0.4
+    centres = np.where(zero, 0.0, rng.gamma(2.0, 20.0, size=(n_centres, d)))
+    basis = rng.normal(0.0, spread / np.sqrt(rank), size=(n_centres, d, rank))
+    which = rng.integers(0, n_centres, size=n)
+    X = np.empty((n, d), np.float32)
+    for b in range(0, n, chunk):
+        e = min(n, b + chunk)
+        z = rng.standard_normal((e - b, rank))
+        blk = centres[which[b:e]] + np.einsum("ndr,nr->nd", basis[which[b:e]], z)
+        X[b:e] = np.clip(np.rint(blk), 0, 255)
+    return X
+
+
+def gist_like(n: int, d: int = 960, latent: int = 64, seed: int = 0,
+              chunk: int = 1 << 16) -> np.ndarray:
+    rng = _rng(seed)
+    M = rng.normal(0.0, 1.0 / np.sqrt(d), size=(d, d)).astype(np.float32)
+    X = np.empty((n, d), np.float32)
+    for b in range(0, n, chunk):
+        e = min(n, b + chunk)
+        u = np.empty((e - b, d), np.float32)
+        u[:, :latent] = rng.standard_normal((e - b, latent))
+        u[:, latent:] = 0.1 * rng.standard_normal((e - b, d - latent))
+        X[b:e] = np.abs(u @ M.T)
+    return X
+
+
+def sample_nodes(n: int, count: int, seed: int = 0) -> np.ndarray:
+    """Sorted distinct node ids for sampled recall checks."""
+    rng = _rng(seed)
+    count = min(count, n)
+    return np.sort(rng.choice(n, size=count, replace=False))
+
+
+# The five workloads (sizes, metric, k, rounds).  Data seed = 1000 + index.
+WORKLOADS = {
+    "smerge_gmm_10k_d32_k10": dict(kind="symmetric", gen="gaussian_mixture", n=10_000, d=32,
+                                   k=10, metric="l2", rounds=8, sample_rate=0.5, seed=1001,
+                                   gen_args=dict(n_comp=16)),
+    "smerge_sift_1m_d128_k20": dict(kind="symmetric", gen="sift_like", n=1_000_000, d=128, k=20,
+                                    metric="l2", rounds=10, sample_rate=0.5, seed=1002,
+                                    gen_args={}),
+    "jmerge_gmm_2m_d96_k16_cos": dict(kind="joint", gen="gaussian_mixture", n=2_000_000, d=96,
+                                      k=16, metric="cos", rounds=10, sample_rate=0.5, seed=1003,
+                                      gen_args=dict(n_comp=16, normalize=True)),
+    "serve_sift_2m_d128_k16": dict(kind="serve", gen="sift_like", n=2_000_000, d=128, k=16,
+                                   metric="l2", rounds=10, sample_rate=0.5, seed=1004,
+                                   gen_args={}),
+    "smerge_gist_1m_d960_k20": dict(kind="symmetric", gen="gist_like", n=1_000_000, d=960,
+                                    k=20, metric="l1", rounds=10, sample_rate=0.5, seed=1005,
+                                    gen_args={}),
+}
+
+
+def generate(name: str, n: int | None = None) -> np.ndarray:
+    w = WORKLOADS[name]
+    gen = {"gaussian_mixture": gaussian_mixture, "sift_like": sift_like,
+           "gist_like": gist_like}[w["gen"]]
+    return gen(n if n is not None else w["n"], w["d"], seed=w["seed"], **w["gen_args"])
