@@ -1,0 +1,174 @@
+/*
+ * knnm.h -- C ABI of the GB300 k-NN graph merge library (libknnm.so).
+ *
+ * The library merges approximate k-NN graphs as in Zhao, Wang, Lin and Ngo,
+ * "On the Merge of k-NN Graph":
+ *   - knnm_merge_symmetric: Symmetric Merge (S-Merge, Alg. 1, Sec. 3.1): two
+ *     graphs G1 on S1 and G2 on S2 become one graph on S1 u S2.
+ *   - knnm_merge_joint: Joint Merge (J-Merge, Alg. 2, Sec. 3.2): a graph G1 on
+ *     S1 is expanded with a raw set S2.
+ *   - knnm_build: J-Merge with an empty existing graph, i.e. NN-Descent, used
+ *     to make input graphs.
+ * plus one entry point per step of a merge round (knnm_step_*) so that each
+ * step can be checked on its own.
+ *
+ * Conventions shared by every call
+ *   - Return value: KNNM_OK (0) or a negative KNNM_ERR_* code.  No C++
+ *     exception crosses the ABI.  The message of the last failure of a context
+ *     is returned by knnm_last_error().
+ *   - Vectors are row-major float32 [n][d].  Graph ids are int32 [n][k]; input
+ *     graphs hold ids local to their own set (0..n_set-1), outputs hold global
+ *     ids with S1 rows first, then S2 rows.
+ *   - Output lists are sorted by (distance, id) ascending, ids unique, no self.
+ *     Distances are the library's canonical FP32 distances: one accumulator,
+ *     dimensions in index order, fused multiply-add per term.  KNNM_L2 is the
+ *     squared Euclidean distance (same ranking as l2), KNNM_IP is 0 - a.b,
+ *     KNNM_COS is 1 - a.b/(|a||b|) (1 when a norm is zero), KNNM_L1 is the sum of
+ *     |a_t - b_t| in index order.  Inputs must be finite.
+ *   - knnm_merge_* and knnm_build accept host or device pointers for every
+ *     array argument (the library asks the CUDA runtime which one each is).
+ *     Host inputs are copied to the device and host outputs copied back inside
+ *     the call.  The step entry points take device pointers only.
+ *   - The caller owns every array it passes.  The library owns only its
+ *     scratch, which the context keeps and reuses between calls.
+ *   - Every call runs on the context's stream and has finished when it
+ *     returns.  Calls on one context must not overlap.
+ */
+#ifndef KNNM_H
+#define KNNM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  KNNM_OK = 0,
+  KNNM_ERR_INVALID = -1,   /* bad argument or malformed input graph */
+  KNNM_ERR_NOMEM = -2,     /* device or host allocation failed */
+  KNNM_ERR_CUDA = -3,      /* a CUDA runtime call failed */
+  KNNM_ERR_TIMEOUT = -4,   /* a bounded device or host wait ran out */
+  KNNM_ERR_NOT_READY = -5, /* serving: the request has not completed yet */
+  KNNM_ERR_DEVICE = -6     /* a kernel reported an internal error */
+};
+
+typedef enum { KNNM_L2 = 0, KNNM_IP = 1, KNNM_COS = 2, KNNM_L1 = 3 } knnm_metric;
+
+/* KNNM_FP32: every distance is the canonical FP32 distance, one thread per pair
+ * on the CUDA cores.  KNNM_BF16_RERANK: distances are first estimated from
+ * BF16 copies of the vectors on the tensor cores (FP32 accumulation); a pair is
+ * re-computed canonically in FP32 whenever a proven error bound cannot rule it
+ * out, so the merged graph is identical to the KNNM_FP32 one.  L1 has no
+ * tensor-core form and always runs as KNNM_FP32. */
+typedef enum { KNNM_FP32 = 0, KNNM_BF16_RERANK = 1 } knnm_precision;
+
+typedef struct {
+  int k;             /* list length K, 1..32 (Alg. 1 Data line: k-NN graphs) */
+  int metric;        /* knnm_metric */
+  int precision;     /* knnm_precision */
+  int max_iters;     /* cap on local-join rounds, 1..KNNM_MAX_ROUNDS */
+  float sample_rate; /* rho: each round samples s = max(1, floor(rho*K)) new entries */
+  float keep_ratio;  /* r of Sec. 5.2.1: K_keep = floor(r*K) entries survive Divide */
+  float delta;       /* stop once a round changes <= delta*N*K list entries */
+  uint64_t seed;     /* seed of every random draw (init and sampling) */
+} knnm_params;
+
+#define KNNM_MAX_ROUNDS 64
+
+typedef struct {
+  int rounds;                             /* rounds run */
+  int64_t updates[KNNM_MAX_ROUNDS];       /* c_t: entries new to the lists after round t */
+  int64_t dist_evals[KNNM_MAX_ROUNDS];    /* pairs compared in round t (scanning rate C) */
+  int64_t proposals[KNNM_MAX_ROUNDS];     /* edges offered to UpdateNN after the k-th filter */
+  int64_t reranked[KNNM_MAX_ROUNDS];      /* BF16 path: pairs re-computed in FP32 */
+  float ms_init, ms_rounds, ms_final;     /* device time of init, all rounds, final merge */
+  float ms_total;                         /* wall time of the call */
+} knnm_stats;
+
+typedef struct knnm_ctx knnm_ctx;
+
+/* Creates a context bound to CUDA device `device` and stream `cuda_stream`
+ * (a cudaStream_t; NULL means the legacy default stream). */
+int knnm_create(knnm_ctx** out, int device, void* cuda_stream);
+/* Frees the context and its scratch. */
+int knnm_destroy(knnm_ctx* ctx);
+/* Rebinds the context to another stream of the same device. */
+int knnm_set_stream(knnm_ctx* ctx, void* cuda_stream);
+/* Message of the context's last failure ("" if none).  Owned by the context. */
+const char* knnm_last_error(const knnm_ctx* ctx);
+/* Static name of an error code. */
+const char* knnm_strerror(int code);
+/* Fills `p` with the defaults: K=20, L2, FP32, 10 rounds, rho=0.5, r=0.5,
+ * delta=0.001, seed=0. */
+void knnm_default_params(knnm_params* p);
+
+/* S-Merge (Alg. 1).  S1 [n1][d], G1 [n1][K] (ids in 0..n1-1), S2 [n2][d],
+ * G2 [n2][K] (ids in 0..n2-1).  out_ids/out_dists [n1+n2][K].  Each input row
+ * must hold K distinct ids other than its own; n1, n2 >= K+1 and
+ * >= K - floor(r*K).  `stats` may be NULL.  Malformed graphs give
+ * KNNM_ERR_INVALID. */
+int knnm_merge_symmetric(knnm_ctx* ctx, const float* S1, int64_t n1, const int32_t* G1,
+                         const float* S2, int64_t n2, const int32_t* G2, int d,
+                         const knnm_params* params, int32_t* out_ids, float* out_dists,
+                         knnm_stats* stats);
+
+/* J-Merge (Alg. 2).  S1 [n1][d] with graph G1 [n1][K]; raw rows S_new [n2][d].
+ * Output rows: S1 first, then S_new.  n1 >= K+1 (or n1 == 0, which is
+ * knnm_build), n1+n2 >= K+1, n2 >= K - floor(r*K) when n1 > 0. */
+int knnm_merge_joint(knnm_ctx* ctx, const float* S1, int64_t n1, const int32_t* G1,
+                     const float* S_new, int64_t n2, int d, const knnm_params* params,
+                     int32_t* out_ids, float* out_dists, knnm_stats* stats);
+
+/* NN-Descent build of S [n][d] (J-Merge with an empty graph); n >= K+1. */
+int knnm_build(knnm_ctx* ctx, const float* S, int64_t n, int d, const knnm_params* params,
+               int32_t* out_ids, float* out_dists, knnm_stats* stats);
+
+/* ---------------------------------------------------------------------------
+ * Round steps.  Device pointers only.  Working state of a merge of N rows is
+ *   ids int32 [N][K], dists float [N][K], flags uint8 [N][K] (1 = new),
+ *   rear_ids int32 [N][Kr], rear_dists float [N][Kr] (id -1 where a row has none)
+ * with each list sorted by (distance, id).  Vectors are passed as X1 [nx1][d]
+ * holding rows 0..nx1-1 and X2 holding rows nx1..N-1 (X2 may be NULL when
+ * nx1 == N).  `set_split` is n1: rows below it are S1, the rest S2.
+ * `mode` 0 = S-Merge, 1 = J-Merge (and build with set_split = 0).
+ * ------------------------------------------------------------------------- */
+
+/* Divide / Append (Alg. 1) and Initialize (Alg. 2).  G1 rows cover
+ * 0..set_split-1; G2 rows cover set_split..N-1 in S-Merge and must be NULL in
+ * J-Merge.  K_keep = floor(keep_ratio*K) (K when set_split == 0 in J-Merge);
+ * Kr = K - K_keep. */
+int knnm_step_init(knnm_ctx* ctx, int mode, const float* X1, int64_t nx1, const float* X2,
+                   int64_t N, int64_t set_split, int d, const int32_t* G1, const int32_t* G2,
+                   const knnm_params* params, int32_t* ids, float* dists, uint8_t* flags,
+                   int32_t* rear_ids, float* rear_dists);
+
+/* Reverse(G) and the sampled candidate sets of round t: flips the flags of the
+ * sampled forward-new entries to old and writes new_ids [N][cap_new],
+ * new_cnt [N], old_ids [N][cap_old], old_cnt [N] with cap_new >= 2s and
+ * cap_old >= K+s, s = max(1, floor(sample_rate*K)). */
+int knnm_step_sample(knnm_ctx* ctx, int64_t N, int K, const int32_t* ids, const float* dists,
+                     uint8_t* flags, uint64_t seed, int t, int s, int cap_new, int cap_old,
+                     int32_t* new_ids, int32_t* new_cnt, int32_t* old_ids, int32_t* old_cnt);
+
+/* Local join and UpdateNN of one round (Alg. 1 / Alg. 2 inner loops) on the
+ * given candidate sets: updates ids/dists/flags in place, writes c_t to
+ * *updates and the pair count to *dist_evals.  Counts must not exceed
+ * cap_new/cap_old and cap_new + cap_old <= 96. */
+int knnm_step_join(knnm_ctx* ctx, int mode, const float* X1, int64_t nx1, const float* X2,
+                   int64_t N, int64_t set_split, int d, const knnm_params* params, int32_t* ids,
+                   float* dists, uint8_t* flags, int cap_new, int cap_old, const int32_t* new_ids,
+                   const int32_t* new_cnt, const int32_t* old_ids, const int32_t* old_cnt,
+                   int64_t* updates, int64_t* dist_evals);
+
+/* Merge and Sort (Alg. 1 last step): first K distinct ids of each working list
+ * merged with its rear list. */
+int knnm_step_final(knnm_ctx* ctx, int64_t N, int K, const int32_t* ids, const float* dists,
+                    int Kr, const int32_t* rear_ids, const float* rear_dists, int32_t* out_ids,
+                    float* out_dists);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KNNM_H */

@@ -1,0 +1,779 @@
+// knnm_api.cu -- the C ABI of libknnm.so (include/knnm.h): argument checks,
+// scratch management, host/device pointer handling and the round loop that
+// drives the kernels of S-Merge (Alg. 1), J-Merge (Alg. 2) and the build.
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/knnm.h"
+#include "knnm_internal.cuh"
+
+using namespace knnm;
+
+struct knnm_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  DevCounters* host_ctr = nullptr;  // pinned
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  char err[512] = {0};
+};
+
+namespace {
+
+int fail(knnm_ctx* c, int code, const char* fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+#define KNNM_CUDA(call)                                                                  \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(ctx, KNNM_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));   \
+  } while (0)
+
+// Bump allocator over the context's arena; sizes are rounded to 256 bytes.
+struct Carver {
+  size_t off = 0;
+  char* base = nullptr;
+  template <typename T>
+  T* take(size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~(size_t)255;
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += bytes;
+    return p;
+  }
+};
+
+int ensure_arena(knnm_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->arena_bytes) return KNNM_OK;
+  if (ctx->arena) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->arena);
+    ctx->arena = nullptr;
+    ctx->arena_bytes = 0;
+  }
+  size_t want = bytes + (bytes >> 4);
+  cudaError_t e = cudaMalloc(&ctx->arena, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->arena = nullptr;
+    return fail(ctx, KNNM_ERR_NOMEM, "cannot allocate %zu bytes of device scratch: %s", want,
+                cudaGetErrorString(e));
+  }
+  ctx->arena_bytes = want;
+  return KNNM_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+struct Derived {
+  int K, K_keep, Kr, s, cap_new, cap_old;
+};
+
+int derive(knnm_ctx* ctx, const knnm_params* p, int mode, int64_t n1, Derived* out) {
+  if (!p) return fail(ctx, KNNM_ERR_INVALID, "params is NULL");
+  if (p->k < 1 || p->k > 32) return fail(ctx, KNNM_ERR_INVALID, "k=%d outside 1..32", p->k);
+  if (p->metric < 0 || p->metric > 3) return fail(ctx, KNNM_ERR_INVALID, "bad metric %d", p->metric);
+  if (p->precision < 0 || p->precision > 1)
+    return fail(ctx, KNNM_ERR_INVALID, "bad precision %d", p->precision);
+  if (p->max_iters < 0 || p->max_iters > KNNM_MAX_ROUNDS)
+    return fail(ctx, KNNM_ERR_INVALID, "max_iters=%d outside 0..%d", p->max_iters, KNNM_MAX_ROUNDS);
+  if (!(p->sample_rate > 0.f) || !(p->keep_ratio >= 0.f) || !(p->keep_ratio <= 1.f) ||
+      !(p->delta >= 0.f))
+    return fail(ctx, KNNM_ERR_INVALID, "sample_rate, keep_ratio or delta out of range");
+  Derived d;
+  d.K = p->k;
+  d.K_keep = (int)((double)p->keep_ratio * (double)d.K);
+  if (mode == JOINT && n1 == 0) d.K_keep = d.K;
+  d.Kr = d.K - d.K_keep;
+  double sd = (double)p->sample_rate * (double)d.K;
+  d.s = sd >= (double)d.K ? d.K : (int)sd;
+  if (d.s < 1) d.s = 1;
+  d.cap_new = 2 * d.s;
+  d.cap_old = d.K + d.s;
+  *out = d;
+  return KNNM_OK;
+}
+
+// Copies a host array to freshly carved device scratch when needed.
+struct Staged {
+  const void* dev = nullptr;
+  bool copied = false;
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// The merge driver shared by the three whole-merge entry points.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct MergeIn {
+  int mode;
+  const float* S1;
+  int64_t n1;  // rows of S1 (= set split)
+  const int32_t* G1;
+  const float* S2;
+  int64_t n2;
+  const int32_t* G2;
+  int d;
+};
+
+int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32_t* out_ids,
+              float* out_dists, knnm_stats* stats) {
+  auto t_wall0 = std::chrono::steady_clock::now();
+  if (!ctx) return KNNM_ERR_INVALID;
+  ctx->err[0] = 0;
+  Derived D;
+  int rc = derive(ctx, params, in.mode, in.n1, &D);
+  if (rc) return rc;
+  const int64_t N = in.n1 + in.n2;
+  const int d = in.d;
+  const int K = D.K;
+  if (d < 1) return fail(ctx, KNNM_ERR_INVALID, "d=%d", d);
+  if (in.n1 < 0 || in.n2 < 0 || N > 0x7FFFFFFFLL)
+    return fail(ctx, KNNM_ERR_INVALID, "row counts out of range");
+  if (!out_ids || !out_dists) return fail(ctx, KNNM_ERR_INVALID, "output arrays are NULL");
+  if (in.mode == SYMMETRIC) {
+    if (in.n1 < K + 1 || in.n2 < K + 1)
+      return fail(ctx, KNNM_ERR_INVALID, "S-Merge needs n1, n2 >= k+1 (n1=%lld n2=%lld k=%d)",
+                  (long long)in.n1, (long long)in.n2, K);
+    if (in.n1 < D.Kr || in.n2 < D.Kr)
+      return fail(ctx, KNNM_ERR_INVALID, "each set needs at least k - floor(r*k) = %d rows", D.Kr);
+    if (!in.S1 || !in.S2 || !in.G1 || !in.G2)
+      return fail(ctx, KNNM_ERR_INVALID, "NULL input array");
+  } else {
+    if (N < K + 1) return fail(ctx, KNNM_ERR_INVALID, "n1+n2 must be >= k+1");
+    if (in.n1 > 0 && (in.n1 < K + 1 || in.n2 < D.Kr || !in.G1 || !in.S1))
+      return fail(ctx, KNNM_ERR_INVALID,
+                  "J-Merge needs n1 >= k+1, n2 >= k - floor(r*k) and G1 when n1 > 0");
+    if (in.n2 > 0 && !in.S2) return fail(ctx, KNNM_ERR_INVALID, "S_new is NULL");
+  }
+  const int precision = (params->precision == KNNM_BF16_RERANK && params->metric != KNNM_L1)
+                            ? KNNM_BF16_RERANK
+                            : KNNM_FP32;
+  if (precision == KNNM_BF16_RERANK && d % 8 != 0)
+    return fail(ctx, KNNM_ERR_INVALID, "the BF16 path needs d %% 8 == 0 (d=%d)", d);
+
+  cudaStream_t st = ctx->stream;
+  KNNM_CUDA(cudaSetDevice(ctx->device));
+
+  // Where does each array live?
+  const bool s1_dev = in.n1 == 0 || is_device_ptr(in.S1);
+  const bool s2_dev = in.n2 == 0 || is_device_ptr(in.S2);
+  const bool g1_dev = !in.G1 || is_device_ptr(in.G1);
+  const bool g2_dev = !in.G2 || is_device_ptr(in.G2);
+  const bool oi_dev = is_device_ptr(out_ids);
+  const bool od_dev = is_device_ptr(out_dists);
+
+  JoinPlan plan;
+  {
+    cudaError_t e = plan_join(precision, params->metric, D.cap_new, D.cap_old, d, &plan);
+    if (e != cudaSuccess)
+      return fail(ctx, KNNM_ERR_INVALID, "no join configuration for k=%d, s=%d, d=%d: %s", K,
+                  D.s, d, cudaGetErrorString(e));
+  }
+  const uint64_t per_node = 384;
+  uint64_t region_cap = ((uint64_t)N * per_node + plan.grid - 1) / plan.grid;
+  if (region_cap < 1024) region_cap = 1024;
+
+  // Carve the scratch (two passes: size, then pointers).
+  struct Ptrs {
+    float* X;
+    int32_t *G1, *G2, *oi;
+    float* od;
+    uint64_t *keys, *prev, *rear, *rev_new, *rev_old, *prop_key;
+    uint8_t* flags;
+    int32_t *new_ids, *new_cnt, *old_ids, *old_cnt, *prop_tgt;
+    float* norms;
+    __nv_bfloat16* Xb;
+    float4* aux;
+    unsigned long long* region_cnt;
+    DevCounters* ctr;
+  } P;
+  auto carve = [&](Carver& c) {
+    P.X = (!s1_dev || !s2_dev) ? c.take<float>((size_t)N * d) : nullptr;
+    P.G1 = (in.G1 && !g1_dev) ? c.take<int32_t>((size_t)in.n1 * K) : nullptr;
+    P.G2 = (in.G2 && !g2_dev) ? c.take<int32_t>((size_t)in.n2 * K) : nullptr;
+    P.oi = !oi_dev ? c.take<int32_t>((size_t)N * K) : nullptr;
+    P.od = !od_dev ? c.take<float>((size_t)N * K) : nullptr;
+    P.keys = c.take<uint64_t>((size_t)N * K);
+    P.prev = c.take<uint64_t>((size_t)N * K);
+    P.rear = c.take<uint64_t>((size_t)N * (D.Kr > 0 ? D.Kr : 1));
+    P.rev_new = c.take<uint64_t>((size_t)N * D.s);
+    P.rev_old = c.take<uint64_t>((size_t)N * D.s);
+    P.flags = c.take<uint8_t>((size_t)N * K);
+    P.new_ids = c.take<int32_t>((size_t)N * D.cap_new);
+    P.new_cnt = c.take<int32_t>((size_t)N);
+    P.old_ids = c.take<int32_t>((size_t)N * D.cap_old);
+    P.old_cnt = c.take<int32_t>((size_t)N);
+    P.norms = params->metric == KNNM_COS ? c.take<float>((size_t)N) : nullptr;
+    P.Xb = precision == KNNM_BF16_RERANK ? c.take<__nv_bfloat16>((size_t)N * d) : nullptr;
+    P.aux = precision == KNNM_BF16_RERANK ? c.take<float4>((size_t)N) : nullptr;
+    P.prop_tgt = c.take<int32_t>(region_cap * plan.grid);
+    P.prop_key = c.take<uint64_t>(region_cap * plan.grid);
+    P.region_cnt = c.take<unsigned long long>((size_t)plan.grid);
+    P.ctr = c.take<DevCounters>(1);
+  };
+  Carver sizer;
+  carve(sizer);
+  rc = ensure_arena(ctx, sizer.off);
+  if (rc) return rc;
+  Carver real;
+  real.base = (char*)ctx->arena;
+  carve(real);
+
+  // Stage host inputs.
+  const float* X1 = in.S1;
+  const float* X2 = in.S2;
+  int64_t nx1 = in.n1;
+  if (P.X) {
+    if (in.n1 > 0)
+      KNNM_CUDA(cudaMemcpyAsync(P.X, in.S1, (size_t)in.n1 * d * 4,
+                                s1_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    if (in.n2 > 0)
+      KNNM_CUDA(cudaMemcpyAsync(P.X + (size_t)in.n1 * d, in.S2, (size_t)in.n2 * d * 4,
+                                s2_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    X1 = P.X;
+    X2 = P.X + (size_t)in.n1 * d;
+    nx1 = N;
+  }
+  if (in.n1 == 0) {  // build: every row lives in S_new
+    X1 = X2;
+    nx1 = N;
+  }
+  const int32_t* G1 = in.G1;
+  const int32_t* G2 = in.G2;
+  if (P.G1) {
+    KNNM_CUDA(cudaMemcpyAsync(P.G1, in.G1, (size_t)in.n1 * K * 4, cudaMemcpyHostToDevice, st));
+    G1 = P.G1;
+  }
+  if (P.G2) {
+    KNNM_CUDA(cudaMemcpyAsync(P.G2, in.G2, (size_t)in.n2 * K * 4, cudaMemcpyHostToDevice, st));
+    G2 = P.G2;
+  }
+  Rows rows{X1, X2 ? X2 : X1, nx1, d};
+  const bool use_bulk =
+      d % 4 == 0 && aligned16(rows.X1) && aligned16(rows.X2) && (nx1 == N || aligned16(rows.X2));
+
+  KNNM_CUDA(cudaEventRecord(ctx->ev[0], st));
+  KNNM_CUDA(cudaMemsetAsync(P.ctr, 0, sizeof(DevCounters), st));
+  KNNM_CUDA(cudaMemsetAsync(&P.ctr->err_row, 0xFF, 8, st));
+  if (P.norms) KNNM_CUDA(launch_norms(rows, N, P.norms, st));
+  if (P.Xb) KNNM_CUDA(launch_bf16_prep(rows, N, P.Xb, P.aux, st));
+
+  InitArgs ia;
+  ia.mode = in.mode;
+  ia.rows = rows;
+  ia.N = N;
+  ia.n1 = in.n1;
+  ia.G1 = G1;
+  ia.G2 = G2;
+  ia.K = K;
+  ia.K_keep = D.K_keep;
+  ia.metric = params->metric;
+  ia.seed = params->seed;
+  ia.norms = P.norms;
+  ia.keys = P.keys;
+  ia.flags = P.flags;
+  ia.rear = P.rear;
+  ia.ctr = P.ctr;
+  KNNM_CUDA(launch_init(ia, st));
+  KNNM_CUDA(cudaMemcpyAsync(ctx->host_ctr, P.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+  KNNM_CUDA(cudaEventRecord(ctx->ev[1], st));
+  KNNM_CUDA(cudaStreamSynchronize(st));
+  if (ctx->host_ctr->err)
+    return fail(ctx, KNNM_ERR_INVALID, "input graph row %llu is malformed (%s)",
+                (unsigned long long)ctx->host_ctr->err_row,
+                (ctx->host_ctr->err & DERR_DUP_ID) ? "repeated id" : "id out of range or self");
+
+  knnm_stats local;
+  memset(&local, 0, sizeof(local));
+  SampleArgs sa;
+  sa.N = N;
+  sa.K = K;
+  sa.s = D.s;
+  sa.seed = params->seed;
+  sa.keys = P.keys;
+  sa.flags = P.flags;
+  sa.prev_keys = P.prev;
+  sa.rev_new = P.rev_new;
+  sa.rev_old = P.rev_old;
+  sa.cap_new = D.cap_new;
+  sa.cap_old = D.cap_old;
+  sa.new_ids = P.new_ids;
+  sa.new_cnt = P.new_cnt;
+  sa.old_ids = P.old_ids;
+  sa.old_cnt = P.old_cnt;
+  sa.ctr = P.ctr;
+  JoinArgs ja;
+  ja.mode = in.mode;
+  ja.rows = rows;
+  ja.N = N;
+  ja.n1 = in.n1;
+  ja.K = K;
+  ja.metric = params->metric;
+  ja.norms = P.norms;
+  ja.keys = P.keys;
+  ja.cap_new = D.cap_new;
+  ja.cap_old = D.cap_old;
+  ja.new_ids = P.new_ids;
+  ja.new_cnt = P.new_cnt;
+  ja.old_ids = P.old_ids;
+  ja.old_cnt = P.old_cnt;
+  ja.prop_tgt = P.prop_tgt;
+  ja.prop_key = P.prop_key;
+  ja.region_cap = region_cap;
+  ja.region_cnt = P.region_cnt;
+  ja.live_keys = P.keys;
+  ja.ctr = P.ctr;
+  ja.Xb = P.Xb;
+  ja.aux = P.aux;
+  ja.use_bulk = use_bulk ? 1 : 0;
+  UpdateArgs ua{P.prop_tgt, P.prop_key, P.keys, K};
+  FinalizeArgs fa{N, K, P.keys, P.prev, P.flags, P.ctr};
+
+  const double stop_at = (double)params->delta * (double)N * (double)K;
+  for (int t = 1; t <= params->max_iters; ++t) {
+    KNNM_CUDA(cudaMemsetAsync(P.ctr, 0, sizeof(DevCounters), st));
+    KNNM_CUDA(cudaMemsetAsync(&P.ctr->err_row, 0xFF, 8, st));
+    KNNM_CUDA(cudaMemsetAsync(P.rev_new, 0xFF, (size_t)N * D.s * 8, st));
+    KNNM_CUDA(cudaMemsetAsync(P.rev_old, 0xFF, (size_t)N * D.s * 8, st));
+    sa.t = t;
+    KNNM_CUDA(launch_sample(sa, st));
+    KNNM_CUDA(launch_join(precision, ja, plan, st));
+    KNNM_CUDA(launch_update_regions(ua, P.region_cnt, region_cap, plan.grid, st));
+    KNNM_CUDA(launch_finalize(fa, st));
+    KNNM_CUDA(cudaMemcpyAsync(ctx->host_ctr, P.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+    KNNM_CUDA(cudaStreamSynchronize(st));
+    const DevCounters& h = *ctx->host_ctr;
+    if (h.err)
+      return fail(ctx, KNNM_ERR_DEVICE, "round %d: device error bits 0x%llx (row %llu)", t,
+                  (unsigned long long)h.err, (unsigned long long)h.err_row);
+    local.updates[t - 1] = (int64_t)h.updates;
+    local.dist_evals[t - 1] = (int64_t)h.dist_evals;
+    local.proposals[t - 1] = (int64_t)h.proposals;
+    local.reranked[t - 1] = (int64_t)h.reranked;
+    local.rounds = t;
+    if ((double)h.updates <= stop_at) break;
+  }
+  KNNM_CUDA(cudaEventRecord(ctx->ev[2], st));
+  int32_t* oi = P.oi ? P.oi : out_ids;
+  float* od = P.od ? P.od : out_dists;
+  KNNM_CUDA(launch_final(N, K, P.keys, D.Kr, P.rear, oi, od, st));
+  KNNM_CUDA(cudaEventRecord(ctx->ev[3], st));
+  if (P.oi)
+    KNNM_CUDA(cudaMemcpyAsync(out_ids, P.oi, (size_t)N * K * 4, cudaMemcpyDeviceToHost, st));
+  if (P.od)
+    KNNM_CUDA(cudaMemcpyAsync(out_dists, P.od, (size_t)N * K * 4, cudaMemcpyDeviceToHost, st));
+  KNNM_CUDA(cudaStreamSynchronize(st));
+  if (stats) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+    local.ms_init = ms;
+    cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]);
+    local.ms_rounds = ms;
+    cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
+    local.ms_final = ms;
+    local.ms_total = (float)std::chrono::duration<double, std::milli>(
+                         std::chrono::steady_clock::now() - t_wall0)
+                         .count();
+    *stats = local;
+  }
+  return KNNM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+
+extern "C" int knnm_create(knnm_ctx** out, int device, void* cuda_stream) {
+  if (!out) return KNNM_ERR_INVALID;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return KNNM_ERR_INVALID;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return KNNM_ERR_CUDA;
+  knnm_ctx* c = new (std::nothrow) knnm_ctx();
+  if (!c) return KNNM_ERR_NOMEM;
+  c->device = device;
+  c->stream = (cudaStream_t)cuda_stream;
+  if (cudaMallocHost(&c->host_ctr, sizeof(DevCounters)) != cudaSuccess) {
+    delete c;
+    return KNNM_ERR_NOMEM;
+  }
+  for (auto& e : c->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      knnm_destroy(c);
+      return KNNM_ERR_CUDA;
+    }
+  *out = c;
+  return KNNM_OK;
+}
+
+extern "C" int knnm_destroy(knnm_ctx* c) {
+  if (!c) return KNNM_OK;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->arena) cudaFree(c->arena);
+  if (c->host_ctr) cudaFreeHost(c->host_ctr);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  delete c;
+  return KNNM_OK;
+}
+
+extern "C" int knnm_set_stream(knnm_ctx* c, void* s) {
+  if (!c) return KNNM_ERR_INVALID;
+  c->stream = (cudaStream_t)s;
+  return KNNM_OK;
+}
+
+extern "C" const char* knnm_last_error(const knnm_ctx* c) { return c ? c->err : "no context"; }
+
+extern "C" const char* knnm_strerror(int code) {
+  switch (code) {
+    case KNNM_OK: return "ok";
+    case KNNM_ERR_INVALID: return "invalid argument";
+    case KNNM_ERR_NOMEM: return "out of memory";
+    case KNNM_ERR_CUDA: return "CUDA error";
+    case KNNM_ERR_TIMEOUT: return "timeout";
+    case KNNM_ERR_NOT_READY: return "not ready";
+    case KNNM_ERR_DEVICE: return "device-side error";
+    default: return "unknown error";
+  }
+}
+
+extern "C" void knnm_default_params(knnm_params* p) {
+  if (!p) return;
+  p->k = 20;
+  p->metric = KNNM_L2;
+  p->precision = KNNM_FP32;
+  p->max_iters = 10;
+  p->sample_rate = 0.5f;
+  p->keep_ratio = 0.5f;
+  p->delta = 0.001f;
+  p->seed = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Whole merges
+// ---------------------------------------------------------------------------
+
+extern "C" int knnm_merge_symmetric(knnm_ctx* ctx, const float* S1, int64_t n1, const int32_t* G1,
+                                    const float* S2, int64_t n2, const int32_t* G2, int d,
+                                    const knnm_params* params, int32_t* out_ids, float* out_dists,
+                                    knnm_stats* stats) {
+  MergeIn in{SYMMETRIC, S1, n1, G1, S2, n2, G2, d};
+  return run_merge(ctx, in, params, out_ids, out_dists, stats);
+}
+
+extern "C" int knnm_merge_joint(knnm_ctx* ctx, const float* S1, int64_t n1, const int32_t* G1,
+                                const float* S_new, int64_t n2, int d, const knnm_params* params,
+                                int32_t* out_ids, float* out_dists, knnm_stats* stats) {
+  MergeIn in{JOINT, S1, n1, G1, S_new, n2, nullptr, d};
+  return run_merge(ctx, in, params, out_ids, out_dists, stats);
+}
+
+extern "C" int knnm_build(knnm_ctx* ctx, const float* S, int64_t n, int d,
+                          const knnm_params* params, int32_t* out_ids, float* out_dists,
+                          knnm_stats* stats) {
+  MergeIn in{JOINT, nullptr, 0, nullptr, S, n, nullptr, d};
+  return run_merge(ctx, in, params, out_ids, out_dists, stats);
+}
+
+// ---------------------------------------------------------------------------
+// Round steps (device pointers)
+// ---------------------------------------------------------------------------
+
+namespace {
+
+int check_rows(knnm_ctx* ctx, const float* X1, int64_t nx1, const float* X2, int64_t N, int d) {
+  if (!X1 || d < 1 || N < 1 || nx1 < 1 || nx1 > N || (nx1 < N && !X2) || N > 0x7FFFFFFFLL)
+    return fail(ctx, KNNM_ERR_INVALID, "bad row arrays");
+  return KNNM_OK;
+}
+
+int read_counters(knnm_ctx* ctx, DevCounters* dev) {
+  KNNM_CUDA(cudaMemcpyAsync(ctx->host_ctr, dev, sizeof(DevCounters), cudaMemcpyDeviceToHost,
+                            ctx->stream));
+  KNNM_CUDA(cudaStreamSynchronize(ctx->stream));
+  return KNNM_OK;
+}
+
+}  // namespace
+
+extern "C" int knnm_step_init(knnm_ctx* ctx, int mode, const float* X1, int64_t nx1,
+                              const float* X2, int64_t N, int64_t set_split, int d,
+                              const int32_t* G1, const int32_t* G2, const knnm_params* params,
+                              int32_t* ids, float* dists, uint8_t* flags, int32_t* rear_ids,
+                              float* rear_dists) {
+  if (!ctx) return KNNM_ERR_INVALID;
+  ctx->err[0] = 0;
+  int rc = check_rows(ctx, X1, nx1, X2, N, d);
+  if (rc) return rc;
+  Derived D;
+  rc = derive(ctx, params, mode, set_split, &D);
+  if (rc) return rc;
+  if (mode != SYMMETRIC && mode != JOINT) return fail(ctx, KNNM_ERR_INVALID, "bad mode");
+  if (set_split < 0 || set_split > N || (set_split > 0 && !G1) ||
+      (mode == SYMMETRIC && (!G2 || set_split == 0 || set_split == N)))
+    return fail(ctx, KNNM_ERR_INVALID, "bad graphs or split");
+  const int K = D.K;
+  cudaStream_t st = ctx->stream;
+  KNNM_CUDA(cudaSetDevice(ctx->device));
+  Carver c0;
+  auto carve = [&](Carver& c, uint64_t*& keys, uint64_t*& rear, float*& norms, DevCounters*& ctr) {
+    keys = c.take<uint64_t>((size_t)N * K);
+    rear = c.take<uint64_t>((size_t)N * (D.Kr > 0 ? D.Kr : 1));
+    norms = c.take<float>((size_t)N);
+    ctr = c.take<DevCounters>(1);
+  };
+  uint64_t *keys, *rear;
+  float* norms;
+  DevCounters* ctr;
+  carve(c0, keys, rear, norms, ctr);
+  rc = ensure_arena(ctx, c0.off);
+  if (rc) return rc;
+  Carver c1;
+  c1.base = (char*)ctx->arena;
+  carve(c1, keys, rear, norms, ctr);
+  Rows rows{X1, X2 ? X2 : X1, nx1, d};
+  KNNM_CUDA(cudaMemsetAsync(ctr, 0, sizeof(DevCounters), st));
+  KNNM_CUDA(cudaMemsetAsync(&ctr->err_row, 0xFF, 8, st));
+  if (params->metric == KNNM_COS) KNNM_CUDA(launch_norms(rows, N, norms, st));
+  InitArgs ia;
+  ia.mode = mode;
+  ia.rows = rows;
+  ia.N = N;
+  ia.n1 = set_split;
+  ia.G1 = G1;
+  ia.G2 = G2;
+  ia.K = K;
+  ia.K_keep = D.K_keep;
+  ia.metric = params->metric;
+  ia.seed = params->seed;
+  ia.norms = params->metric == KNNM_COS ? norms : nullptr;
+  ia.keys = keys;
+  ia.flags = flags;
+  ia.rear = rear;
+  ia.ctr = ctr;
+  KNNM_CUDA(launch_init(ia, st));
+  KNNM_CUDA(launch_unpack((int64_t)N * K, keys, ids, dists, st));
+  if (D.Kr > 0) KNNM_CUDA(launch_unpack((int64_t)N * D.Kr, rear, rear_ids, rear_dists, st));
+  rc = read_counters(ctx, ctr);
+  if (rc) return rc;
+  if (ctx->host_ctr->err)
+    return fail(ctx, KNNM_ERR_INVALID, "input graph row %llu is malformed",
+                (unsigned long long)ctx->host_ctr->err_row);
+  return KNNM_OK;
+}
+
+extern "C" int knnm_step_sample(knnm_ctx* ctx, int64_t N, int K, const int32_t* ids,
+                                const float* dists, uint8_t* flags, uint64_t seed, int t, int s,
+                                int cap_new, int cap_old, int32_t* new_ids, int32_t* new_cnt,
+                                int32_t* old_ids, int32_t* old_cnt) {
+  if (!ctx) return KNNM_ERR_INVALID;
+  ctx->err[0] = 0;
+  if (N < 1 || K < 1 || K > 32 || s < 1 || s > K || cap_new < 2 * s || cap_old < K + s || !ids ||
+      !dists || !flags || !new_ids || !new_cnt || !old_ids || !old_cnt)
+    return fail(ctx, KNNM_ERR_INVALID, "bad sampling arguments");
+  cudaStream_t st = ctx->stream;
+  KNNM_CUDA(cudaSetDevice(ctx->device));
+  auto carve = [&](Carver& c, uint64_t*& keys, uint64_t*& rn, uint64_t*& ro, DevCounters*& ctr) {
+    keys = c.take<uint64_t>((size_t)N * K);
+    rn = c.take<uint64_t>((size_t)N * s);
+    ro = c.take<uint64_t>((size_t)N * s);
+    ctr = c.take<DevCounters>(1);
+  };
+  uint64_t *keys, *rn, *ro;
+  DevCounters* ctr;
+  Carver c0;
+  carve(c0, keys, rn, ro, ctr);
+  int rc = ensure_arena(ctx, c0.off);
+  if (rc) return rc;
+  Carver c1;
+  c1.base = (char*)ctx->arena;
+  carve(c1, keys, rn, ro, ctr);
+  KNNM_CUDA(launch_pack((int64_t)N * K, ids, dists, keys, st));
+  KNNM_CUDA(cudaMemsetAsync(rn, 0xFF, (size_t)N * s * 8, st));
+  KNNM_CUDA(cudaMemsetAsync(ro, 0xFF, (size_t)N * s * 8, st));
+  KNNM_CUDA(cudaMemsetAsync(ctr, 0, sizeof(DevCounters), st));
+  SampleArgs sa;
+  sa.N = N;
+  sa.K = K;
+  sa.s = s;
+  sa.seed = seed;
+  sa.t = t;
+  sa.keys = keys;
+  sa.flags = flags;
+  sa.prev_keys = nullptr;
+  sa.rev_new = rn;
+  sa.rev_old = ro;
+  sa.cap_new = cap_new;
+  sa.cap_old = cap_old;
+  sa.new_ids = new_ids;
+  sa.new_cnt = new_cnt;
+  sa.old_ids = old_ids;
+  sa.old_cnt = old_cnt;
+  sa.ctr = ctr;
+  KNNM_CUDA(launch_sample(sa, st));
+  return read_counters(ctx, ctr);
+}
+
+extern "C" int knnm_step_join(knnm_ctx* ctx, int mode, const float* X1, int64_t nx1,
+                              const float* X2, int64_t N, int64_t set_split, int d,
+                              const knnm_params* params, int32_t* ids, float* dists,
+                              uint8_t* flags, int cap_new, int cap_old, const int32_t* new_ids,
+                              const int32_t* new_cnt, const int32_t* old_ids,
+                              const int32_t* old_cnt, int64_t* updates, int64_t* dist_evals) {
+  if (!ctx) return KNNM_ERR_INVALID;
+  ctx->err[0] = 0;
+  int rc = check_rows(ctx, X1, nx1, X2, N, d);
+  if (rc) return rc;
+  if (!params || params->k < 1 || params->k > 32 || params->metric < 0 || params->metric > 3)
+    return fail(ctx, KNNM_ERR_INVALID, "bad params");
+  if (cap_new < 1 || cap_old < 1 || cap_new + cap_old > 96 || set_split < 0 || set_split > N ||
+      (mode != SYMMETRIC && mode != JOINT))
+    return fail(ctx, KNNM_ERR_INVALID, "bad capacities, split or mode");
+  const int K = params->k;
+  const int precision = (params->precision == KNNM_BF16_RERANK && params->metric != KNNM_L1)
+                            ? KNNM_BF16_RERANK
+                            : KNNM_FP32;
+  if (precision == KNNM_BF16_RERANK && d % 8 != 0)
+    return fail(ctx, KNNM_ERR_INVALID, "the BF16 path needs d %% 8 == 0");
+  cudaStream_t st = ctx->stream;
+  KNNM_CUDA(cudaSetDevice(ctx->device));
+  JoinPlan plan;
+  {
+    cudaError_t e = plan_join(precision, params->metric, cap_new, cap_old, d, &plan);
+    if (e != cudaSuccess)
+      return fail(ctx, KNNM_ERR_INVALID, "no join configuration: %s", cudaGetErrorString(e));
+  }
+  uint64_t region_cap = ((uint64_t)N * 2 * cap_new * (cap_new + cap_old) + plan.grid - 1) / plan.grid;
+  if (region_cap < 256) region_cap = 256;
+  uint64_t *keys, *prev, *pkey;
+  int32_t* ptgt;
+  unsigned long long* rcnt;
+  float* norms;
+  __nv_bfloat16* Xb;
+  float4* aux;
+  DevCounters* ctr;
+  auto carve = [&](Carver& c) {
+    keys = c.take<uint64_t>((size_t)N * K);
+    prev = c.take<uint64_t>((size_t)N * K);
+    ptgt = c.take<int32_t>(region_cap * plan.grid);
+    pkey = c.take<uint64_t>(region_cap * plan.grid);
+    rcnt = c.take<unsigned long long>((size_t)plan.grid);
+    norms = c.take<float>((size_t)N);
+    Xb = precision == KNNM_BF16_RERANK ? c.take<__nv_bfloat16>((size_t)N * d) : nullptr;
+    aux = precision == KNNM_BF16_RERANK ? c.take<float4>((size_t)N) : nullptr;
+    ctr = c.take<DevCounters>(1);
+  };
+  Carver c0;
+  carve(c0);
+  rc = ensure_arena(ctx, c0.off);
+  if (rc) return rc;
+  Carver c1;
+  c1.base = (char*)ctx->arena;
+  carve(c1);
+  Rows rows{X1, X2 ? X2 : X1, nx1, d};
+  KNNM_CUDA(cudaMemsetAsync(ctr, 0, sizeof(DevCounters), st));
+  KNNM_CUDA(cudaMemsetAsync(&ctr->err_row, 0xFF, 8, st));
+  KNNM_CUDA(launch_pack((int64_t)N * K, ids, dists, keys, st));
+  KNNM_CUDA(cudaMemcpyAsync(prev, keys, (size_t)N * K * 8, cudaMemcpyDeviceToDevice, st));
+  if (params->metric == KNNM_COS) KNNM_CUDA(launch_norms(rows, N, norms, st));
+  if (Xb) KNNM_CUDA(launch_bf16_prep(rows, N, Xb, aux, st));
+  JoinArgs ja;
+  ja.mode = mode;
+  ja.rows = rows;
+  ja.N = N;
+  ja.n1 = set_split;
+  ja.K = K;
+  ja.metric = params->metric;
+  ja.norms = norms;
+  ja.keys = keys;
+  ja.cap_new = cap_new;
+  ja.cap_old = cap_old;
+  ja.new_ids = new_ids;
+  ja.new_cnt = new_cnt;
+  ja.old_ids = old_ids;
+  ja.old_cnt = old_cnt;
+  ja.prop_tgt = ptgt;
+  ja.prop_key = pkey;
+  ja.region_cap = region_cap;
+  ja.region_cnt = rcnt;
+  ja.live_keys = keys;
+  ja.ctr = ctr;
+  ja.Xb = Xb;
+  ja.aux = aux;
+  ja.use_bulk = (d % 4 == 0 && aligned16(rows.X1) && aligned16(rows.X2)) ? 1 : 0;
+  KNNM_CUDA(launch_join(precision, ja, plan, st));
+  UpdateArgs ua{ptgt, pkey, keys, K};
+  KNNM_CUDA(launch_update_regions(ua, rcnt, region_cap, plan.grid, st));
+  FinalizeArgs fa{N, K, keys, prev, flags, ctr};
+  KNNM_CUDA(launch_finalize(fa, st));
+  KNNM_CUDA(launch_unpack((int64_t)N * K, keys, ids, dists, st));
+  rc = read_counters(ctx, ctr);
+  if (rc) return rc;
+  if (ctx->host_ctr->err)
+    return fail(ctx, KNNM_ERR_DEVICE, "device error bits 0x%llx",
+                (unsigned long long)ctx->host_ctr->err);
+  if (updates) *updates = (int64_t)ctx->host_ctr->updates;
+  if (dist_evals) *dist_evals = (int64_t)ctx->host_ctr->dist_evals;
+  return KNNM_OK;
+}
+
+extern "C" int knnm_step_final(knnm_ctx* ctx, int64_t N, int K, const int32_t* ids,
+                               const float* dists, int Kr, const int32_t* rear_ids,
+                               const float* rear_dists, int32_t* out_ids, float* out_dists) {
+  if (!ctx) return KNNM_ERR_INVALID;
+  ctx->err[0] = 0;
+  if (N < 1 || K < 1 || K > 32 || Kr < 0 || Kr > 32 || !ids || !dists || !out_ids ||
+      !out_dists || (Kr > 0 && (!rear_ids || !rear_dists)))
+    return fail(ctx, KNNM_ERR_INVALID, "bad final-merge arguments");
+  cudaStream_t st = ctx->stream;
+  KNNM_CUDA(cudaSetDevice(ctx->device));
+  uint64_t *keys, *rear;
+  auto carve = [&](Carver& c) {
+    keys = c.take<uint64_t>((size_t)N * K);
+    rear = c.take<uint64_t>((size_t)N * (Kr > 0 ? Kr : 1));
+  };
+  Carver c0;
+  carve(c0);
+  int rc = ensure_arena(ctx, c0.off);
+  if (rc) return rc;
+  Carver c1;
+  c1.base = (char*)ctx->arena;
+  carve(c1);
+  KNNM_CUDA(launch_pack((int64_t)N * K, ids, dists, keys, st));
+  if (Kr > 0) KNNM_CUDA(launch_pack((int64_t)N * Kr, rear_ids, rear_dists, rear, st));
+  KNNM_CUDA(launch_final(N, K, keys, Kr, rear, out_ids, out_dists, st));
+  KNNM_CUDA(cudaStreamSynchronize(st));
+  return KNNM_OK;
+}

@@ -1,0 +1,399 @@
+// knnm_internal.cuh -- device helpers and kernel interfaces shared by the
+// translation units of libknnm.so (never installed, never seen by callers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace knnm {
+
+// ---------------------------------------------------------------------------
+// List entries are packed 64-bit keys: (orderable FP32 distance bits) << 32 |
+// id.  Unsigned comparison of two keys is the (distance, id) order of the
+// lists; equal keys mean the same id (distances are canonical, so one id has
+// one distance).  KEY_EMPTY sorts after every real entry.
+// ---------------------------------------------------------------------------
+constexpr uint64_t KEY_EMPTY = ~0ull;
+constexpr uint8_t FLAG_OLD = 0;
+constexpr uint8_t FLAG_NEW = 1;
+
+enum Metric { L2 = 0, IP = 1, COS = 2, L1 = 3 };
+enum Mode { SYMMETRIC = 0, JOINT = 1 };
+enum Stream { STREAM_FWD_NEW = 0, STREAM_REV_NEW = 1, STREAM_REV_OLD = 2, STREAM_INIT = 3 };
+
+// Error bits a kernel may raise in the context's device error word.
+enum DevErr : unsigned {
+  DERR_BAD_ID = 1u,        // input id out of range or self
+  DERR_DUP_ID = 2u,        // input row repeats an id
+  DERR_CAPACITY = 4u,      // candidate list longer than its capacity
+  DERR_WAIT_TIMEOUT = 8u,  // an mbarrier wait ran out of iterations
+  DERR_BAD_PAIR = 16u      // a candidate index out of range
+};
+
+__host__ __device__ __forceinline__ uint32_t float_to_ordered(float f) {
+#ifdef __CUDA_ARCH__
+  uint32_t u = __float_as_uint(f);
+#else
+  uint32_t u;
+  memcpy(&u, &f, 4);
+#endif
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__host__ __device__ __forceinline__ float ordered_to_float(uint32_t o) {
+  uint32_t u = (o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o;
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(u);
+#else
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+#endif
+}
+
+__host__ __device__ __forceinline__ uint64_t make_key(float dist, int32_t id) {
+  return ((uint64_t)float_to_ordered(dist) << 32) | (uint32_t)id;
+}
+__host__ __device__ __forceinline__ int32_t key_id(uint64_t k) { return (int32_t)(uint32_t)k; }
+__host__ __device__ __forceinline__ float key_dist(uint64_t k) {
+  return ordered_to_float((uint32_t)(k >> 32));
+}
+
+// ---------------------------------------------------------------------------
+// Counter-based random numbers: chained SplitMix64 steps (Steele, Lea and
+// Flood, OOPSLA 2014), one step per absorbed 64-bit word.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint64_t mix_step(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Hash prefix over (seed, t, stream, owner); absorb the member with mix_step.
+__host__ __device__ __forceinline__ uint64_t hash_prefix(uint64_t seed, uint64_t t,
+                                                         uint64_t stream, uint64_t owner) {
+  return mix_step(mix_step(mix_step(mix_step(seed) ^ t) ^ stream) ^ owner);
+}
+
+// Sampling key: high half of the hash, member id in the low half.
+__host__ __device__ __forceinline__ uint64_t sampling_key(uint64_t prefix, int32_t member) {
+  uint64_t h = mix_step(prefix ^ (uint64_t)(int64_t)member);
+  return (h & 0xFFFFFFFF00000000ull) | (uint32_t)member;
+}
+
+// ---------------------------------------------------------------------------
+// Canonical FP32 distances: one accumulator, dimensions in index order,
+// correctly rounded operations only (no reassociation, no contraction).
+// ---------------------------------------------------------------------------
+template <int METRIC>
+struct Canon;
+
+template <>
+struct Canon<L2> {
+  __device__ __forceinline__ static float step(float acc, float a, float b) {
+    float x = __fsub_rn(a, b);
+    return __fmaf_rn(x, x, acc);
+  }
+};
+template <>
+struct Canon<IP> {
+  __device__ __forceinline__ static float step(float acc, float a, float b) {
+    return __fmaf_rn(a, b, acc);
+  }
+};
+template <>
+struct Canon<COS> {
+  __device__ __forceinline__ static float step(float acc, float a, float b) {
+    return __fmaf_rn(a, b, acc);
+  }
+};
+template <>
+struct Canon<L1> {
+  __device__ __forceinline__ static float step(float acc, float a, float b) {
+    return __fadd_rn(acc, fabsf(__fsub_rn(a, b)));
+  }
+};
+
+// Turns the accumulated value into the distance.  `na`, `nb` are the
+// canonical norms (sqrt of the in-order fmaf sum of squares), used by COS only.
+template <int METRIC>
+__device__ __forceinline__ float canon_finish(float acc, float na, float nb) {
+  if (METRIC == IP) return __fsub_rn(0.0f, acc);
+  if (METRIC == COS) {
+    float den = __fmul_rn(na, nb);
+    if (den == 0.0f) return 1.0f;
+    return __fsub_rn(1.0f, __fdiv_rn(acc, den));
+  }
+  return acc;
+}
+
+// Canonical distance of two rows read from global memory (any alignment).
+template <int METRIC>
+__device__ __forceinline__ float canon_dist_global(const float* __restrict__ a,
+                                                   const float* __restrict__ b, int d, float na,
+                                                   float nb) {
+  float acc = 0.0f;
+  for (int t = 0; t < d; ++t) acc = Canon<METRIC>::step(acc, __ldg(a + t), __ldg(b + t));
+  return canon_finish<METRIC>(acc, na, nb);
+}
+
+__device__ __forceinline__ float canon_norm_global(const float* __restrict__ a, int d) {
+  float acc = 0.0f;
+  for (int t = 0; t < d; ++t) {
+    float v = __ldg(a + t);
+    acc = __fmaf_rn(v, v, acc);
+  }
+  return __fsqrt_rn(acc);
+}
+
+// Row i of the dataset split in two arrays (rows < nx1 in X1, the rest in X2).
+struct Rows {
+  const float* X1;
+  const float* X2;
+  int64_t nx1;
+  int d;
+  __host__ __device__ __forceinline__ const float* row(int64_t i) const {
+    return i < nx1 ? X1 + (size_t)i * d : X2 + (size_t)(i - nx1) * d;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Warp utilities (K <= 32 entries: one per lane).
+// ---------------------------------------------------------------------------
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+// Ascending bitonic sort of one 64-bit key per lane.
+__device__ __forceinline__ uint64_t warp_sort32(uint64_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      uint64_t o = __shfl_xor_sync(FULL, v, j);
+      bool lower = (lane & j) == 0;
+      bool asc = (lane & k) == 0;
+      uint64_t mn = v < o ? v : o, mx = v < o ? o : v;
+      v = (lower == asc) ? mn : mx;
+    }
+  }
+  return v;
+}
+
+// Ascending bitonic sort of 64 keys, element e = h*32 + lane held in v[h].
+__device__ __forceinline__ void warp_sort64(uint64_t& v0, uint64_t& v1) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j == 32) {
+        // partners are (lane, h=0) and (lane, h=1); both ascending for k = 64
+        uint64_t mn = v0 < v1 ? v0 : v1, mx = v0 < v1 ? v1 : v0;
+        v0 = mn;
+        v1 = mx;
+      } else {
+        uint64_t o0 = __shfl_xor_sync(FULL, v0, j);
+        uint64_t o1 = __shfl_xor_sync(FULL, v1, j);
+        bool lower = (lane & j) == 0;
+        bool asc0 = ((lane) & k) == 0;
+        bool asc1 = ((lane + 32) & k) == 0;
+        uint64_t mn0 = v0 < o0 ? v0 : o0, mx0 = v0 < o0 ? o0 : v0;
+        uint64_t mn1 = v1 < o1 ? v1 : o1, mx1 = v1 < o1 ? o1 : v1;
+        v0 = (lower == asc0) ? mn0 : mx0;
+        v1 = (lower == asc1) ? mn1 : mx1;
+      }
+    }
+  }
+}
+
+// Inserts `x` into the ascending array slots[0..m) that keeps the m smallest
+// distinct keys ever offered to it.  Slots only ever decrease (atomicMin), so
+// the result does not depend on the order or interleaving of insertions: slot
+// j ends up holding the (j+1)-th smallest distinct key offered.  A key equal
+// to one already held is a duplicate and is dropped.  Reads of slots that are
+// already below x skip ahead; a stale read only makes the skip shorter.
+__device__ __forceinline__ void slots_insert(uint64_t* slots, int m, uint64_t x) {
+  int j = 0;
+  for (; j < m; ++j) {
+    uint64_t cur = *((volatile uint64_t*)(slots + j));
+    if (cur == x) return;
+    if (cur > x) break;
+  }
+  for (; j < m; ++j) {
+    unsigned long long old = atomicMin((unsigned long long*)(slots + j), (unsigned long long)x);
+    if (old == x) return;
+    if (old > x) {
+      if (old == KEY_EMPTY) return;
+      x = old;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier + bulk async copy (the TMA engine's non-tensor form).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// 1-D bulk copy global -> shared, completion counted on `bar` in bytes.
+// dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after `limit` polls (each poll may suspend briefly).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+constexpr uint32_t WAIT_LIMIT = 1u << 22;
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (defined in knnm_kernels.cu / knnm_join.cu).  All take the
+// stream they run on and return cudaGetLastError() of the launch.
+// ---------------------------------------------------------------------------
+struct DevCounters {
+  unsigned long long updates;     // c_t
+  unsigned long long dist_evals;  // pairs compared
+  unsigned long long proposals;   // proposals written to the buffer
+  unsigned long long overflow;    // proposals inserted directly (buffer full)
+  unsigned long long reranked;    // BF16 path: FP32 recomputations
+  unsigned long long err;         // DevErr bits
+  unsigned long long err_row;     // smallest offending row
+  unsigned long long pad;
+};
+
+struct InitArgs {
+  int mode;
+  Rows rows;
+  int64_t N, n1;
+  const int32_t* G1;
+  const int32_t* G2;
+  int K, K_keep, metric;
+  uint64_t seed;
+  const float* norms;  // canonical norms [N] for COS, else nullptr
+  uint64_t* keys;      // [N][K]
+  uint8_t* flags;      // [N][K]
+  uint64_t* rear;      // [N][Kr]
+  DevCounters* ctr;
+};
+cudaError_t launch_init(const InitArgs& a, cudaStream_t st);
+
+cudaError_t launch_norms(Rows rows, int64_t N, float* norms, cudaStream_t st);
+
+struct SampleArgs {
+  int64_t N;
+  int K, s;
+  uint64_t seed;
+  int t;
+  const uint64_t* keys;   // [N][K]
+  uint8_t* flags;         // [N][K], sampled entries flipped to old
+  uint64_t* prev_keys;    // [N][K] snapshot for the finalize step (may be null)
+  uint64_t* rev_new;      // [N][s] slots, KEY_EMPTY-initialised
+  uint64_t* rev_old;      // [N][s]
+  int cap_new, cap_old;
+  int32_t* new_ids;  // [N][cap_new]
+  int32_t* new_cnt;  // [N]
+  int32_t* old_ids;  // [N][cap_old]
+  int32_t* old_cnt;  // [N]
+  DevCounters* ctr;
+};
+cudaError_t launch_sample(const SampleArgs& a, cudaStream_t st);
+
+struct JoinArgs {
+  int mode;
+  Rows rows;
+  int64_t N, n1;
+  int K, metric;
+  const float* norms;  // COS
+  const uint64_t* keys;  // round-start lists [N][K] (read for the k-th key)
+  int cap_new, cap_old;
+  const int32_t* new_ids;
+  const int32_t* new_cnt;
+  const int32_t* old_ids;
+  const int32_t* old_cnt;
+  int32_t* prop_tgt;   // proposal buffer: block b writes region b
+  uint64_t* prop_key;
+  uint64_t region_cap;  // proposals per region
+  unsigned long long* region_cnt;  // [grid] proposals written per region
+  uint64_t* live_keys;  // lists receiving direct inserts when a region is full
+  DevCounters* ctr;
+  // BF16 path
+  const __nv_bfloat16* Xb;  // [N][d] bf16 copy
+  const float4* aux;        // per-row {bf16 squared norm, bf16 rounding-error norm, bf16 norm, canonical norm}
+  int use_bulk;             // rows may be fetched with bulk async copies
+};
+// Persistent join kernels: `grid` blocks loop over the nodes.
+struct JoinPlan {
+  int grid;       // blocks (= proposal regions)
+  size_t smem;    // dynamic shared memory per block
+  int chunk;      // dimensions staged per pass (FP32 kernel)
+};
+cudaError_t plan_join(int precision, int metric, int cap_new, int cap_old, int d, JoinPlan* out);
+cudaError_t launch_join(int precision, const JoinArgs& a, const JoinPlan& plan, cudaStream_t st);
+
+struct UpdateArgs {
+  const int32_t* prop_tgt;  // proposal buffer, region b = [b*region_cap, (b+1)*region_cap)
+  const uint64_t* prop_key;
+  uint64_t* keys;  // [N][K] lists receiving the proposals
+  int K;
+};
+// One block per region; region_cnt[b] proposals were written into region b.
+cudaError_t launch_update_regions(const UpdateArgs& a, const unsigned long long* region_cnt,
+                                  uint64_t region_cap, int regions, cudaStream_t st);
+
+struct FinalizeArgs {
+  int64_t N;
+  int K;
+  const uint64_t* keys;
+  const uint64_t* prev_keys;
+  uint8_t* flags;
+  DevCounters* ctr;
+};
+cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t st);
+
+cudaError_t launch_final(int64_t N, int K, const uint64_t* keys, int Kr, const uint64_t* rear,
+                         int32_t* out_ids, float* out_dists, cudaStream_t st);
+
+// Conversions between the packed working lists and the (ids, dists) arrays.
+cudaError_t launch_pack(int64_t count, const int32_t* ids, const float* dists, uint64_t* keys,
+                        cudaStream_t st);
+cudaError_t launch_unpack(int64_t count, const uint64_t* keys, int32_t* ids, float* dists,
+                          cudaStream_t st);
+
+// BF16 shadow copy and per-row error data for the tensor-core path.
+cudaError_t launch_bf16_prep(Rows rows, int64_t N, __nv_bfloat16* Xb, float4* aux,
+                             cudaStream_t st);
+
+}  // namespace knnm

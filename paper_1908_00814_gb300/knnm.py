@@ -1,0 +1,279 @@
+"""Thin ctypes binding over libknnm.so (declared in include/knnm.h).
+
+Only argument marshalling happens here: every step of a merge runs in the
+library's CUDA kernels.  Arrays may be torch tensors (CUDA or CPU) or numpy
+arrays; CUDA tensors are passed as device pointers, everything else as host
+pointers (the library copies host data in and out inside the call).  Importing
+this module does not load the library; the first call does, and raises if the
+library has not been built (``paper_1908_00814_gb300.build``).
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+
+_LIB_PATH = Path(__file__).resolve().parent / "libknnm.so"
+
+L2, IP, COS, L1 = 0, 1, 2, 3
+FP32, BF16_RERANK = 0, 1
+SYMMETRIC, JOINT = 0, 1
+MAX_ROUNDS = 64
+METRICS = {"l2": L2, "ip": IP, "cos": COS, "l1": L1}
+
+ERRORS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA error",
+          -4: "timeout", -5: "not ready", -6: "device-side error"}
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("metric", ctypes.c_int), ("precision", ctypes.c_int),
+                ("max_iters", ctypes.c_int), ("sample_rate", ctypes.c_float),
+                ("keep_ratio", ctypes.c_float), ("delta", ctypes.c_float),
+                ("seed", ctypes.c_uint64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int),
+                ("updates", ctypes.c_int64 * MAX_ROUNDS),
+                ("dist_evals", ctypes.c_int64 * MAX_ROUNDS),
+                ("proposals", ctypes.c_int64 * MAX_ROUNDS),
+                ("reranked", ctypes.c_int64 * MAX_ROUNDS),
+                ("ms_init", ctypes.c_float), ("ms_rounds", ctypes.c_float),
+                ("ms_final", ctypes.c_float), ("ms_total", ctypes.c_float)]
+
+    def as_dict(self):
+        r = self.rounds
+        return {"rounds": r, "updates": list(self.updates[:r]),
+                "dist_evals": list(self.dist_evals[:r]), "proposals": list(self.proposals[:r]),
+                "reranked": list(self.reranked[:r]), "ms_init": self.ms_init,
+                "ms_rounds": self.ms_rounds, "ms_final": self.ms_final,
+                "ms_total": self.ms_total}
+
+
+_lib = None
+
+# name -> (restype, argtypes) of every entry point in include/knnm.h
+_P, _I, _I64, _U64, _F = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_float
+SIGNATURES = {
+    "knnm_create": (_I, [ctypes.POINTER(ctypes.c_void_p), _I, _P]),
+    "knnm_destroy": (_I, [_P]),
+    "knnm_set_stream": (_I, [_P, _P]),
+    "knnm_last_error": (ctypes.c_char_p, [_P]),
+    "knnm_strerror": (ctypes.c_char_p, [_I]),
+    "knnm_default_params": (None, [ctypes.POINTER(Params)]),
+    "knnm_merge_symmetric": (_I, [_P, _P, _I64, _P, _P, _I64, _P, _I, ctypes.POINTER(Params),
+                                  _P, _P, ctypes.POINTER(Stats)]),
+    "knnm_merge_joint": (_I, [_P, _P, _I64, _P, _P, _I64, _I, ctypes.POINTER(Params), _P, _P,
+                              ctypes.POINTER(Stats)]),
+    "knnm_build": (_I, [_P, _P, _I64, _I, ctypes.POINTER(Params), _P, _P,
+                        ctypes.POINTER(Stats)]),
+    "knnm_step_init": (_I, [_P, _I, _P, _I64, _P, _I64, _I64, _I, _P, _P, ctypes.POINTER(Params),
+                            _P, _P, _P, _P, _P]),
+    "knnm_step_sample": (_I, [_P, _I64, _I, _P, _P, _P, _U64, _I, _I, _I, _I, _P, _P, _P, _P]),
+    "knnm_step_join": (_I, [_P, _I, _P, _I64, _P, _I64, _I64, _I, ctypes.POINTER(Params), _P, _P,
+                            _P, _I, _I, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int64),
+                            ctypes.POINTER(ctypes.c_int64)]),
+    "knnm_step_final": (_I, [_P, _I64, _I, _P, _P, _I, _P, _P, _P, _P]),
+}
+
+
+def lib_path() -> Path:
+    return _LIB_PATH
+
+
+def lib():
+    """Loads libknnm.so; raises if it is missing (there is no fallback path)."""
+    global _lib
+    if _lib is None:
+        if not _LIB_PATH.exists():
+            raise RuntimeError(f"{_LIB_PATH} is not built: run python -m "
+                               "paper_1908_00814_gb300.build (no CPU fallback exists)")
+        L = ctypes.CDLL(str(_LIB_PATH))
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class KnnmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def params(k=20, metric="l2", precision="fp32", max_iters=10, sample_rate=0.5, keep_ratio=0.5,
+           delta=0.001, seed=0) -> Params:
+    p = Params()
+    p.k = k
+    p.metric = METRICS[metric] if isinstance(metric, str) else int(metric)
+    p.precision = {"fp32": FP32, "bf16": BF16_RERANK}[precision] if isinstance(precision, str) \
+        else int(precision)
+    p.max_iters = max_iters
+    p.sample_rate = sample_rate
+    p.keep_ratio = keep_ratio
+    p.delta = delta
+    p.seed = seed
+    return p
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """Device or host pointer of a tensor / array (None stays None)."""
+    if x is None:
+        return None
+    if _is_torch(x):
+        assert x.is_contiguous(), "arrays must be contiguous"
+        return ctypes.c_void_p(x.data_ptr())
+    assert x.flags["C_CONTIGUOUS"], "arrays must be contiguous"
+    return x.ctypes.data_as(ctypes.c_void_p)
+
+
+def _current_stream(device):
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+class Context:
+    """A library context bound to one device; follows torch's current stream."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        h = ctypes.c_void_p()
+        rc = lib().knnm_create(ctypes.byref(h), device, None)
+        if rc != 0:
+            raise KnnmError(rc, "knnm_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().knnm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _sync_stream(self):
+        try:
+            import torch
+            if torch.cuda.is_available():
+                lib().knnm_set_stream(self.h, _current_stream(self.device))
+        except ImportError:
+            pass
+
+    def _check(self, rc):
+        if rc != 0:
+            raise KnnmError(rc, lib().knnm_last_error(self.h).decode())
+
+    # ------------------------------------------------------------ whole merges
+    def _outputs(self, like, n, k):
+        if _is_torch(like):
+            import torch
+            dev = like.device if like.is_cuda else "cpu"
+            return (torch.empty((n, k), dtype=torch.int32, device=dev),
+                    torch.empty((n, k), dtype=torch.float32, device=dev))
+        return np.empty((n, k), np.int32), np.empty((n, k), np.float32)
+
+    def merge_symmetric(self, S1, G1, S2, G2, p: Params):
+        n1, d = S1.shape
+        n2 = S2.shape[0]
+        ids, dists = self._outputs(S1, n1 + n2, p.k)
+        st = Stats()
+        self._sync_stream()
+        self._check(lib().knnm_merge_symmetric(self.h, _ptr(S1), n1, _ptr(G1), _ptr(S2), n2,
+                                               _ptr(G2), d, ctypes.byref(p), _ptr(ids),
+                                               _ptr(dists), ctypes.byref(st)))
+        return ids, dists, st.as_dict()
+
+    def merge_joint(self, S1, G1, S_new, p: Params):
+        n1, d = S1.shape
+        n2 = S_new.shape[0]
+        ids, dists = self._outputs(S_new, n1 + n2, p.k)
+        st = Stats()
+        self._sync_stream()
+        self._check(lib().knnm_merge_joint(self.h, _ptr(S1), n1, _ptr(G1), _ptr(S_new), n2, d,
+                                           ctypes.byref(p), _ptr(ids), _ptr(dists),
+                                           ctypes.byref(st)))
+        return ids, dists, st.as_dict()
+
+    def build(self, S, p: Params):
+        n, d = S.shape
+        ids, dists = self._outputs(S, n, p.k)
+        st = Stats()
+        self._sync_stream()
+        self._check(lib().knnm_build(self.h, _ptr(S), n, d, ctypes.byref(p), _ptr(ids),
+                                     _ptr(dists), ctypes.byref(st)))
+        return ids, dists, st.as_dict()
+
+    # ------------------------------------------------------------ round steps
+    # All arrays: CUDA torch tensors.
+    def step_init(self, mode, X, set_split, G1, G2, p: Params):
+        import torch
+        N, d = X.shape
+        K = p.k
+        K_keep = int(float(np.float32(p.keep_ratio)) * K)
+        if mode == JOINT and set_split == 0:
+            K_keep = K
+        Kr = K - K_keep
+        dev = X.device
+        ids = torch.empty((N, K), dtype=torch.int32, device=dev)
+        dists = torch.empty((N, K), dtype=torch.float32, device=dev)
+        flags = torch.empty((N, K), dtype=torch.uint8, device=dev)
+        rid = torch.empty((N, max(Kr, 0)), dtype=torch.int32, device=dev)
+        rd = torch.empty((N, max(Kr, 0)), dtype=torch.float32, device=dev)
+        self._sync_stream()
+        self._check(lib().knnm_step_init(self.h, mode, _ptr(X), N, None, N, set_split, d,
+                                         _ptr(G1), _ptr(G2), ctypes.byref(p), _ptr(ids),
+                                         _ptr(dists), _ptr(flags), _ptr(rid) if Kr else None,
+                                         _ptr(rd) if Kr else None))
+        return ids, dists, flags, rid, rd
+
+    def step_sample(self, ids, dists, flags, seed, t, s, cap_new=None, cap_old=None):
+        import torch
+        N, K = ids.shape
+        cap_new = cap_new or 2 * s
+        cap_old = cap_old or K + s
+        dev = ids.device
+        new_ids = torch.full((N, cap_new), -1, dtype=torch.int32, device=dev)
+        old_ids = torch.full((N, cap_old), -1, dtype=torch.int32, device=dev)
+        new_cnt = torch.zeros(N, dtype=torch.int32, device=dev)
+        old_cnt = torch.zeros(N, dtype=torch.int32, device=dev)
+        self._sync_stream()
+        self._check(lib().knnm_step_sample(self.h, N, K, _ptr(ids), _ptr(dists), _ptr(flags), seed,
+                                           t, s, cap_new, cap_old, _ptr(new_ids), _ptr(new_cnt),
+                                           _ptr(old_ids), _ptr(old_cnt)))
+        return new_ids, new_cnt, old_ids, old_cnt
+
+    def step_join(self, mode, X, set_split, p: Params, ids, dists, flags, cands):
+        N, d = X.shape
+        new_ids, new_cnt, old_ids, old_cnt = cands
+        upd = ctypes.c_int64(0)
+        ev = ctypes.c_int64(0)
+        self._sync_stream()
+        self._check(lib().knnm_step_join(self.h, mode, _ptr(X), N, None, N, set_split, d,
+                                         ctypes.byref(p), _ptr(ids), _ptr(dists), _ptr(flags),
+                                         new_ids.shape[1], old_ids.shape[1], _ptr(new_ids),
+                                         _ptr(new_cnt), _ptr(old_ids), _ptr(old_cnt),
+                                         ctypes.byref(upd), ctypes.byref(ev)))
+        return int(upd.value), int(ev.value)
+
+    def step_final(self, ids, dists, rear_ids, rear_dists):
+        import torch
+        N, K = ids.shape
+        Kr = rear_ids.shape[1]
+        out_i = torch.empty_like(ids)
+        out_d = torch.empty_like(dists)
+        self._sync_stream()
+        self._check(lib().knnm_step_final(self.h, N, K, _ptr(ids), _ptr(dists), Kr,
+                                          _ptr(rear_ids) if Kr else None,
+                                          _ptr(rear_dists) if Kr else None, _ptr(out_i),
+                                          _ptr(out_d)))
+        return out_i, out_d

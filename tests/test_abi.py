@@ -1,0 +1,65 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+that include/knnm.h declares; the Python binding covers exactly those.  No
+compute call is made here (no GPU needed)."""
+import ctypes
+import re
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parents[1]
+HEADER = ROOT / "include" / "knnm.h"
+
+
+def declared_functions():
+    text = HEADER.read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(knnm_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def built_lib():
+    from paper_1908_00814_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(str(path))
+
+
+def test_header_declares_the_merge_calls():
+    names = declared_functions()
+    for must in ("knnm_merge_symmetric", "knnm_merge_joint", "knnm_build", "knnm_step_init",
+                 "knnm_step_sample", "knnm_step_join", "knnm_step_final", "knnm_create",
+                 "knnm_destroy"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(built_lib):
+    missing = [n for n in declared_functions() if not hasattr(built_lib, n)]
+    assert not missing, missing
+
+
+def test_binding_matches_header(built_lib):
+    from paper_1908_00814_gb300 import knnm
+    assert sorted(knnm.SIGNATURES) == declared_functions()
+
+
+def test_library_targets_sm103a(built_lib):
+    from paper_1908_00814_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+
+
+def test_strerror_needs_no_gpu(built_lib):
+    built_lib.knnm_strerror.restype = ctypes.c_char_p
+    assert built_lib.knnm_strerror(-1) == b"invalid argument"
+    built_lib.knnm_default_params.argtypes = [ctypes.c_void_p]
+    from paper_1908_00814_gb300 import knnm
+    p = knnm.Params()
+    built_lib.knnm_default_params(ctypes.byref(p))
+    assert p.k == 20 and abs(p.sample_rate - 0.5) < 1e-7 and p.max_iters == 10
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    from paper_1908_00814_gb300 import knnm
+    monkeypatch.setattr(knnm, "_LIB_PATH", tmp_path / "missing.so")
+    monkeypatch.setattr(knnm, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        knnm.lib()

@@ -1,0 +1,340 @@
+"""Parity of the CUDA library (through the C ABI) with the CPU oracle.
+
+Every comparison is element by element on the same seeded inputs: ids and
+flags bit-exact, distances bit-exact (both sides compute the canonical FP32
+distance), per-round counters equal.  The BF16 tensor-core path must produce
+the very same graphs as the FP32 path (its re-rank is exact whenever the
+error bound cannot rule a pair out).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1908_00814_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as _t
+    if not _t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return _t
+
+
+@pytest.fixture(scope="module")
+def km(torch):
+    from paper_1908_00814_gb300 import build, knnm
+    build.build()
+    return knnm
+
+
+@pytest.fixture(scope="module")
+def ctx(km):
+    return km.Context(0)
+
+
+def cuda(torch, a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+def assert_same(a, b, what=""):
+    a, b = np.asarray(a), np.asarray(b)
+    assert a.shape == b.shape, (what, a.shape, b.shape)
+    if a.dtype == np.float32:
+        bad = a.view(np.uint32) != b.view(np.uint32)
+    else:
+        bad = a != b
+    if bad.any():
+        idx = np.argwhere(bad)[:5]
+        raise AssertionError(f"{what}: {bad.sum()} mismatches, first at {idx.tolist()}: "
+                             f"{a[tuple(idx[0])]} vs {b[tuple(idx[0])]}")
+
+
+def split_data(seed=3, n1=700, n2=600, d=16, kind="gmm"):
+    if kind == "sift":
+        X = datagen.sift_like(n1 + n2, d, seed=seed)
+    else:
+        X = datagen.gaussian_mixture(n1 + n2, d, n_comp=8, seed=seed)
+    return X, n1
+
+
+METRIC_NAMES = {0: "l2", 1: "ip", 2: "cos", 3: "l1"}
+
+
+# ------------------------------------------------------------------ steps
+
+def test_hand_traced_round(torch, km, ctx):
+    fx = json.load(open(os.path.join(GOLDEN, "hand_round_3p3.json")))
+    X = np.array(fx["points"], np.float32)[:, None].repeat(4, 1) * np.array([1, 0, 0, 0],
+                                                                            np.float32)
+    n = len(X)
+    gs = fx["graph_script"]
+    cap = max(len(g) for g in gs)
+    new_ids = np.full((n, cap), -1, np.int32)
+    for u, g in enumerate(gs):
+        new_ids[u, :len(g)] = g
+    new_cnt = np.array([len(g) for g in gs], np.int32)
+    old_ids = np.full((n, 1), -1, np.int32)
+    old_cnt = np.zeros(n, np.int32)
+    for mode, key in ((km.SYMMETRIC, "symmetric"), (km.JOINT, "joint")):
+        ids = cuda(torch, np.array(fx["start_ids"], np.int32))
+        dists = cuda(torch, np.array(fx["start_dists"], np.float32))
+        flags = cuda(torch, np.zeros((n, 2), np.uint8))
+        p = km.params(k=2, metric="l2")
+        c, ev = ctx.step_join(mode, cuda(torch, X), fx["n1"], p, ids, dists, flags,
+                              tuple(cuda(torch, a) for a in (new_ids, new_cnt, old_ids, old_cnt)))
+        exp = fx[key]
+        assert ev == exp["dist_evals"] and c == exp["updates"]
+        assert host(ids).tolist() == exp["end_ids"]
+        assert host(dists).tolist() == exp["end_dists"]
+        if "end_inserted" in exp:
+            assert host(flags).tolist() == exp["end_inserted"]
+
+
+@pytest.mark.parametrize("mode", ["symmetric", "joint", "build"])
+@pytest.mark.parametrize("metric", [0, 1, 2, 3])
+def test_init_parity(torch, km, ctx, orc, mode, metric):
+    X, n1 = split_data(seed=5 + metric)
+    n = len(X)
+    K = 10
+    G1 = G2 = None
+    if mode != "build":
+        G1, _ = orc.bruteforce_knn(X[:n1], K, metric=metric)
+        # shuffle the rows' order: init must re-sort the input lists
+        G1 = np.random.default_rng(0).permuted(G1, axis=1)
+    if mode == "symmetric":
+        G2, _ = orc.bruteforce_knn(X[n1:], K, metric=metric)
+    m = orc.SYMMETRIC if mode == "symmetric" else orc.JOINT
+    split = 0 if mode == "build" else n1
+    Kk = K if mode == "build" else orc.keep_count(K, 0.5)
+    ref = orc.init(m, X, split, K, Kk, seed=9, metric=metric, G1=G1, G2=G2)
+    p = km.params(k=K, metric=metric, seed=9)
+    got = ctx.step_init(m, cuda(torch, X), split, None if G1 is None else cuda(torch, G1),
+                        None if G2 is None else cuda(torch, G2), p)
+    assert_same(host(got[0]), ref.ids, "ids")
+    assert_same(host(got[1]), ref.dists, "dists")
+    assert_same(host(got[2]), ref.flags, "flags")
+    if ref.rear_ids.shape[1]:
+        assert_same(host(got[3]), ref.rear_ids, "rear ids")
+        assert_same(host(got[4]), ref.rear_dists, "rear dists")
+
+
+@pytest.mark.parametrize("K,s,n", [(10, 5, 1300), (20, 10, 2049), (7, 3, 33), (32, 16, 500),
+                                   (1, 1, 40)])
+def test_sample_parity(torch, km, ctx, orc, K, s, n):
+    X = datagen.gaussian_mixture(n, 8, seed=K)
+    st = orc.init(orc.JOINT, X, 0, K, K, seed=4)
+    rng = np.random.default_rng(K)
+    st.flags[:] = (rng.random(st.flags.shape) < 0.55).astype(np.uint8)
+    flags_gpu = cuda(torch, st.flags)
+    ids_gpu, d_gpu = cuda(torch, st.ids), cuda(torch, st.dists)
+    ref = orc.sample(st, 21, 3, s)
+    got = ctx.step_sample(ids_gpu, d_gpu, flags_gpu, 21, 3, s)
+    assert_same(host(flags_gpu), st.flags, "flipped flags")
+    for a, b, what in ((got[1], ref[1], "new_cnt"), (got[3], ref[3], "old_cnt")):
+        assert_same(host(a), b, what)
+    for u in range(n):
+        assert host(got[0][u, :ref[1][u]]).tolist() == ref[0][u, :ref[1][u]].tolist()
+        assert host(got[2][u, :ref[3][u]]).tolist() == ref[2][u, :ref[3][u]].tolist()
+
+
+def _join_case(orc, X, n1, K, mode, metric, seed=1, t=2, s=None):
+    """Oracle state after init + one round, then the candidate sets of the next."""
+    G1 = G2 = None
+    if n1 > 0:
+        G1, _ = orc.bruteforce_knn(X[:n1], K, metric=metric)
+    if mode == orc.SYMMETRIC:
+        G2, _ = orc.bruteforce_knn(X[n1:], K, metric=metric)
+    Kk = K if n1 == 0 else orc.keep_count(K, 0.5)
+    st = orc.init(mode, X, n1, K, Kk, seed=seed, metric=metric, G1=G1, G2=G2)
+    s = s or orc.sample_count(K, 0.5)
+    cands = orc.sample(st, seed, 1, s)
+    orc.join(mode, X, n1, st, cands, metric=metric)
+    cands = orc.sample(st, seed, t, s)
+    return st, cands
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("metric", [0, 1, 2, 3])
+@pytest.mark.parametrize("mode", ["symmetric", "joint", "build"])
+def test_join_parity(torch, km, ctx, orc, precision, metric, mode):
+    X, n1 = split_data(seed=11 + metric, n1=800, n2=700, d=24)
+    K = 12
+    m = orc.SYMMETRIC if mode == "symmetric" else orc.JOINT
+    split = 0 if mode == "build" else n1
+    st, cands = _join_case(orc, X, split, K, m, metric)
+    ids, dists, flags = cuda(torch, st.ids), cuda(torch, st.dists), cuda(torch, st.flags)
+    gc = tuple(cuda(torch, a) for a in cands)
+    ref = st.copy()
+    c_ref, e_ref = orc.join(m, X, split, ref, cands, metric=metric)
+    p = km.params(k=K, metric=metric, precision=precision)
+    c, e = ctx.step_join(m, cuda(torch, X), split, p, ids, dists, flags, gc)
+    assert (c, e) == (c_ref, e_ref)
+    assert_same(host(ids), ref.ids, "ids")
+    assert_same(host(dists), ref.dists, "dists")
+    assert_same(host(flags), ref.flags, "flags")
+
+
+@pytest.mark.parametrize("d", [3, 8, 128, 960, 1030])
+def test_join_parity_dims(torch, km, ctx, orc, d):
+    """Row lengths that are not a multiple of 4 (plain loads), exactly one
+    vector, and rows long enough to be processed in several chunks."""
+    X = datagen.sift_like(900, d, seed=d)
+    K = 8
+    st, cands = _join_case(orc, X, 0, K, orc.JOINT, 0)
+    ids, dists, flags = cuda(torch, st.ids), cuda(torch, st.dists), cuda(torch, st.flags)
+    ref = st.copy()
+    c_ref, e_ref = orc.join(orc.JOINT, X, 0, ref, cands)
+    for precision in (["fp32", "bf16"] if d % 8 == 0 else ["fp32"]):
+        i2, d2, f2 = ids.clone(), dists.clone(), flags.clone()
+        c, e = ctx.step_join(km.JOINT, cuda(torch, X), 0, km.params(k=K, precision=precision),
+                             i2, d2, f2, tuple(cuda(torch, a) for a in cands))
+        assert (c, e) == (c_ref, e_ref), precision
+        assert_same(host(i2), ref.ids, f"ids {precision}")
+        assert_same(host(d2), ref.dists, f"dists {precision}")
+
+
+def test_final_parity(torch, km, ctx, orc):
+    X, n1 = split_data(seed=2)
+    K = 10
+    G1, _ = orc.bruteforce_knn(X[:n1], K)
+    G2, _ = orc.bruteforce_knn(X[n1:], K)
+    st = orc.init(orc.SYMMETRIC, X, n1, K, 5, seed=1, G1=G1, G2=G2)
+    ref_i, ref_d = orc.final(st)
+    oi, od = ctx.step_final(cuda(torch, st.ids), cuda(torch, st.dists), cuda(torch, st.rear_ids),
+                            cuda(torch, st.rear_dists))
+    assert_same(host(oi), ref_i, "ids")
+    assert_same(host(od), ref_d, "dists")
+
+
+# ------------------------------------------------------------------ whole merges
+
+def _smerge_both(torch, km, ctx, orc, X, n1, K, rounds, metric=0, sample_rate=0.5, seed=0,
+                 delta=0.0, precisions=("fp32", "bf16")):
+    G1, _ = orc.bruteforce_knn(X[:n1], K, metric=metric)
+    G2, _ = orc.bruteforce_knn(X[n1:], K, metric=metric)
+    ref_i, ref_d, ref_st = orc.merge_symmetric(X[:n1], G1, X[n1:], G2, K, metric=metric,
+                                               max_iters=rounds, sample_rate=sample_rate,
+                                               seed=seed, delta=delta)
+    for precision in precisions:
+        p = km.params(k=K, metric=metric, precision=precision, max_iters=rounds,
+                      sample_rate=sample_rate, seed=seed, delta=delta)
+        gi, gd, st = ctx.merge_symmetric(cuda(torch, X[:n1]), cuda(torch, G1),
+                                         cuda(torch, X[n1:]), cuda(torch, G2), p)
+        assert st["updates"] == ref_st["updates"], precision
+        assert st["dist_evals"] == ref_st["dist_evals"], precision
+        assert_same(host(gi), ref_i, f"ids {precision}")
+        assert_same(host(gd), ref_d, f"dists {precision}")
+    return ref_i, ref_d, ref_st
+
+
+def test_smerge_config1_parity(torch, km, ctx, orc):
+    """The 2 x 5,000 x 32 Gaussian-mixture S-Merge, k=10, 8 rounds, rho=0.5."""
+    X = datagen.generate("smerge_gmm_10k_d32_k10")
+    _smerge_both(torch, km, ctx, orc, X, 5000, 10, 8)
+
+
+@pytest.mark.parametrize("metric", [1, 2, 3])
+def test_smerge_metrics_parity(torch, km, ctx, orc, metric):
+    X = datagen.gaussian_mixture(1800, 24, n_comp=6, seed=40 + metric,
+                                 normalize=(metric == 2))
+    _smerge_both(torch, km, ctx, orc, X, 1000, 12, 5, metric=metric,
+                 precisions=("fp32",) if metric == 3 else ("fp32", "bf16"))
+
+
+def test_smerge_sift_parity(torch, km, ctx, orc):
+    X = datagen.sift_like(4000, 128, seed=77)
+    _smerge_both(torch, km, ctx, orc, X, 2100, 20, 6, delta=0.001)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_jmerge_parity(torch, km, ctx, orc, precision):
+    X = datagen.gaussian_mixture(3000, 32, n_comp=10, seed=8, normalize=True)
+    n1, K = 2000, 16
+    G1, _ = orc.bruteforce_knn(X[:n1], K, metric=orc.COS)
+    ref_i, ref_d, ref_st = orc.merge_joint(X[:n1], G1, X[n1:], K, metric=orc.COS, max_iters=6)
+    p = km.params(k=K, metric="cos", precision=precision, max_iters=6, delta=0.0)
+    gi, gd, st = ctx.merge_joint(cuda(torch, X[:n1]), cuda(torch, G1), cuda(torch, X[n1:]), p)
+    assert st["updates"] == ref_st["updates"] and st["dist_evals"] == ref_st["dist_evals"]
+    assert_same(host(gi), ref_i, "ids")
+    assert_same(host(gd), ref_d, "dists")
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_build_parity(torch, km, ctx, orc, precision):
+    X = datagen.sift_like(2500, 64, seed=12)
+    ref_i, ref_d, ref_st = orc.build_graph(X, 20, max_iters=5, seed=3)
+    p = km.params(k=20, precision=precision, max_iters=5, seed=3, delta=0.0)
+    gi, gd, st = ctx.build(cuda(torch, X), p)
+    assert st["updates"] == ref_st["updates"]
+    assert_same(host(gi), ref_i, "ids")
+    assert_same(host(gd), ref_d, "dists")
+
+
+def test_host_pointers_match_device(torch, km, ctx, orc):
+    """Host (numpy) inputs and outputs go through the same kernels."""
+    X = datagen.gaussian_mixture(1200, 16, seed=1)
+    n1, K = 600, 8
+    G1, _ = orc.bruteforce_knn(X[:n1], K)
+    G2, _ = orc.bruteforce_knn(X[n1:], K)
+    p = km.params(k=K, max_iters=4, delta=0.0)
+    hi, hd, _ = ctx.merge_symmetric(X[:n1].copy(), G1, X[n1:].copy(), G2, p)
+    gi, gd, _ = ctx.merge_symmetric(cuda(torch, X[:n1]), cuda(torch, G1), cuda(torch, X[n1:]),
+                                    cuda(torch, G2), p)
+    assert isinstance(hi, np.ndarray)
+    assert_same(hi, host(gi), "ids")
+    assert_same(hd, host(gd), "dists")
+
+
+def test_edge_sizes(torch, km, ctx, orc):
+    # the smallest legal build: every list holds all other rows
+    X = datagen.gaussian_mixture(9, 5, seed=3)
+    gi, gd, _ = ctx.build(cuda(torch, X), km.params(k=8, max_iters=2, delta=0.0))
+    ref_i, ref_d = orc.bruteforce_knn(X, 8)
+    assert_same(host(gi), ref_i, "ids")
+    assert_same(host(gd), ref_d, "dists")
+    # k = 1 and k = 32, ragged row counts
+    for K, n in ((1, 37), (32, 333)):
+        X = datagen.gaussian_mixture(n, 6, seed=K)
+        ref_i, ref_d, _ = orc.build_graph(X, K, max_iters=3, seed=2)
+        gi, gd, _ = ctx.build(cuda(torch, X), km.params(k=K, max_iters=3, seed=2, delta=0.0))
+        assert_same(host(gi), ref_i, f"ids k={K}")
+        assert_same(host(gd), ref_d, f"dists k={K}")
+
+
+def test_invalid_inputs_are_rejected(torch, km, ctx, orc):
+    X = datagen.gaussian_mixture(100, 8, seed=1)
+    n1, K = 50, 6
+    G1, _ = orc.bruteforce_knn(X[:n1], K)
+    G2, _ = orc.bruteforce_knn(X[n1:], K)
+    p = km.params(k=K, max_iters=2)
+    bad = []
+    g = G1.copy(); g[3, 2] = 3; bad.append(g)          # self
+    g = G1.copy(); g[4, 1] = g[4, 0]; bad.append(g)    # repeat
+    g = G1.copy(); g[5, 0] = n1; bad.append(g)         # out of range
+    for g in bad:
+        with pytest.raises(km.KnnmError) as ei:
+            ctx.merge_symmetric(cuda(torch, X[:n1]), cuda(torch, g), cuda(torch, X[n1:]),
+                                cuda(torch, G2), p)
+        assert ei.value.code == -1
+    with pytest.raises(km.KnnmError):
+        ctx.merge_symmetric(cuda(torch, X[:5]), cuda(torch, G1[:5]), cuda(torch, X[n1:]),
+                            cuda(torch, G2), p)
+    with pytest.raises(km.KnnmError):
+        ctx.build(cuda(torch, X[:, :7].copy()), km.params(k=K, precision="bf16"))
+    # the context stays usable
+    gi, _, _ = ctx.merge_symmetric(cuda(torch, X[:n1]), cuda(torch, G1), cuda(torch, X[n1:]),
+                                   cuda(torch, G2), p)
+    assert host(gi).shape == (100, K)
