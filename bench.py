@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Benchmark of the k-NN graph merge on GB300.
+
+Workload (one "step"): the symmetric merge (S-Merge, Alg. 1) of two SIFT-like
+sets of 500,000 x 128 float32 vectors (L2, k = 20, rho = 0.5, keep ratio 0.5,
+up to 10 local-join rounds, stop when a round changes <= 0.1% of the entries).
+The input graphs are NN-Descent builds of each half (10 rounds), made once
+before timing.  The whole merge (init + rounds + final merge) is one step.
+
+Reported: points merged per second of the BF16 tensor-core + FP32 re-rank path
+(the headline), the plain FP32 path beside it, recall@10 of the merged graph
+against the exact graph on 1,000 sampled nodes, the roofline of the dominant
+kernel, the end-to-end rate through the C ABI with host buffers, and the CPU
+oracle timed on a bounded sample of the same workload.
+
+Multi-GPU: the merge does not shard; N ranks run N independent replicas of the
+workload (weak scaling) and the value is the sum of their points over the
+slowest rank's time.
+
+``--impl reference`` times the CPU oracle instead (the only reference this
+method has: a plain restatement of the paper's algorithm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1908_00814_gb300 import datagen  # noqa: E402
+
+WORKLOAD = "smerge_sift_1m_d128_k20"
+METRIC = "points merged/sec at recall@10>=0.95 (BF16+rerank vs FP32 plain); serving p50/p99 batch latency"
+UNIT = "points/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+def workload_config(w, precision):
+    return {"workload": WORKLOAD, "merge": "symmetric (Alg. 1)", "n1": w["n"] // 2,
+            "n2": w["n"] - w["n"] // 2, "d": w["d"], "k": w["k"], "metric": w["metric"],
+            "max_rounds": w["rounds"], "sample_rate": w["sample_rate"], "keep_ratio": 0.5,
+            "delta": 0.001, "precision": precision,
+            "inputs": "NN-Descent builds of each half, 10 rounds, made before timing",
+            "l2_flush": "inputs larger than L2 (512 MB vectors + 0.5 GB list state per step)",
+            "parallelism": "replicas"}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append(parts)
+                except ValueError:
+                    pass
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def oracle_sample(w, per_half, seed_off=0):
+    """The same workload cut to `per_half` rows of each half, with input graphs
+    from the oracle's own NN-Descent build (10 rounds)."""
+    import oracle
+    X = datagen.generate(WORKLOAD, n=w["n"])
+    h = w["n"] // 2
+    S1 = np.ascontiguousarray(X[:per_half])
+    S2 = np.ascontiguousarray(X[h:h + per_half])
+    G1, _, _ = oracle.build_graph(S1, w["k"], max_iters=10, delta=0.001, seed=11)
+    G2, _, _ = oracle.build_graph(S2, w["k"], max_iters=10, delta=0.001, seed=12)
+    return S1, G1, S2, G2
+
+
+def time_oracle_merge(w, S1, G1, S2, G2, seed=0):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.merge_symmetric(S1, G1, S2, G2, w["k"], max_iters=w["rounds"],
+                           sample_rate=w["sample_rate"], delta=0.001, seed=seed)
+    return time.perf_counter() - t0
+
+
+def run_reference(args, w):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    per_half = args.reference_rows
+    S1, G1, S2, G2 = oracle_sample(w, per_half)
+    for i in range(args.warmup):
+        time_oracle_merge(w, S1, G1, S2, G2, seed=i)
+    times = [time_oracle_merge(w, S1, G1, S2, G2, seed=i) for i in range(args.steps)]
+    ms = 1000.0 * sum(times) / len(times)
+    value = 2 * per_half / (ms / 1000.0)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": workload_config(w, "fp32 (CPU oracle)"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"S-Merge of {per_half} rows of each half "
+                                       f"({2 * per_half} points) per step, single-threaded"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def exact_recall(torch, X_dev, ids_dev, queries, K=10, chunk=131072, extra=48):
+    """recall@K of the merged lists on `queries` against exact float64 neighbours."""
+    q = torch.as_tensor(queries, device=X_dev.device, dtype=torch.long)
+    Q = X_dev[q]
+    qn = (Q.double() ** 2).sum(1)
+    best_d = None
+    best_i = None
+    n = X_dev.shape[0]
+    for b in range(0, n, chunk):
+        Xb = X_dev[b:b + chunk]
+        D = (qn[:, None] + (Xb.double() ** 2).sum(1)[None, :]
+             - 2.0 * (Q.double() @ Xb.double().T))
+        idx = torch.arange(b, b + Xb.shape[0], device=X_dev.device)
+        D[idx[None, :] == q[:, None]] = float("inf")
+        d2, i2 = torch.topk(D, min(K + extra, D.shape[1]), dim=1, largest=False)
+        i2 = i2 + b
+        if best_d is None:
+            best_d, best_i = d2, i2
+        else:
+            cd = torch.cat([best_d, d2], 1)
+            ci = torch.cat([best_i, i2], 1)
+            best_d, o = torch.topk(cd, K + extra, dim=1, largest=False)
+            best_i = torch.gather(ci, 1, o)
+    # exact float64 distances of the candidates and of the returned ids
+    def direct(ids):
+        return ((X_dev[ids].double() - Q.double()[:, None, :]) ** 2).sum(-1)
+    cd = direct(best_i)
+    kth = torch.sort(cd, dim=1).values[:, K - 1]
+    got = ids_dev[q][:, :K].long()
+    gd = direct(got)
+    hits = (gd <= kth[:, None] * (1 + 1e-9)).sum().item()
+    return hits / (len(queries) * K)
+
+
+def run_ours(args, w):
+    import torch
+    from paper_1908_00814_gb300 import build as kbuild, knnm
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    kbuild.build()
+    ctx = knnm.Context(local)
+    peaks, peaks_kind = load_peaks()
+
+    X = datagen.generate(WORKLOAD, n=w["n"])
+    n1 = w["n"] // 2
+    K, d = w["k"], w["d"]
+    Xd = torch.from_numpy(X).cuda()
+    S1, S2 = Xd[:n1].contiguous(), Xd[n1:].contiguous()
+    bp = knnm.params(k=K, precision="bf16", max_iters=10, sample_rate=w["sample_rate"],
+                     delta=0.001, seed=11)
+    G1, _, _ = ctx.build(S1, bp)
+    bp.seed = 12
+    G2, _, _ = ctx.build(S2, bp)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def timed(precision, steps, warmup):
+        p = knnm.params(k=K, precision=precision, max_iters=w["rounds"],
+                        sample_rate=w["sample_rate"], delta=0.001, seed=rank)
+        for _ in range(warmup):
+            ctx.merge_symmetric(S1, G1, S2, G2, p)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sampler = ClockSampler(local)
+        sampler.start()
+        e0.record(stream)
+        stats = []
+        out = None
+        for _ in range(steps):
+            out = ctx.merge_symmetric(S1, G1, S2, G2, p)
+            stats.append(out[2])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        ms = e0.elapsed_time(e1) / steps
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, stats, out, clocks
+
+    ms_bf, st_bf, out_bf, clocks = timed("bf16", args.steps, args.warmup)
+    res = {"ms_bf16": ms_bf}
+    if not args.no_fp32:
+        ms_fp, st_fp, out_fp, clocks_fp = timed("fp32", args.steps, args.warmup)
+        same = bool(torch.equal(out_fp[0], out_bf[0]) and torch.equal(
+            out_fp[1].view(torch.int32), out_bf[1].view(torch.int32)))
+    # recall@10 on sampled nodes (not timed)
+    queries = datagen.sample_nodes(w["n"], args.recall_queries, seed=0)
+    recall = exact_recall(torch, Xd, out_bf[0], queries, K=10)
+
+    # roofline of the dominant kernel (per-round device times from the library's events)
+    tot = {"sample": 0.0, "join": 0.0, "update": 0.0}
+    bytes_join = 0.0
+    launches_join = 0
+    launches = 0
+    for st in st_bf:
+        launches += st["kernel_launches"]
+        tot["sample"] += sum(st["ms_sample"])
+        tot["join"] += sum(st["ms_join"])
+        tot["update"] += sum(st["ms_update"])
+        launches_join += st["rounds"]
+        for r in range(st["rounds"]):
+            # per staged row: the BF16 row, its id, k-th key and error data;
+            # per re-ranked pair: both FP32 rows; per proposal: target + key;
+            # per node: the two list lengths
+            bytes_join += (st["gathered"][r] * (d * 2 + 4 + 8 + 16)
+                           + st["reranked"][r] * 2 * d * 4
+                           + st["proposals"][r] * 12 + w["n"] * 8)
+    dominant = max(tot, key=tot.get)
+    achieved = bytes_join / (tot["join"] / 1000.0) / 1e9 if tot["join"] > 0 else 0.0
+    hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    roofline = {"kernel": "k_join_bf16 (distance block)", "bound": "hbm", "achieved": achieved,
+                "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "peak_source": f"hbm_gbs of {peaks_kind}", "traffic": None,
+                "time_share": {k: v / sum(tot.values()) for k, v in tot.items()},
+                "dominant_phase": dominant, "launches": launches_join,
+                "algorithmic_bytes_per_launch": bytes_join / max(launches_join, 1)}
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hS1 = S1.cpu().pin_memory()
+        hS2 = S2.cpu().pin_memory()
+        hG1 = G1.cpu().pin_memory()
+        hG2 = G2.cpu().pin_memory()
+        p = knnm.params(k=K, precision="bf16", max_iters=w["rounds"],
+                        sample_rate=w["sample_rate"], delta=0.001, seed=rank)
+        ctx.merge_symmetric(hS1, hG1, hS2, hG2, p)
+        ts = []
+        for _ in range(max(1, min(args.steps, 3))):
+            barrier()
+            t0 = time.perf_counter()
+            ids, dists, _ = ctx.merge_symmetric(hS1, hG1, hS2, hG2, p)
+            ts.append(time.perf_counter() - t0)
+        h2d = (hS1.numel() + hS2.numel()) * 4 + (hG1.numel() + hG2.numel()) * 4
+        d2h = ids.numel() * 4 + dists.numel() * 4
+        e2e = {"value": world * w["n"] / statistics.mean(ts), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "note": "knnm_merge_symmetric with pinned host inputs/outputs; copies inside"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        per_half = args.cpu_rows
+        S1h, G1h, S2h, G2h = oracle_sample(w, per_half)
+        t = time_oracle_merge(w, S1h, G1h, S2h, G2h)
+        cpu = {"value": 2 * per_half / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"S-Merge of the first {per_half} rows of each half "
+                         f"({2 * per_half} points), inputs from the oracle's own NN-Descent "
+                         f"build, single-threaded, {t:.1f} s"}
+
+    value = world * w["n"] / (ms_bf / 1000.0)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_bf,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16+f32", "data": "synthetic", "config": workload_config(w, "bf16_rerank"),
+            "recall_at_10": recall, "recall_queries": len(queries),
+            "rounds": st_bf[-1]["rounds"], "updates_per_round": st_bf[-1]["updates"],
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": launches}
+    if not args.no_fp32:
+        line["fp32_plain"] = {"value": world * w["n"] / (ms_fp / 1000.0), "ms_per_step": ms_fp,
+                              "dtype": "f32", "identical_graph_to_bf16": same,
+                              "ms_join_per_step": sum(sum(s["ms_join"]) for s in st_fp) / len(st_fp),
+                              "clocks": clocks_fp}
+        line["bf16_speedup_over_fp32"] = ms_fp / ms_bf
+    line["phase_ms_per_step"] = {k: v / len(st_bf) for k, v in tot.items()}
+    line["ms_init"] = st_bf[-1]["ms_init"]
+    line["ms_final"] = st_bf[-1]["ms_final"]
+    line["valid"] = recall >= 0.95
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--recall-queries", type=int, default=1000)
+    ap.add_argument("--cpu-rows", type=int, default=20000)
+    ap.add_argument("--reference-rows", type=int, default=5000)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps")
+    w = datagen.WORKLOADS[WORKLOAD]
+    if args.impl == "reference":
+        return run_reference(args, w)
+    return run_ours(args, w)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

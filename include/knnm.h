@@ -78,10 +78,15 @@ typedef struct {
 
 typedef struct {
   int rounds;                             /* rounds run */
+  int kernel_launches;                    /* kernels the call launched */
   int64_t updates[KNNM_MAX_ROUNDS];       /* c_t: entries new to the lists after round t */
   int64_t dist_evals[KNNM_MAX_ROUNDS];    /* pairs compared in round t (scanning rate C) */
   int64_t proposals[KNNM_MAX_ROUNDS];     /* edges offered to UpdateNN after the k-th filter */
   int64_t reranked[KNNM_MAX_ROUNDS];      /* BF16 path: pairs re-computed in FP32 */
+  int64_t gathered[KNNM_MAX_ROUNDS];      /* candidate rows staged by the join (sum of |new|+|old|) */
+  float ms_sample[KNNM_MAX_ROUNDS];       /* device time of the sampler kernels in round t */
+  float ms_join[KNNM_MAX_ROUNDS];         /* device time of the join kernel in round t */
+  float ms_update[KNNM_MAX_ROUNDS];       /* device time of the top-k insert + flag pass */
   float ms_init, ms_rounds, ms_final;     /* device time of init, all rounds, final merge */
   float ms_total;                         /* wall time of the call */
 } knnm_stats;

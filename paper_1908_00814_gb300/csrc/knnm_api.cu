@@ -19,6 +19,7 @@ struct knnm_ctx {
   size_t arena_bytes = 0;
   DevCounters* host_ctr = nullptr;  // pinned
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t rev[4] = {nullptr, nullptr, nullptr, nullptr};  // per-round phases
   char err[512] = {0};
 };
 
@@ -277,11 +278,18 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   const bool use_bulk =
       d % 4 == 0 && aligned16(rows.X1) && aligned16(rows.X2) && (nx1 == N || aligned16(rows.X2));
 
+  int launches = 1;
   KNNM_CUDA(cudaEventRecord(ctx->ev[0], st));
   KNNM_CUDA(cudaMemsetAsync(P.ctr, 0, sizeof(DevCounters), st));
   KNNM_CUDA(cudaMemsetAsync(&P.ctr->err_row, 0xFF, 8, st));
-  if (P.norms) KNNM_CUDA(launch_norms(rows, N, P.norms, st));
-  if (P.Xb) KNNM_CUDA(launch_bf16_prep(rows, N, P.Xb, P.aux, st));
+  if (P.norms) {
+    KNNM_CUDA(launch_norms(rows, N, P.norms, st));
+    ++launches;
+  }
+  if (P.Xb) {
+    KNNM_CUDA(launch_bf16_prep(rows, N, P.Xb, P.aux, st));
+    ++launches;
+  }
 
   InitArgs ia;
   ia.mode = in.mode;
@@ -361,10 +369,15 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     KNNM_CUDA(cudaMemsetAsync(P.rev_new, 0xFF, (size_t)N * D.s * 8, st));
     KNNM_CUDA(cudaMemsetAsync(P.rev_old, 0xFF, (size_t)N * D.s * 8, st));
     sa.t = t;
+    KNNM_CUDA(cudaEventRecord(ctx->rev[0], st));
     KNNM_CUDA(launch_sample(sa, st));
+    KNNM_CUDA(cudaEventRecord(ctx->rev[1], st));
     KNNM_CUDA(launch_join(precision, ja, plan, st));
+    KNNM_CUDA(cudaEventRecord(ctx->rev[2], st));
     KNNM_CUDA(launch_update_regions(ua, P.region_cnt, region_cap, plan.grid, st));
     KNNM_CUDA(launch_finalize(fa, st));
+    KNNM_CUDA(cudaEventRecord(ctx->rev[3], st));
+    launches += 5;
     KNNM_CUDA(cudaMemcpyAsync(ctx->host_ctr, P.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
     KNNM_CUDA(cudaStreamSynchronize(st));
     const DevCounters& h = *ctx->host_ctr;
@@ -375,6 +388,10 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     local.dist_evals[t - 1] = (int64_t)h.dist_evals;
     local.proposals[t - 1] = (int64_t)h.proposals;
     local.reranked[t - 1] = (int64_t)h.reranked;
+    local.gathered[t - 1] = (int64_t)h.gathered;
+    cudaEventElapsedTime(&local.ms_sample[t - 1], ctx->rev[0], ctx->rev[1]);
+    cudaEventElapsedTime(&local.ms_join[t - 1], ctx->rev[1], ctx->rev[2]);
+    cudaEventElapsedTime(&local.ms_update[t - 1], ctx->rev[2], ctx->rev[3]);
     local.rounds = t;
     if ((double)h.updates <= stop_at) break;
   }
@@ -382,6 +399,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   int32_t* oi = P.oi ? P.oi : out_ids;
   float* od = P.od ? P.od : out_dists;
   KNNM_CUDA(launch_final(N, K, P.keys, D.Kr, P.rear, oi, od, st));
+  ++launches;
   KNNM_CUDA(cudaEventRecord(ctx->ev[3], st));
   if (P.oi)
     KNNM_CUDA(cudaMemcpyAsync(out_ids, P.oi, (size_t)N * K * 4, cudaMemcpyDeviceToHost, st));
@@ -396,6 +414,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     local.ms_rounds = ms;
     cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
     local.ms_final = ms;
+    local.kernel_launches = launches;
     local.ms_total = (float)std::chrono::duration<double, std::milli>(
                          std::chrono::steady_clock::now() - t_wall0)
                          .count();
@@ -432,6 +451,11 @@ extern "C" int knnm_create(knnm_ctx** out, int device, void* cuda_stream) {
       knnm_destroy(c);
       return KNNM_ERR_CUDA;
     }
+  for (auto& e : c->rev)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      knnm_destroy(c);
+      return KNNM_ERR_CUDA;
+    }
   *out = c;
   return KNNM_OK;
 }
@@ -443,6 +467,8 @@ extern "C" int knnm_destroy(knnm_ctx* c) {
   if (c->arena) cudaFree(c->arena);
   if (c->host_ctr) cudaFreeHost(c->host_ctr);
   for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : c->rev)
     if (e) cudaEventDestroy(e);
   delete c;
   return KNNM_OK;

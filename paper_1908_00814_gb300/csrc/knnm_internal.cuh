@@ -291,7 +291,7 @@ struct DevCounters {
   unsigned long long reranked;    // BF16 path: FP32 recomputations
   unsigned long long err;         // DevErr bits
   unsigned long long err_row;     // smallest offending row
-  unsigned long long pad;
+  unsigned long long gathered;    // candidate rows staged by the join
 };
 
 struct InitArgs {

@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(JT) k_join_fp32(JoinArgs a, int chunk, int pai
   }
   __syncthreads();
   uint32_t phase = 0;
-  unsigned long long evals = 0;
+  unsigned long long evals = 0, gathered = 0;
   const bool bulk = a.use_bulk != 0;
 
   for (int64_t u = blockIdx.x; u < a.N; u += gridDim.x) {
@@ -224,6 +224,7 @@ __global__ void __launch_bounds__(JT) k_join_fp32(JoinArgs a, int chunk, int pai
     __syncthreads();
     const int np = build_pairs(a, nn, M, S);
     evals += (threadIdx.x == 0) ? (unsigned long long)np : 0ull;
+    gathered += (threadIdx.x == 0 && np > 0) ? (unsigned long long)M : 0ull;
     for (int c0 = 0; c0 < d; c0 += chunk) {
       const int cw = min(chunk, d - c0);
       if (np > 0) {
@@ -282,6 +283,7 @@ __global__ void __launch_bounds__(JT) k_join_fp32(JoinArgs a, int chunk, int pai
     if ((uint64_t)fill > a.region_cap)
       atomicAdd(&a.ctr->overflow, (unsigned long long)((uint64_t)fill - a.region_cap));
     atomicAdd(&a.ctr->dist_evals, evals);
+    atomicAdd(&a.ctr->gathered, gathered);
   }
 }
 
@@ -388,7 +390,7 @@ __global__ void __launch_bounds__(JT) k_join_bf16(JoinArgs a, int pair_cap) {
   for (int idx = threadIdx.x; idx < TC_ROWS * bstride / 4; idx += JT) ((uint32_t*)srows)[idx] = 0u;
   __syncthreads();
   uint32_t phase = 0;
-  unsigned long long evals = 0, reranked = 0;
+  unsigned long long evals = 0, reranked = 0, gathered = 0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   for (int64_t u = blockIdx.x; u < a.N; u += gridDim.x) {
@@ -398,6 +400,7 @@ __global__ void __launch_bounds__(JT) k_join_bf16(JoinArgs a, int pair_cap) {
     for (int r = threadIdx.x; r < M; r += JT) saux[r] = a.aux[S.cid[r]];
     __syncthreads();
     if (nn > 0 && M > 1) {
+      gathered += (threadIdx.x == 0) ? (unsigned long long)M : 0ull;
       stage_rows<__nv_bfloat16>(a, S, M, Bf16Row{a.Xb, d}, 0, d, srows, bstride, phase);
       __syncthreads();
       // Gram tile: warp w takes m-tile (w & 1) (rows 16*(w&1) ..) and n-tiles
@@ -493,6 +496,7 @@ __global__ void __launch_bounds__(JT) k_join_bf16(JoinArgs a, int pair_cap) {
       atomicAdd(&a.ctr->overflow, (unsigned long long)((uint64_t)fill - a.region_cap));
     atomicAdd(&a.ctr->dist_evals, tot);
     atomicAdd(&a.ctr->reranked, reranked);
+    atomicAdd(&a.ctr->gathered, gathered);
   }
 }
 

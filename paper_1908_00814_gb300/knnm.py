@@ -34,21 +34,26 @@ class Params(ctypes.Structure):
 
 
 class Stats(ctypes.Structure):
-    _fields_ = [("rounds", ctypes.c_int),
+    _fields_ = [("rounds", ctypes.c_int), ("kernel_launches", ctypes.c_int),
                 ("updates", ctypes.c_int64 * MAX_ROUNDS),
                 ("dist_evals", ctypes.c_int64 * MAX_ROUNDS),
                 ("proposals", ctypes.c_int64 * MAX_ROUNDS),
                 ("reranked", ctypes.c_int64 * MAX_ROUNDS),
+                ("gathered", ctypes.c_int64 * MAX_ROUNDS),
+                ("ms_sample", ctypes.c_float * MAX_ROUNDS),
+                ("ms_join", ctypes.c_float * MAX_ROUNDS),
+                ("ms_update", ctypes.c_float * MAX_ROUNDS),
                 ("ms_init", ctypes.c_float), ("ms_rounds", ctypes.c_float),
                 ("ms_final", ctypes.c_float), ("ms_total", ctypes.c_float)]
 
     def as_dict(self):
         r = self.rounds
-        return {"rounds": r, "updates": list(self.updates[:r]),
-                "dist_evals": list(self.dist_evals[:r]), "proposals": list(self.proposals[:r]),
-                "reranked": list(self.reranked[:r]), "ms_init": self.ms_init,
-                "ms_rounds": self.ms_rounds, "ms_final": self.ms_final,
-                "ms_total": self.ms_total}
+        out = {"rounds": r, "kernel_launches": self.kernel_launches, "ms_init": self.ms_init,
+               "ms_rounds": self.ms_rounds, "ms_final": self.ms_final, "ms_total": self.ms_total}
+        for name in ("updates", "dist_evals", "proposals", "reranked", "gathered", "ms_sample",
+                     "ms_join", "ms_update"):
+            out[name] = list(getattr(self, name)[:r])
+        return out
 
 
 _lib = None
