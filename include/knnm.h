@@ -156,6 +156,35 @@ int knnm_step_sample(knnm_ctx* ctx, int64_t N, int K, const int32_t* ids, const 
                      uint8_t* flags, uint64_t seed, int t, int s, int cap_new, int cap_old,
                      int32_t* new_ids, int32_t* new_cnt, int32_t* old_ids, int32_t* old_cnt);
 
+/* Size of the fixed scratch array used by knnm_step_sample_noalloc. */
+#define KNNM_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/* knnm_step_sample without any device allocation.  The paper has no
+ * counterpart to this call; it exists for callers of this library that must
+ * not allocate device memory: plug-ins whose host application owns the whole
+ * device-memory budget, and serving processes that reserve all their memory at
+ * start-up because cudaMalloc/cudaFree may synchronize the device and stall
+ * the other streams' work on the request path.
+ *
+ * Same arguments, outputs and results as knnm_step_sample (device pointers),
+ * except that it takes the CUDA stream directly instead of a context and runs
+ * on the calling thread's current device.  Its scratch (packed list keys and
+ * the two reverse-sample slot arrays) is one fixed __device__ array of
+ * KNNM_NOALLOC_SCRATCH_BYTES inside the library, held by every GPU that loads
+ * the library until the process exits.  Limit: N*(K + 2*s)*8 + 256 bytes must
+ * fit in it (with K = 20, s = 10 that is about 26,000 rows); larger inputs
+ * return KNNM_ERR_INVALID before anything is launched.  The call allocates
+ * nothing, neither device nor host memory.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture starts.  Every call shares the one array: it
+ * resets what must start empty, but calls whose work overlaps on the GPU (other
+ * threads, other streams) race on it and must be serialized by the caller.
+ * Returns after the stream has finished the call's work. */
+int knnm_step_sample_noalloc(void* cuda_stream, int64_t N, int K, const int32_t* ids,
+                             const float* dists, uint8_t* flags, uint64_t seed, int t, int s,
+                             int cap_new, int cap_old, int32_t* new_ids, int32_t* new_cnt,
+                             int32_t* old_ids, int32_t* old_cnt);
+
 /* Local join and UpdateNN of one round (Alg. 1 / Alg. 2 inner loops) on the
  * given candidate sets: updates ids/dists/flags in place, writes c_t to
  * *updates and the pair count to *dist_evals.  Counts must not exceed

@@ -80,6 +80,8 @@ SIGNATURES = {
                             _P, _I, _I, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int64),
                             ctypes.POINTER(ctypes.c_int64)]),
     "knnm_step_final": (_I, [_P, _I64, _I, _P, _P, _I, _P, _P, _P, _P]),
+    "knnm_step_sample_noalloc": (_I, [_P, _I64, _I, _P, _P, _P, _U64, _I, _I, _I, _I, _P, _P,
+                                      _P, _P]),
 }
 
 
@@ -282,3 +284,19 @@ class Context:
                                           _ptr(rear_dists) if Kr else None, _ptr(out_i),
                                           _ptr(out_d)))
         return out_i, out_d
+
+
+def step_sample_noalloc(ids, dists, flags, seed, t, s, new_ids, new_cnt, old_ids, old_cnt,
+                        stream=None) -> int:
+    """knnm_step_sample_noalloc: the sampler with the library's fixed scratch
+    instead of allocated scratch, for callers that must not allocate device
+    memory.  All arrays are caller-owned CUDA tensors (outputs included, so
+    the call itself allocates nothing); returns the library's status code."""
+    import torch
+    N, K = ids.shape
+    if stream is None:
+        stream = torch.cuda.current_stream(ids.device).cuda_stream
+    return lib().knnm_step_sample_noalloc(ctypes.c_void_p(stream), N, K, _ptr(ids), _ptr(dists),
+                                          _ptr(flags), seed, t, s, new_ids.shape[1],
+                                          old_ids.shape[1], _ptr(new_ids), _ptr(new_cnt),
+                                          _ptr(old_ids), _ptr(old_cnt))
