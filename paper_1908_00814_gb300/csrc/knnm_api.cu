@@ -117,11 +117,34 @@ int derive(knnm_ctx* ctx, const knnm_params* p, int mode, int64_t n1, Derived* o
   return KNNM_OK;
 }
 
-// Copies a host array to freshly carved device scratch when needed.
-struct Staged {
-  const void* dev = nullptr;
-  bool copied = false;
+// The join kernel a merge uses: the pipelined one when the shapes fit it,
+// else the single-stage one (long rows, large candidate sets, unaligned rows).
+struct JoinPath {
+  bool pipe = false;
+  JoinPlan plan;
+  PipeArgs pa;
+  size_t smem = 0;
+  int grid = 0;
+  int regions() const { return pipe ? grid : plan.grid; }
 };
+
+int choose_join(knnm_ctx* ctx, int precision, int metric, int cap_new, int cap_old, int d,
+                bool rows_aligned, JoinPath* jp) {
+  const bool tc = precision == KNNM_BF16_RERANK && metric != KNNM_L1;
+  if (tc || rows_aligned) {
+    if (plan_pipe(precision, metric, cap_new, cap_old, d, &jp->pa, &jp->smem, &jp->grid) ==
+        cudaSuccess) {
+      jp->pipe = true;
+      return KNNM_OK;
+    }
+    cudaGetLastError();
+  }
+  cudaError_t e = plan_join(precision, metric, cap_new, cap_old, d, &jp->plan);
+  if (e != cudaSuccess)
+    return fail(ctx, KNNM_ERR_INVALID, "no join configuration for cap %d+%d, d=%d: %s", cap_new,
+                cap_old, d, cudaGetErrorString(e));
+  return KNNM_OK;
+}
 
 }  // namespace
 
@@ -188,15 +211,17 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   const bool oi_dev = is_device_ptr(out_ids);
   const bool od_dev = is_device_ptr(out_dists);
 
-  JoinPlan plan;
-  {
-    cudaError_t e = plan_join(precision, params->metric, D.cap_new, D.cap_old, d, &plan);
-    if (e != cudaSuccess)
-      return fail(ctx, KNNM_ERR_INVALID, "no join configuration for k=%d, s=%d, d=%d: %s", K,
-                  D.s, d, cudaGetErrorString(e));
-  }
-  const uint64_t per_node = 384;
-  uint64_t region_cap = ((uint64_t)N * per_node + plan.grid - 1) / plan.grid;
+  // rows staged from the caller's device arrays need 16-byte alignment for bulk copies
+  const bool rows_aligned = d % 4 == 0 && (!s1_dev || !s2_dev ||
+                                           ((in.n1 == 0 || aligned16(in.S1)) &&
+                                            (in.n2 == 0 || aligned16(in.S2))));
+  JoinPath jp;
+  rc = choose_join(ctx, precision, params->metric, D.cap_new, D.cap_old, d, rows_aligned, &jp);
+  if (rc) return rc;
+  const int regions = jp.regions();
+  const bool tc = precision == KNNM_BF16_RERANK;
+  const uint64_t per_node = 256;
+  uint64_t region_cap = ((uint64_t)N * per_node + regions - 1) / regions;
   if (region_cap < 1024) region_cap = 1024;
 
   // Carve the scratch (two passes: size, then pointers).
@@ -210,8 +235,14 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     float* norms;
     __nv_bfloat16* Xb;
     float4* aux;
+    float* rmax;
+    __nv_bfloat16* Xe;
+    unsigned char* rec;
     unsigned long long* region_cnt;
     DevCounters* ctr;
+    int32_t* pcnt;
+    unsigned long long *offs, *tile_sum, *total;
+    uint64_t* bucket;
   } P;
   auto carve = [&](Carver& c) {
     P.X = (!s1_dev || !s2_dev) ? c.take<float>((size_t)N * d) : nullptr;
@@ -230,12 +261,20 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     P.old_ids = c.take<int32_t>((size_t)N * D.cap_old);
     P.old_cnt = c.take<int32_t>((size_t)N);
     P.norms = params->metric == KNNM_COS ? c.take<float>((size_t)N) : nullptr;
-    P.Xb = precision == KNNM_BF16_RERANK ? c.take<__nv_bfloat16>((size_t)N * d) : nullptr;
-    P.aux = precision == KNNM_BF16_RERANK ? c.take<float4>((size_t)N) : nullptr;
-    P.prop_tgt = c.take<int32_t>(region_cap * plan.grid);
-    P.prop_key = c.take<uint64_t>(region_cap * plan.grid);
-    P.region_cnt = c.take<unsigned long long>((size_t)plan.grid);
+    P.Xb = tc && !jp.pipe ? c.take<__nv_bfloat16>((size_t)N * d) : nullptr;
+    P.aux = tc && !jp.pipe ? c.take<float4>((size_t)N) : nullptr;
+    P.rmax = tc && !jp.pipe ? c.take<float>((size_t)N) : nullptr;
+    P.Xe = tc && jp.pipe ? c.take<__nv_bfloat16>((size_t)N * jp.pa.dx) : nullptr;
+    P.rec = jp.pipe ? c.take<unsigned char>((size_t)N * rec_bytes(jp.pa.cap)) : nullptr;
+    P.prop_tgt = c.take<int32_t>(region_cap * regions);
+    P.prop_key = c.take<uint64_t>(region_cap * regions);
+    P.region_cnt = c.take<unsigned long long>((size_t)regions);
     P.ctr = c.take<DevCounters>(1);
+    P.pcnt = c.take<int32_t>((size_t)N);
+    P.offs = c.take<unsigned long long>((size_t)N + 1);
+    P.tile_sum = c.take<unsigned long long>((size_t)(N + 1023) / 1024 + 1);
+    P.total = c.take<unsigned long long>(1);
+    P.bucket = c.take<uint64_t>(region_cap * regions);
   };
   Carver sizer;
   carve(sizer);
@@ -287,7 +326,11 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     ++launches;
   }
   if (P.Xb) {
-    KNNM_CUDA(launch_bf16_prep(rows, N, P.Xb, P.aux, st));
+    KNNM_CUDA(launch_bf16_prep(rows, N, P.Xb, P.aux, P.rmax, st));
+    ++launches;
+  }
+  if (P.Xe) {
+    KNNM_CUDA(launch_bf16_ext(rows, N, jp.pa.dx, P.Xe, st));
     ++launches;
   }
 
@@ -335,6 +378,14 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   sa.old_ids = P.old_ids;
   sa.old_cnt = P.old_cnt;
   sa.ctr = P.ctr;
+  if (jp.pipe) {
+    sa.rec = P.rec;
+    sa.rec_cap = jp.pa.cap;
+    sa.norms = P.norms;
+    sa.K_list = K;
+    jp.pa.rec = P.rec;
+    jp.pa.Xe = P.Xe;
+  }
   JoinArgs ja;
   ja.mode = in.mode;
   ja.rows = rows;
@@ -355,12 +406,14 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   ja.region_cap = region_cap;
   ja.region_cnt = P.region_cnt;
   ja.live_keys = P.keys;
+  ja.prop_cnt = P.pcnt;
   ja.ctr = P.ctr;
   ja.Xb = P.Xb;
   ja.aux = P.aux;
+  ja.rmax = P.rmax;
   ja.use_bulk = use_bulk ? 1 : 0;
-  UpdateArgs ua{P.prop_tgt, P.prop_key, P.keys, K};
-  FinalizeArgs fa{N, K, P.keys, P.prev, P.flags, P.ctr};
+  MergeArgs ma{N, K, P.keys, P.prev, P.flags, P.pcnt, P.offs, P.bucket, P.ctr};
+  KNNM_CUDA(cudaMemsetAsync(P.pcnt, 0, (size_t)N * 4, st));
 
   const double stop_at = (double)params->delta * (double)N * (double)K;
   for (int t = 1; t <= params->max_iters; ++t) {
@@ -372,12 +425,15 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     KNNM_CUDA(cudaEventRecord(ctx->rev[0], st));
     KNNM_CUDA(launch_sample(sa, st));
     KNNM_CUDA(cudaEventRecord(ctx->rev[1], st));
-    KNNM_CUDA(launch_join(precision, ja, plan, st));
+    if (jp.pipe)
+      KNNM_CUDA(launch_pipe(precision, ja, jp.pa, jp.smem, jp.grid, st));
+    else
+      KNNM_CUDA(launch_join(precision, ja, jp.plan, st));
     KNNM_CUDA(cudaEventRecord(ctx->rev[2], st));
-    KNNM_CUDA(launch_update_regions(ua, P.region_cnt, region_cap, plan.grid, st));
-    KNNM_CUDA(launch_finalize(fa, st));
+    KNNM_CUDA(launch_bucket_update(ma, P.prop_tgt, P.prop_key, P.region_cnt, region_cap,
+                                   regions, P.tile_sum, P.total, st));
     KNNM_CUDA(cudaEventRecord(ctx->rev[3], st));
-    launches += 5;
+    launches += 8;
     KNNM_CUDA(cudaMemcpyAsync(ctx->host_ctr, P.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
     KNNM_CUDA(cudaStreamSynchronize(st));
     const DevCounters& h = *ctx->host_ctr;
@@ -695,31 +751,44 @@ extern "C" int knnm_step_join(knnm_ctx* ctx, int mode, const float* X1, int64_t 
     return fail(ctx, KNNM_ERR_INVALID, "the BF16 path needs d %% 8 == 0");
   cudaStream_t st = ctx->stream;
   KNNM_CUDA(cudaSetDevice(ctx->device));
-  JoinPlan plan;
-  {
-    cudaError_t e = plan_join(precision, params->metric, cap_new, cap_old, d, &plan);
-    if (e != cudaSuccess)
-      return fail(ctx, KNNM_ERR_INVALID, "no join configuration: %s", cudaGetErrorString(e));
-  }
-  uint64_t region_cap = ((uint64_t)N * 2 * cap_new * (cap_new + cap_old) + plan.grid - 1) / plan.grid;
+  JoinPath jp;
+  rc = choose_join(ctx, precision, params->metric, cap_new, cap_old, d,
+                   d % 4 == 0 && aligned16(X1) && aligned16(X2 ? X2 : X1), &jp);
+  if (rc) return rc;
+  const int regions = jp.regions();
+  const bool tc = precision == KNNM_BF16_RERANK;
+  uint64_t per_node = (uint64_t)2 * cap_new * (cap_new + cap_old);
+  if (per_node > 512) per_node = 512;
+  uint64_t region_cap = ((uint64_t)N * per_node + regions - 1) / regions;
   if (region_cap < 256) region_cap = 256;
-  uint64_t *keys, *prev, *pkey;
-  int32_t* ptgt;
-  unsigned long long* rcnt;
+  uint64_t *keys, *prev, *pkey, *bucket;
+  int32_t *ptgt, *pcnt;
+  unsigned long long *rcnt, *offs, *tsum, *total;
   float* norms;
   __nv_bfloat16* Xb;
   float4* aux;
+  float* rmax;
+  __nv_bfloat16* Xe;
+  unsigned char* rec;
   DevCounters* ctr;
   auto carve = [&](Carver& c) {
     keys = c.take<uint64_t>((size_t)N * K);
     prev = c.take<uint64_t>((size_t)N * K);
-    ptgt = c.take<int32_t>(region_cap * plan.grid);
-    pkey = c.take<uint64_t>(region_cap * plan.grid);
-    rcnt = c.take<unsigned long long>((size_t)plan.grid);
+    ptgt = c.take<int32_t>(region_cap * regions);
+    pkey = c.take<uint64_t>(region_cap * regions);
+    rcnt = c.take<unsigned long long>((size_t)regions);
     norms = c.take<float>((size_t)N);
-    Xb = precision == KNNM_BF16_RERANK ? c.take<__nv_bfloat16>((size_t)N * d) : nullptr;
-    aux = precision == KNNM_BF16_RERANK ? c.take<float4>((size_t)N) : nullptr;
+    Xb = tc && !jp.pipe ? c.take<__nv_bfloat16>((size_t)N * d) : nullptr;
+    aux = tc && !jp.pipe ? c.take<float4>((size_t)N) : nullptr;
+    rmax = tc && !jp.pipe ? c.take<float>((size_t)N) : nullptr;
     ctr = c.take<DevCounters>(1);
+    pcnt = c.take<int32_t>((size_t)N);
+    offs = c.take<unsigned long long>((size_t)N + 1);
+    tsum = c.take<unsigned long long>((size_t)(N + 1023) / 1024 + 1);
+    total = c.take<unsigned long long>(1);
+    bucket = c.take<uint64_t>(region_cap * regions);
+    Xe = tc && jp.pipe ? c.take<__nv_bfloat16>((size_t)N * jp.pa.dx) : nullptr;
+    rec = jp.pipe ? c.take<unsigned char>((size_t)N * rec_bytes(jp.pa.cap)) : nullptr;
   };
   Carver c0;
   carve(c0);
@@ -734,7 +803,8 @@ extern "C" int knnm_step_join(knnm_ctx* ctx, int mode, const float* X1, int64_t 
   KNNM_CUDA(launch_pack((int64_t)N * K, ids, dists, keys, st));
   KNNM_CUDA(cudaMemcpyAsync(prev, keys, (size_t)N * K * 8, cudaMemcpyDeviceToDevice, st));
   if (params->metric == KNNM_COS) KNNM_CUDA(launch_norms(rows, N, norms, st));
-  if (Xb) KNNM_CUDA(launch_bf16_prep(rows, N, Xb, aux, st));
+  if (Xb) KNNM_CUDA(launch_bf16_prep(rows, N, Xb, aux, rmax, st));
+  if (Xe) KNNM_CUDA(launch_bf16_ext(rows, N, jp.pa.dx, Xe, st));
   JoinArgs ja;
   ja.mode = mode;
   ja.rows = rows;
@@ -755,15 +825,25 @@ extern "C" int knnm_step_join(knnm_ctx* ctx, int mode, const float* X1, int64_t 
   ja.region_cap = region_cap;
   ja.region_cnt = rcnt;
   ja.live_keys = keys;
+  ja.prop_cnt = pcnt;
   ja.ctr = ctr;
   ja.Xb = Xb;
   ja.aux = aux;
+  ja.rmax = rmax;
   ja.use_bulk = (d % 4 == 0 && aligned16(rows.X1) && aligned16(rows.X2)) ? 1 : 0;
-  KNNM_CUDA(launch_join(precision, ja, plan, st));
-  UpdateArgs ua{ptgt, pkey, keys, K};
-  KNNM_CUDA(launch_update_regions(ua, rcnt, region_cap, plan.grid, st));
-  FinalizeArgs fa{N, K, keys, prev, flags, ctr};
-  KNNM_CUDA(launch_finalize(fa, st));
+  KNNM_CUDA(cudaMemsetAsync(pcnt, 0, (size_t)N * 4, st));
+  if (jp.pipe) {
+    KNNM_CUDA(launch_build_records(N, K, keys, params->metric == KNNM_COS ? norms : nullptr,
+                                   cap_new, cap_old, new_ids, new_cnt, old_ids, old_cnt, rec,
+                                   jp.pa.cap, st));
+    jp.pa.rec = rec;
+    jp.pa.Xe = Xe;
+    KNNM_CUDA(launch_pipe(precision, ja, jp.pa, jp.smem, jp.grid, st));
+  } else {
+    KNNM_CUDA(launch_join(precision, ja, jp.plan, st));
+  }
+  MergeArgs ma{N, K, keys, prev, flags, pcnt, offs, bucket, ctr};
+  KNNM_CUDA(launch_bucket_update(ma, ptgt, pkey, rcnt, region_cap, regions, tsum, total, st));
   KNNM_CUDA(launch_unpack((int64_t)N * K, keys, ids, dists, st));
   rc = read_counters(ctx, ctr);
   if (rc) return rc;

@@ -328,8 +328,28 @@ struct SampleArgs {
   int32_t* old_ids;  // [N][cap_old]
   int32_t* old_cnt;  // [N]
   DevCounters* ctr;
+  // optional per-node candidate records for the pipelined join (may be null)
+  unsigned char* rec = nullptr;  // [N][rec_bytes]
+  int rec_cap = 0;               // ids per record (multiple of 4)
+  const float* norms = nullptr;  // canonical norms (COS) copied into the records, else null
+  int K_list = 0;                // list length, for the k-th key of each candidate
 };
 cudaError_t launch_sample(const SampleArgs& a, cudaStream_t st);
+
+// Candidate record of one node, read by the pipelined join with one bulk copy:
+//   int32 {nn, no, 0, 0} | int32 ids[cap] (new first) | uint64 kth[cap] | float cn[cap]
+// kth[r] is the k-th key of candidate r's list at round start; cn[r] its
+// canonical norm (COS only).  cap is a multiple of 4, so the record is a
+// multiple of 16 bytes.
+__host__ __device__ __forceinline__ int rec_bytes(int cap) { return 16 + 16 * cap; }
+__host__ __device__ __forceinline__ int round_up4(int x) { return (x + 3) & ~3; }
+
+// Builds records from public candidate lists (the step-API path).
+cudaError_t launch_build_records(int64_t N, int K, const uint64_t* keys, const float* norms,
+                                 int cap_new, int cap_old, const int32_t* new_ids,
+                                 const int32_t* new_cnt, const int32_t* old_ids,
+                                 const int32_t* old_cnt, unsigned char* rec, int rec_cap,
+                                 cudaStream_t st);
 
 struct JoinArgs {
   int mode;
@@ -348,12 +368,36 @@ struct JoinArgs {
   uint64_t region_cap;  // proposals per region
   unsigned long long* region_cnt;  // [grid] proposals written per region
   uint64_t* live_keys;  // lists receiving direct inserts when a region is full
+  int32_t* prop_cnt;    // [N] proposals written per target (bucket sizes)
   DevCounters* ctr;
   // BF16 path
   const __nv_bfloat16* Xb;  // [N][d] bf16 copy
   const float4* aux;        // per-row {bf16 squared norm, bf16 rounding-error norm, bf16 norm, canonical norm}
+  const float* rmax;        // per-row max |x| of exact-integer rows, -1 otherwise
   int use_bulk;             // rows may be fetched with bulk async copies
 };
+// Pipelined join (knnm_join_pipe.cu): per-node candidate records and rows are
+// staged by a producer warp through NS shared-memory stages.
+struct PipeArgs {
+  const unsigned char* rec;  // [N][rec_bytes(cap)] candidate records
+  int cap;                   // ids per record
+  const __nv_bfloat16* Xe;   // BF16 rows with a 32-byte error-data tail [N][dx]
+  int dx;                    // bf16 elements per extended row
+  int nstages;               // 2 * cw
+  int cw;                    // consumer warps per block
+  int row_bytes;             // bytes copied per candidate row
+  int row_stride;            // bytes between staged rows
+  int stage_bytes;           // record + rows of one stage
+  int pair_cap;              // cap_new * (cap_new + cap_old)
+};
+// Fills the layout fields of P (not rec / Xe), the dynamic shared memory and
+// the persistent grid; fails when the shapes do not fit the pipeline.
+cudaError_t plan_pipe(int precision, int metric, int cap_new, int cap_old, int d, PipeArgs* P,
+                      size_t* smem, int* grid);
+cudaError_t launch_pipe(int precision, const JoinArgs& a, const PipeArgs& P, size_t smem,
+                        int grid, cudaStream_t st);
+cudaError_t launch_bf16_ext(Rows rows, int64_t N, int dx, __nv_bfloat16* Xe, cudaStream_t st);
+
 // Persistent join kernels: `grid` blocks loop over the nodes.
 struct JoinPlan {
   int grid;       // blocks (= proposal regions)
@@ -363,25 +407,24 @@ struct JoinPlan {
 cudaError_t plan_join(int precision, int metric, int cap_new, int cap_old, int d, JoinPlan* out);
 cudaError_t launch_join(int precision, const JoinArgs& a, const JoinPlan& plan, cudaStream_t st);
 
-struct UpdateArgs {
-  const int32_t* prop_tgt;  // proposal buffer, region b = [b*region_cap, (b+1)*region_cap)
-  const uint64_t* prop_key;
-  uint64_t* keys;  // [N][K] lists receiving the proposals
-  int K;
-};
-// One block per region; region_cnt[b] proposals were written into region b.
-cudaError_t launch_update_regions(const UpdateArgs& a, const unsigned long long* region_cnt,
-                                  uint64_t region_cap, int regions, cudaStream_t st);
-
-struct FinalizeArgs {
+struct MergeArgs {
   int64_t N;
   int K;
-  const uint64_t* keys;
-  const uint64_t* prev_keys;
-  uint8_t* flags;
+  uint64_t* keys;             // [N][K] lists, merged in place
+  const uint64_t* prev_keys;  // [N][K] round-start snapshot (flags / c_t)
+  uint8_t* flags;             // [N][K] round-start flags in, merged flags out
+  int32_t* cnt;               // [N] per-target proposal counts; consumed back to zero
+  unsigned long long* offs;   // [N+1] bucket offsets (written by the scan)
+  uint64_t* bucket;           // proposal keys grouped by target
   DevCounters* ctr;
 };
-cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t st);
+// Scan of the counts, scatter of the proposal regions into buckets, and the
+// per-node merge of list and bucket (UpdateNN of the whole round) with flags
+// and c_t.  tile_sum needs ceil(N / 1024) entries.
+cudaError_t launch_bucket_update(const MergeArgs& a, const int32_t* prop_tgt,
+                                 const uint64_t* prop_key, const unsigned long long* region_cnt,
+                                 uint64_t region_cap, int regions, unsigned long long* tile_sum,
+                                 unsigned long long* total, cudaStream_t st);
 
 cudaError_t launch_final(int64_t N, int K, const uint64_t* keys, int Kr, const uint64_t* rear,
                          int32_t* out_ids, float* out_dists, cudaStream_t st);
@@ -393,7 +436,8 @@ cudaError_t launch_unpack(int64_t count, const uint64_t* keys, int32_t* ids, flo
                           cudaStream_t st);
 
 // BF16 shadow copy and per-row error data for the tensor-core path.
-cudaError_t launch_bf16_prep(Rows rows, int64_t N, __nv_bfloat16* Xb, float4* aux,
+// rmax[i] = max |x| of row i when BF16 holds the row exactly as integers, else -1.
+cudaError_t launch_bf16_prep(Rows rows, int64_t N, __nv_bfloat16* Xb, float4* aux, float* rmax,
                              cudaStream_t st);
 
 }  // namespace knnm

@@ -118,6 +118,7 @@ __device__ __forceinline__ void emit(const JoinArgs& a, JoinShared& S, bool hp, 
     if (pos < a.region_cap) {
       a.prop_tgt[region + pos] = tp;
       a.prop_key[region + pos] = kp;
+      atomicAdd(&a.prop_cnt[tp], 1);
     } else {
       slots_insert(a.live_keys + (size_t)tp * a.K, a.K, kp);
     }
@@ -127,6 +128,7 @@ __device__ __forceinline__ void emit(const JoinArgs& a, JoinShared& S, bool hp, 
     if (pos < a.region_cap) {
       a.prop_tgt[region + pos] = tq;
       a.prop_key[region + pos] = kq;
+      atomicAdd(&a.prop_cnt[tq], 1);
     } else {
       slots_insert(a.live_keys + (size_t)tq * a.K, a.K, kq);
     }
@@ -355,6 +357,26 @@ __device__ __forceinline__ float tc_bound(float g, float4 ai, float4 aj, int d, 
   }
 }
 
+// Rows whose every value is a non-negative integer <= 256 are held exactly by
+// BF16 (rmax = their max, else -1).  If d * (max_i^2 + max_j^2) < 2^24 every
+// product and every partial sum of the dot product, the norms, their sum and
+// the canonical in-order sum of (x_i - x_j)^2 are integers below 2^24, so the
+// tensor-core accumulation and the canonical FP32 evaluation are both exact
+// and agree bit for bit.
+__device__ __forceinline__ bool exact_pair(float ri, float rj, int d) {
+  if (ri < 0.f || rj < 0.f) return false;
+  const long long mi = (long long)ri, mj = (long long)rj;
+  return (long long)d * (mi * mi + mj * mj) < (1ll << 24);
+}
+
+// The canonical distance from an exact dot product g, finished with the same
+// correctly rounded operations as the canonical evaluation.
+template <int METRIC>
+__device__ __forceinline__ float exact_estimate(float g, float4 ai, float4 aj) {
+  if (METRIC == L2) return __fsub_rn(__fadd_rn(ai.x, aj.x), __fmul_rn(2.0f, g));
+  return canon_finish<METRIC>(g, ai.w, aj.w);
+}
+
 template <int METRIC>
 __global__ void __launch_bounds__(JT) k_join_bf16(JoinArgs a, int pair_cap) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -375,6 +397,8 @@ __global__ void __launch_bounds__(JT) k_join_bf16(JoinArgs a, int pair_cap) {
   p += 16;
   float4* saux = (float4*)p;
   p += TC_ROWS * sizeof(float4);
+  float* srmax = (float*)p;
+  p += TC_ROWS * 4;
   uint16_t* cand = (uint16_t*)p;  // pairs to re-rank
   p += (size_t)pair_cap * 2;
   S.pairs = (uint16_t*)p;  // unused by this kernel except as scratch
@@ -397,7 +421,10 @@ __global__ void __launch_bounds__(JT) k_join_bf16(JoinArgs a, int pair_cap) {
     int nn, M;
     load_candidates(a, u, S, nn, M);
     if (threadIdx.x == 0) s_rr[0] = 0;
-    for (int r = threadIdx.x; r < M; r += JT) saux[r] = a.aux[S.cid[r]];
+    for (int r = threadIdx.x; r < M; r += JT) {
+      saux[r] = a.aux[S.cid[r]];
+      srmax[r] = a.rmax[S.cid[r]];
+    }
     __syncthreads();
     if (nn > 0 && M > 1) {
       gathered += (threadIdx.x == 0) ? (unsigned long long)M : 0ull;
@@ -439,17 +466,32 @@ __global__ void __launch_bounds__(JT) k_join_bf16(JoinArgs a, int pair_cap) {
             const int j = ng * 32 + x * 8 + 2 * (lane & 3) + (h & 1);
             bool ok = i < nn && j < M && j > i &&
                       pair_allowed(a.mode, a.n1, S.cid[i], S.cid[j]);
+            bool hp = false, hq = false;
+            int32_t tp = 0, tq = 0;
+            uint64_t kp = 0, kq = 0;
             if (ok) {
               float est;
-              const float E = tc_bound<METRIC>(c[x][h], saux[i], saux[j], d, &est);
-              const float thr = fmaxf(key_dist(S.kth[i]), key_dist(S.kth[j]));
-              // S.kth holds the full key; a pair whose lower bound exceeds both
-              // k-th distances can be dropped
-              if (est - E <= thr) {
-                int pos = atomicAdd(s_rr, 1);
-                cand[pos] = (uint16_t)((i << 8) | j);
+              if (exact_pair(srmax[i], srmax[j], d)) {
+                // both rows are small non-negative integers: the tensor-core sum
+                // and the canonical FP32 sum are the same exact integers
+                est = exact_estimate<METRIC>(c[x][h], saux[i], saux[j]);
+                tp = S.cid[i];
+                tq = S.cid[j];
+                kp = make_key(est, tq);
+                kq = make_key(est, tp);
+                hp = kp < S.kth[i];
+                hq = kq < S.kth[j];
+              } else {
+                const float E = tc_bound<METRIC>(c[x][h], saux[i], saux[j], d, &est);
+                const float thr = fmaxf(key_dist(S.kth[i]), key_dist(S.kth[j]));
+                // a pair whose lower bound exceeds both k-th distances is dropped
+                if (est - E <= thr) {
+                  int pos = atomicAdd(s_rr, 1);
+                  cand[pos] = (uint16_t)((i << 8) | j);
+                }
               }
             }
+            emit(a, S, hp, tp, kp, hq, tq, kq);
             evals += ok ? 1ull : 0ull;
           }
         }
@@ -510,7 +552,7 @@ size_t fp32_smem_bytes(int cap_rows, int chunk, int pair_cap, bool chunked) {
 
 size_t bf16_smem_bytes(int d, int pair_cap) {
   size_t b = (size_t)TC_ROWS * (d * 2 + 16);
-  b += TC_ROWS * 8 + 16 + TC_ROWS * 4 * 2 + 16 + TC_ROWS * sizeof(float4);
+  b += TC_ROWS * 8 + 16 + TC_ROWS * 4 * 2 + 16 + TC_ROWS * sizeof(float4) + TC_ROWS * 4;
   b += (size_t)pair_cap * 2 * 2;
   return (b + 127) & ~(size_t)127;
 }

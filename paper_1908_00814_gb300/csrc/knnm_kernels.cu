@@ -260,52 +260,231 @@ __global__ void __launch_bounds__(BLOCK) k_sample_rev(SampleArgs a) {
       a.new_cnt[u] = nn;
       a.old_cnt[u] = no;
     }
+    if (a.rec) {
+      unsigned char* R = a.rec + (size_t)u * rec_bytes(a.rec_cap);
+      int32_t* rid = (int32_t*)(R + 16);
+      uint64_t* rkth = (uint64_t*)(R + 16 + 4 * a.rec_cap);
+      float* rcn = (float*)(R + 16 + 12 * a.rec_cap);
+      auto put = [&](int pos, int32_t id) {
+        rid[pos] = id;
+        rkth[pos] = a.keys[(size_t)id * a.K_list + (a.K_list - 1)];
+        if (a.norms) rcn[pos] = a.norms[id];
+      };
+      if (lane < nf) put(lane, fn);
+      if (add_rn) put(nf + __popc(b1 & lanemask_lt()), rn);
+      if (keep_fo) put(nn + __popc(b2 & lanemask_lt()), fo);
+      if (keep_ro) put(nn + __popc(b2) + __popc(b3 & lanemask_lt()), ro);
+      if (lane == 0) {
+        int32_t* h = (int32_t*)R;
+        h[0] = nn;
+        h[1] = no;
+        h[2] = 0;
+        h[3] = 0;
+      }
+    }
   }
 }
 
-// ---------------------------------------------------------------------------
-// Top-k insert (UpdateNN) and the flag / counter pass
-// ---------------------------------------------------------------------------
-
-// One thread per proposal; region b of the buffer was filled by join block b.
-__global__ void k_update(UpdateArgs a, const unsigned long long* region_cnt, uint64_t region_cap) {
-  const uint64_t cnt = region_cnt[blockIdx.x];
-  const uint64_t base = (uint64_t)blockIdx.x * region_cap;
-  for (uint64_t o = threadIdx.x; o < cnt; o += blockDim.x) {
-    int32_t tgt = a.prop_tgt[base + o];
-    uint64_t key = a.prop_key[base + o];
-    slots_insert(a.keys + (size_t)tgt * a.K, a.K, key);
-  }
-}
-
-__global__ void __launch_bounds__(BLOCK) k_finalize(FinalizeArgs a) {
-  __shared__ unsigned long long red[WARPS_PER_BLOCK];
+__global__ void __launch_bounds__(BLOCK) k_build_records(int64_t N, int K, const uint64_t* keys,
+                                                         const float* norms, int cap_new,
+                                                         int cap_old, const int32_t* new_ids,
+                                                         const int32_t* new_cnt,
+                                                         const int32_t* old_ids,
+                                                         const int32_t* old_cnt,
+                                                         unsigned char* rec, int rec_cap) {
   const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
+  for (int64_t u = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5); u < N;
+       u += nwarps) {
+    const int nn = min(new_cnt[u], cap_new), no = min(old_cnt[u], cap_old);
+    unsigned char* R = rec + (size_t)u * rec_bytes(rec_cap);
+    int32_t* rid = (int32_t*)(R + 16);
+    uint64_t* rkth = (uint64_t*)(R + 16 + 4 * rec_cap);
+    float* rcn = (float*)(R + 16 + 12 * rec_cap);
+    for (int r = lane; r < nn + no; r += 32) {
+      const int32_t id = r < nn ? new_ids[(size_t)u * cap_new + r]
+                                : old_ids[(size_t)u * cap_old + (r - nn)];
+      const int32_t safe = (id < 0 || id >= N) ? 0 : id;
+      rid[r] = id;
+      rkth[r] = keys[(size_t)safe * K + (K - 1)];
+      if (norms) rcn[r] = norms[safe];
+    }
+    if (lane == 0) {
+      int32_t* h = (int32_t*)R;
+      h[0] = nn;
+      h[1] = no;
+      h[2] = 0;
+      h[3] = 0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Bucketed UpdateNN: the join counted proposals per target; an exclusive scan
+// turns the counts into bucket offsets, a scatter pass moves every proposal
+// key into its target's bucket, and one warp per node merges its list with its
+// bucket (top-K distinct keys), sets the flags against the round-start
+// snapshot and counts c_t.
+// ---------------------------------------------------------------------------
+
+constexpr int SCAN_TILE = 1024;  // elements per scan block (256 threads x 4)
+
+__global__ void __launch_bounds__(256) k_scan_tiles(const int32_t* cnt, int64_t n,
+                                                    unsigned long long* tile_sum) {
+  __shared__ unsigned long long red[8];
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + threadIdx.x * 4;
+  unsigned long long s = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (base + q < n) s += (unsigned)cnt[base + q];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    tile_sum[blockIdx.x] = t;
+  }
+}
+
+// Exclusive scan of the tile sums in place (one block, running carry).
+__global__ void __launch_bounds__(1024) k_scan_sums(unsigned long long* tile_sum, int64_t ntiles,
+                                                    unsigned long long* total) {
+  __shared__ unsigned long long wsum[32];
+  __shared__ unsigned long long carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int64_t b = 0; b < ntiles; b += 1024) {
+    int64_t i = b + threadIdx.x;
+    unsigned long long v = i < ntiles ? tile_sum[i] : 0ull;
+    unsigned long long x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long y = __shfl_up_sync(FULL, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      unsigned long long z = wsum[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(FULL, z, o);
+        if (lane >= o) z += y;
+      }
+      wsum[lane] = z;
+    }
+    __syncthreads();
+    unsigned long long incl = x + (w > 0 ? wsum[w - 1] : 0ull);
+    if (i < ntiles) tile_sum[i] = carry + incl - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void __launch_bounds__(256) k_scan_apply(const int32_t* cnt, int64_t n,
+                                                    const unsigned long long* tile_off,
+                                                    unsigned long long* offs,
+                                                    const unsigned long long* total) {
+  __shared__ unsigned long long wsum[8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + threadIdx.x * 4;
+  unsigned long long v[4], s = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    v[q] = base + q < n ? (unsigned)cnt[base + q] : 0u;
+    s += v[q];
+  }
+  unsigned long long x = s;
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  unsigned long long before = tile_off[blockIdx.x];
+  for (int q = 0; q < w; ++q) before += wsum[q];
+  before += x - s;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (base + q < n) offs[base + q] = before;
+    before += v[q];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) offs[n] = *total;
+}
+
+// One block per proposal region: moves each key into its target's bucket.
+// Counts are consumed (decremented back to zero) to find the slot.
+__global__ void k_scatter(const int32_t* prop_tgt, const uint64_t* prop_key,
+                          const unsigned long long* region_cnt, uint64_t region_cap,
+                          int32_t* cnt, const unsigned long long* offs, uint64_t* bucket) {
+  const uint64_t n = region_cnt[blockIdx.x];
+  const uint64_t base = (uint64_t)blockIdx.x * region_cap;
+  for (uint64_t o = threadIdx.x; o < n; o += blockDim.x) {
+    const int32_t tgt = prop_tgt[base + o];
+    const uint64_t key = prop_key[base + o];
+    const int pos = atomicSub(&cnt[tgt], 1) - 1;
+    bucket[offs[tgt] + (uint64_t)pos] = key;
+  }
+}
+
+__global__ void __launch_bounds__(BLOCK) k_merge_lists(MergeArgs a) {
+  __shared__ unsigned long long red[WARPS_PER_BLOCK];
+  __shared__ uint64_t stage[WARPS_PER_BLOCK][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
   const int K = a.K;
   unsigned long long cnt = 0;
-  const int64_t nodes_per_pass = nwarps;
-  // every warp runs the same number of passes so the block reduction is safe
-  const int64_t passes = (a.N + nodes_per_pass - 1) / nodes_per_pass;
-  const int64_t w0 = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
+  const int64_t passes = (a.N + nwarps - 1) / nwarps;
+  const int64_t w0 = (int64_t)blockIdx.x * WARPS_PER_BLOCK + w;
   for (int64_t p = 0; p < passes; ++p) {
-    int64_t v = w0 + p * nodes_per_pass;
+    const int64_t v = w0 + p * nwarps;
     if (v >= a.N) continue;
-    uint64_t nk = lane < K ? a.keys[(size_t)v * K + lane] : KEY_EMPTY;
-    uint64_t pk = lane < K ? a.prev_keys[(size_t)v * K + lane] : KEY_EMPTY - 1;
-    uint8_t pf = lane < K ? a.flags[(size_t)v * K + lane] : FLAG_NEW;
+    uint64_t cur = lane < K ? a.keys[(size_t)v * K + lane] : KEY_EMPTY;
+    const uint64_t b0 = a.offs[v], b1 = a.offs[v + 1];
+    for (uint64_t c = b0; c < b1; c += 32) {
+      uint64_t x = c + lane < b1 ? a.bucket[c + lane] : KEY_EMPTY;
+      const uint64_t kth = __shfl_sync(FULL, cur, K - 1);
+      if (x >= kth) x = KEY_EMPTY;
+      if (!__any_sync(FULL, x != KEY_EMPTY)) continue;
+      uint64_t e0 = cur, e1 = x;
+      warp_sort64(e0, e1);
+      uint64_t p0 = __shfl_up_sync(FULL, e0, 1);
+      uint64_t p1 = __shfl_up_sync(FULL, e1, 1);
+      const uint64_t last0 = __shfl_sync(FULL, e0, 31);
+      if (lane == 0) p1 = last0;
+      const bool k0 = e0 != KEY_EMPTY && (lane == 0 || e0 != p0);
+      const bool k1 = e1 != KEY_EMPTY && e1 != p1;
+      const unsigned m0 = __ballot_sync(FULL, k0), m1 = __ballot_sync(FULL, k1);
+      const unsigned lt = (1u << lane) - 1u;
+      const int pos0 = __popc(m0 & lt), pos1 = __popc(m0) + __popc(m1 & lt);
+      stage[w][lane] = KEY_EMPTY;
+      __syncwarp();
+      if (k0 && pos0 < 32) stage[w][pos0] = e0;
+      if (k1 && pos1 < 32) stage[w][pos1] = e1;
+      __syncwarp();
+      cur = lane < K ? stage[w][lane] : KEY_EMPTY;
+      __syncwarp();
+    }
+    // flags against the round-start snapshot; c_t counts entries absent from it
+    const uint64_t pk = lane < K ? a.prev_keys[(size_t)v * K + lane] : KEY_EMPTY - 1;
+    const uint8_t pf = lane < K ? a.flags[(size_t)v * K + lane] : FLAG_NEW;
     bool found = false;
     uint8_t fl = FLAG_NEW;
     for (int m = 0; m < K; ++m) {
-      uint64_t o = __shfl_sync(FULL, pk, m);
-      uint8_t of = (uint8_t)__shfl_sync(FULL, (int)pf, m);
-      if (o == nk) {
+      const uint64_t o = __shfl_sync(FULL, pk, m);
+      const uint8_t of = (uint8_t)__shfl_sync(FULL, (int)pf, m);
+      if (o == cur) {
         found = true;
         fl = of;
       }
     }
     __syncwarp();
-    if (lane < K) a.flags[(size_t)v * K + lane] = found ? fl : FLAG_NEW;
+    if (lane < K) {
+      a.keys[(size_t)v * K + lane] = cur;
+      a.flags[(size_t)v * K + lane] = found ? fl : FLAG_NEW;
+    }
     cnt += __popc(__ballot_sync(FULL, lane < K && !found));
   }
   block_add(&a.ctr->updates, cnt, red);
@@ -359,13 +538,16 @@ __global__ void k_unpack(int64_t count, const uint64_t* keys, int32_t* ids, floa
   }
 }
 
-// BF16 shadow copy; aux = {|b|^2, |b - x| (upper bound), |b| (upper bound), canonical |x|}.
-__global__ void k_bf16_prep(Rows R, int64_t N, __nv_bfloat16* Xb, float4* aux) {
+// BF16 shadow copy; aux = {|b|^2, |b - x| (upper bound), |b| (upper bound),
+// canonical |x|}.  rmax = max |x_t| when every x_t is an integer of magnitude
+// <= 256 (BF16 holds it exactly), else -1.
+__global__ void k_bf16_prep(Rows R, int64_t N, __nv_bfloat16* Xb, float4* aux, float* rmax) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const float* x = R.row(i);
   __nv_bfloat16* o = Xb + (size_t)i * R.d;
-  float nb2 = 0.f, e2 = 0.f, nx2 = 0.f;
+  float nb2 = 0.f, e2 = 0.f, nx2 = 0.f, mx = 0.f;
+  bool exact = true;
   for (int t = 0; t < R.d; ++t) {
     float v = __ldg(x + t);
     __nv_bfloat16 b = __float2bfloat16_rn(v);
@@ -375,11 +557,14 @@ __global__ void k_bf16_prep(Rows R, int64_t N, __nv_bfloat16* Xb, float4* aux) {
     float e = __fsub_rn(bf, v);  // exact: bf and v are within a factor of two
     e2 = __fmaf_rn(e, e, e2);
     nx2 = __fmaf_rn(v, v, nx2);
+    exact = exact && v == rintf(v) && fabsf(v) <= 256.0f;
+    mx = fmaxf(mx, fabsf(v));
   }
   // sums of d non-negative terms carry at most d+1 relative roundings
   const float grow = 1.0f + (float)(R.d + 2) * 1.2e-7f;
   aux[i] = make_float4(nb2, __fsqrt_ru(e2 * grow) * 1.000001f, __fsqrt_ru(nb2 * grow) * 1.000001f,
                        __fsqrt_rn(nx2));
+  rmax[i] = exact ? mx : -1.0f;
 }
 
 }  // namespace
@@ -414,14 +599,29 @@ cudaError_t launch_sample(const SampleArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_update_regions(const UpdateArgs& a, const unsigned long long* region_cnt,
-                                  uint64_t region_cap, int regions, cudaStream_t st) {
-  k_update<<<regions, 256, 0, st>>>(a, region_cnt, region_cap);
+cudaError_t launch_build_records(int64_t N, int K, const uint64_t* keys, const float* norms,
+                                 int cap_new, int cap_old, const int32_t* new_ids,
+                                 const int32_t* new_cnt, const int32_t* old_ids,
+                                 const int32_t* old_cnt, unsigned char* rec, int rec_cap,
+                                 cudaStream_t st) {
+  k_build_records<<<grid_for_warps(N), BLOCK, 0, st>>>(N, K, keys, norms, cap_new, cap_old,
+                                                       new_ids, new_cnt, old_ids, old_cnt, rec,
+                                                       rec_cap);
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t st) {
-  k_finalize<<<grid_for_warps(a.N), BLOCK, 0, st>>>(a);
+cudaError_t launch_bucket_update(const MergeArgs& a, const int32_t* prop_tgt,
+                                 const uint64_t* prop_key, const unsigned long long* region_cnt,
+                                 uint64_t region_cap, int regions, unsigned long long* tile_sum,
+                                 unsigned long long* total, cudaStream_t st) {
+  const int64_t ntiles = (a.N + SCAN_TILE - 1) / SCAN_TILE;
+  k_scan_tiles<<<(unsigned)ntiles, 256, 0, st>>>(a.cnt, a.N, tile_sum);
+  k_scan_sums<<<1, 1024, 0, st>>>(tile_sum, ntiles, total);
+  k_scan_apply<<<(unsigned)ntiles, 256, 0, st>>>(a.cnt, a.N, tile_sum,
+                                                 (unsigned long long*)a.offs, total);
+  k_scatter<<<regions, 256, 0, st>>>(prop_tgt, prop_key, region_cnt, region_cap, a.cnt, a.offs,
+                                     a.bucket);
+  k_merge_lists<<<grid_for_warps(a.N), BLOCK, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -445,10 +645,10 @@ cudaError_t launch_unpack(int64_t count, const uint64_t* keys, int32_t* ids, flo
   return cudaGetLastError();
 }
 
-cudaError_t launch_bf16_prep(Rows rows, int64_t N, __nv_bfloat16* Xb, float4* aux,
+cudaError_t launch_bf16_prep(Rows rows, int64_t N, __nv_bfloat16* Xb, float4* aux, float* rmax,
                              cudaStream_t st) {
   if (N == 0) return cudaSuccess;
-  k_bf16_prep<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(rows, N, Xb, aux);
+  k_bf16_prep<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(rows, N, Xb, aux, rmax);
   return cudaGetLastError();
 }
 

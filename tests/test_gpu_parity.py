@@ -338,3 +338,24 @@ def test_invalid_inputs_are_rejected(torch, km, ctx, orc):
     gi, _, _ = ctx.merge_symmetric(cuda(torch, X[:n1]), cuda(torch, G1), cuda(torch, X[n1:]),
                                    cuda(torch, G2), p)
     assert host(gi).shape == (100, K)
+
+
+@pytest.mark.parametrize("d,hi", [(128, 255), (136, 255), (64, 256), (128, 17)])
+def test_join_parity_integer_extremes(torch, km, ctx, orc, d, hi):
+    """Non-negative integer rows take the exact tensor-core path when
+    d * (max_i^2 + max_j^2) < 2^24 (128 x 255: sums up to 16.6M, just inside),
+    the bounded path otherwise (136 x 255); both must equal the oracle."""
+    rng = np.random.default_rng(d + hi)
+    X = rng.choice(np.array([0, 1, hi - 1, hi], np.float32), size=(900, d),
+                   p=[0.3, 0.2, 0.2, 0.3]).astype(np.float32)
+    X[:, :5] = rng.integers(0, hi + 1, size=(900, 5))  # break exact duplicates
+    K = 10
+    st, cands = _join_case(orc, X, 0, K, orc.JOINT, 0)
+    ref = st.copy()
+    c_ref, e_ref = orc.join(orc.JOINT, X, 0, ref, cands)
+    ids, dists, flags = cuda(torch, st.ids), cuda(torch, st.dists), cuda(torch, st.flags)
+    c, e = ctx.step_join(km.JOINT, cuda(torch, X), 0, km.params(k=K, precision="bf16"), ids,
+                         dists, flags, tuple(cuda(torch, a) for a in cands))
+    assert (c, e) == (c_ref, e_ref)
+    assert_same(host(ids), ref.ids, "ids")
+    assert_same(host(dists), ref.dists, "dists")
