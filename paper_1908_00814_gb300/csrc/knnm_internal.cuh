@@ -383,8 +383,11 @@ struct PipeArgs {
   int cap;                   // ids per record
   const __nv_bfloat16* Xe;   // BF16 rows with a 32-byte error-data tail [N][dx]
   int dx;                    // bf16 elements per extended row
-  int nstages;               // 2 * cw
-  int cw;                    // consumer warps per block
+  int nstages;               // unused by the ring kernel
+  int cw;                    // warps per block
+  int ring_rows;             // rows in each warp's ring
+  unsigned long long cpr_inv;  // ceil(2^32 / (row_bytes / 16)): chunk -> row by multiply-shift
+  int warp_bytes;            // shared memory per warp
   int row_bytes;             // bytes copied per candidate row
   int row_stride;            // bytes between staged rows
   int stage_bytes;           // record + rows of one stage
