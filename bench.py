@@ -227,6 +227,8 @@ def run_ours(args, w):
     X = datagen.generate(WORKLOAD, n=w["n"])
     n1 = w["n"] // 2
     K, d = w["k"], w["d"]
+    if rank == 0:
+        print(f"# workload {WORKLOAD}: {w['n']} x {d}, k={K}", file=sys.stderr, flush=True)
     Xd = torch.from_numpy(X).cuda()
     S1, S2 = Xd[:n1].contiguous(), Xd[n1:].contiguous()
     bp = knnm.params(k=K, precision="bf16", max_iters=10, sample_rate=w["sample_rate"],
@@ -349,6 +351,9 @@ def run_ours(args, w):
             "dtype": "bf16+f32", "data": "synthetic", "config": workload_config(w, "bf16_rerank"),
             "recall_at_10": recall, "recall_queries": len(queries),
             "rounds": st_bf[-1]["rounds"], "updates_per_round": st_bf[-1]["updates"],
+            "per_round": {k: st_bf[-1][k] for k in ("dist_evals", "proposals", "reranked",
+                                                    "gathered", "ms_sample", "ms_join",
+                                                    "ms_update")},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches}
     if not args.no_fp32:
@@ -382,10 +387,14 @@ def main():
     ap.add_argument("--recall-queries", type=int, default=1000)
     ap.add_argument("--cpu-rows", type=int, default=20000)
     ap.add_argument("--reference-rows", type=int, default=5000)
+    ap.add_argument("--rows", type=int, default=None,
+                    help="run the same workload cut to this many points (profiling only)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
-    w = datagen.WORKLOADS[WORKLOAD]
+    w = dict(datagen.WORKLOADS[WORKLOAD])
+    if args.rows:
+        w["n"] = args.rows
     if args.impl == "reference":
         return run_reference(args, w)
     return run_ours(args, w)
