@@ -243,6 +243,9 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     int32_t* pcnt;
     unsigned long long *offs, *tile_sum, *total;
     uint64_t* bucket;
+    int32_t* rcnt;
+    unsigned long long *roffs, *rtile, *rtotal;
+    uint64_t* rbucket;
   } P;
   auto carve = [&](Carver& c) {
     P.X = (!s1_dev || !s2_dev) ? c.take<float>((size_t)N * d) : nullptr;
@@ -253,8 +256,11 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     P.keys = c.take<uint64_t>((size_t)N * K);
     P.prev = c.take<uint64_t>((size_t)N * K);
     P.rear = c.take<uint64_t>((size_t)N * (D.Kr > 0 ? D.Kr : 1));
-    P.rev_new = c.take<uint64_t>((size_t)N * D.s);
-    P.rev_old = c.take<uint64_t>((size_t)N * D.s);
+    P.rcnt = c.take<int32_t>((size_t)2 * N);
+    P.roffs = c.take<unsigned long long>((size_t)2 * N + 1);
+    P.rbucket = c.take<uint64_t>((size_t)N * K);
+    P.rtile = c.take<unsigned long long>((size_t)(2 * N + 1023) / 1024 + 1);
+    P.rtotal = c.take<unsigned long long>(1);
     P.flags = c.take<uint8_t>((size_t)N * K);
     P.new_ids = c.take<int32_t>((size_t)N * D.cap_new);
     P.new_cnt = c.take<int32_t>((size_t)N);
@@ -346,6 +352,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   ia.metric = params->metric;
   ia.seed = params->seed;
   ia.norms = P.norms;
+  ia.vec4 = (d % 4 == 0 && aligned16(rows.X1) && aligned16(rows.X2)) ? 1 : 0;
   ia.keys = P.keys;
   ia.flags = P.flags;
   ia.rear = P.rear;
@@ -369,8 +376,13 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   sa.keys = P.keys;
   sa.flags = P.flags;
   sa.prev_keys = P.prev;
-  sa.rev_new = P.rev_new;
-  sa.rev_old = P.rev_old;
+  sa.rev_new = nullptr;
+  sa.rev_old = nullptr;
+  sa.rcnt = P.rcnt;
+  sa.roffs = P.roffs;
+  sa.rbucket = P.rbucket;
+  sa.tile_sum = P.rtile;
+  sa.total = P.rtotal;
   sa.cap_new = D.cap_new;
   sa.cap_old = D.cap_old;
   sa.new_ids = P.new_ids;
@@ -414,13 +426,12 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   ja.use_bulk = use_bulk ? 1 : 0;
   MergeArgs ma{N, K, P.keys, P.prev, P.flags, P.pcnt, P.offs, P.bucket, P.ctr};
   KNNM_CUDA(cudaMemsetAsync(P.pcnt, 0, (size_t)N * 4, st));
+  KNNM_CUDA(cudaMemsetAsync(P.rcnt, 0, (size_t)N * 8, st));
 
   const double stop_at = (double)params->delta * (double)N * (double)K;
   for (int t = 1; t <= params->max_iters; ++t) {
     KNNM_CUDA(cudaMemsetAsync(P.ctr, 0, sizeof(DevCounters), st));
     KNNM_CUDA(cudaMemsetAsync(&P.ctr->err_row, 0xFF, 8, st));
-    KNNM_CUDA(cudaMemsetAsync(P.rev_new, 0xFF, (size_t)N * D.s * 8, st));
-    KNNM_CUDA(cudaMemsetAsync(P.rev_old, 0xFF, (size_t)N * D.s * 8, st));
     sa.t = t;
     KNNM_CUDA(cudaEventRecord(ctx->rev[0], st));
     KNNM_CUDA(launch_sample(sa, st));
@@ -433,7 +444,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     KNNM_CUDA(launch_bucket_update(ma, P.prop_tgt, P.prop_key, P.region_cnt, region_cap,
                                    regions, P.tile_sum, P.total, st));
     KNNM_CUDA(cudaEventRecord(ctx->rev[3], st));
-    launches += 8;
+    launches += 12;
     KNNM_CUDA(cudaMemcpyAsync(ctx->host_ctr, P.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
     KNNM_CUDA(cudaStreamSynchronize(st));
     const DevCounters& h = *ctx->host_ctr;
@@ -661,6 +672,7 @@ extern "C" int knnm_step_init(knnm_ctx* ctx, int mode, const float* X1, int64_t 
   ia.metric = params->metric;
   ia.seed = params->seed;
   ia.norms = params->metric == KNNM_COS ? norms : nullptr;
+  ia.vec4 = (d % 4 == 0 && aligned16(rows.X1) && aligned16(rows.X2)) ? 1 : 0;
   ia.keys = keys;
   ia.flags = flags;
   ia.rear = rear;
@@ -687,24 +699,28 @@ extern "C" int knnm_step_sample(knnm_ctx* ctx, int64_t N, int K, const int32_t* 
     return fail(ctx, KNNM_ERR_INVALID, "bad sampling arguments");
   cudaStream_t st = ctx->stream;
   KNNM_CUDA(cudaSetDevice(ctx->device));
-  auto carve = [&](Carver& c, uint64_t*& keys, uint64_t*& rn, uint64_t*& ro, DevCounters*& ctr) {
+  uint64_t *keys, *rbucket;
+  int32_t* rcnt;
+  unsigned long long *roffs, *rtile, *rtotal;
+  DevCounters* ctr;
+  auto carve = [&](Carver& c) {
     keys = c.take<uint64_t>((size_t)N * K);
-    rn = c.take<uint64_t>((size_t)N * s);
-    ro = c.take<uint64_t>((size_t)N * s);
+    rcnt = c.take<int32_t>((size_t)2 * N);
+    roffs = c.take<unsigned long long>((size_t)2 * N + 1);
+    rbucket = c.take<uint64_t>((size_t)N * K);
+    rtile = c.take<unsigned long long>((size_t)(2 * N + 1023) / 1024 + 1);
+    rtotal = c.take<unsigned long long>(1);
     ctr = c.take<DevCounters>(1);
   };
-  uint64_t *keys, *rn, *ro;
-  DevCounters* ctr;
   Carver c0;
-  carve(c0, keys, rn, ro, ctr);
+  carve(c0);
   int rc = ensure_arena(ctx, c0.off);
   if (rc) return rc;
   Carver c1;
   c1.base = (char*)ctx->arena;
-  carve(c1, keys, rn, ro, ctr);
+  carve(c1);
   KNNM_CUDA(launch_pack((int64_t)N * K, ids, dists, keys, st));
-  KNNM_CUDA(cudaMemsetAsync(rn, 0xFF, (size_t)N * s * 8, st));
-  KNNM_CUDA(cudaMemsetAsync(ro, 0xFF, (size_t)N * s * 8, st));
+  KNNM_CUDA(cudaMemsetAsync(rcnt, 0, (size_t)N * 8, st));
   KNNM_CUDA(cudaMemsetAsync(ctr, 0, sizeof(DevCounters), st));
   SampleArgs sa;
   sa.N = N;
@@ -715,8 +731,13 @@ extern "C" int knnm_step_sample(knnm_ctx* ctx, int64_t N, int K, const int32_t* 
   sa.keys = keys;
   sa.flags = flags;
   sa.prev_keys = nullptr;
-  sa.rev_new = rn;
-  sa.rev_old = ro;
+  sa.rev_new = nullptr;
+  sa.rev_old = nullptr;
+  sa.rcnt = rcnt;
+  sa.roffs = roffs;
+  sa.rbucket = rbucket;
+  sa.tile_sum = rtile;
+  sa.total = rtotal;
   sa.cap_new = cap_new;
   sa.cap_old = cap_old;
   sa.new_ids = new_ids;

@@ -139,6 +139,24 @@ __device__ __forceinline__ float canon_dist_global(const float* __restrict__ a,
   return canon_finish<METRIC>(acc, na, nb);
 }
 
+// Same with 16-byte loads; a and b 16-byte aligned, d a multiple of 4.
+template <int METRIC>
+__device__ __forceinline__ float canon_dist_global4(const float* __restrict__ a,
+                                                    const float* __restrict__ b, int d, float na,
+                                                    float nb) {
+  float acc = 0.0f;
+  const float4* a4 = reinterpret_cast<const float4*>(a);
+  const float4* b4 = reinterpret_cast<const float4*>(b);
+  for (int t = 0; t < (d >> 2); ++t) {
+    const float4 x = __ldg(a4 + t), y = __ldg(b4 + t);
+    acc = Canon<METRIC>::step(acc, x.x, y.x);
+    acc = Canon<METRIC>::step(acc, x.y, y.y);
+    acc = Canon<METRIC>::step(acc, x.z, y.z);
+    acc = Canon<METRIC>::step(acc, x.w, y.w);
+  }
+  return canon_finish<METRIC>(acc, na, nb);
+}
+
 __device__ __forceinline__ float canon_norm_global(const float* __restrict__ a, int d) {
   float acc = 0.0f;
   for (int t = 0; t < d; ++t) {
@@ -303,6 +321,7 @@ struct InitArgs {
   int K, K_keep, metric;
   uint64_t seed;
   const float* norms;  // canonical norms [N] for COS, else nullptr
+  int vec4;            // rows are 16-byte aligned and d % 4 == 0
   uint64_t* keys;      // [N][K]
   uint8_t* flags;      // [N][K]
   uint64_t* rear;      // [N][Kr]
@@ -333,6 +352,12 @@ struct SampleArgs {
   int rec_cap = 0;               // ids per record (multiple of 4)
   const float* norms = nullptr;  // canonical norms (COS) copied into the records, else null
   int K_list = 0;                // list length, for the k-th key of each candidate
+  // Bucketed reverse sampling (used when rcnt is set; rev_new/rev_old unused):
+  int32_t* rcnt = nullptr;             // [2N] in-edges per (target, stream); zero on entry and exit
+  unsigned long long* roffs = nullptr;  // [2N+1] bucket offsets
+  uint64_t* rbucket = nullptr;         // [N*K] reverse sampling keys grouped by (target, stream)
+  unsigned long long* tile_sum = nullptr;  // [ceil(2N/1024)+1] scan scratch
+  unsigned long long* total = nullptr;     // scan total
 };
 cudaError_t launch_sample(const SampleArgs& a, cudaStream_t st);
 

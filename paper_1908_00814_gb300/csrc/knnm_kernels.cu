@@ -59,12 +59,14 @@ __device__ __forceinline__ void block_add(unsigned long long* dst, unsigned long
 // ---------------------------------------------------------------------------
 
 template <int METRIC>
-__device__ __forceinline__ float dist_rows(const Rows& R, int64_t i, int64_t j, const float* norms) {
+__device__ __forceinline__ float dist_rows(const Rows& R, int64_t i, int64_t j, const float* norms,
+                                           int vec4) {
   float na = 0.f, nb = 0.f;
   if (METRIC == COS) {
     na = norms[i];
     nb = norms[j];
   }
+  if (vec4) return canon_dist_global4<METRIC>(R.row(i), R.row(j), R.d, na, nb);
   return canon_dist_global<METRIC>(R.row(i), R.row(j), R.d, na, nb);
 }
 
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(BLOCK) k_init(InitArgs a) {
       uint64_t key = KEY_EMPTY;
       if (lane < K && !bad) {
         int64_t g = own_base + loc;
-        key = make_key(dist_rows<METRIC>(a.rows, i, g, a.norms), (int32_t)g);
+        key = make_key(dist_rows<METRIC>(a.rows, i, g, a.norms, a.vec4), (int32_t)g);
       }
       key = warp_sort32(key);
       if (lane >= Kk && lane < K) a.rear[(size_t)i * Kr + (lane - Kk)] = key;
@@ -162,7 +164,8 @@ __global__ void __launch_bounds__(BLOCK) k_init(InitArgs a) {
     }
     int32_t drawn = draw_random(a.seed, i, base, n_src, want, K);
     uint64_t dkey = KEY_EMPTY;
-    if (lane < want) dkey = make_key(dist_rows<METRIC>(a.rows, i, drawn, a.norms), drawn);
+    if (lane < want)
+      dkey = make_key(dist_rows<METRIC>(a.rows, i, drawn, a.norms, a.vec4), drawn);
     int first = in ? Kk : 0;
     uint64_t shifted = __shfl_sync(FULL, dkey, (lane - first) & 31);
     uint64_t v = lane < first ? kept : (lane < K ? shifted : KEY_EMPTY);
@@ -209,15 +212,78 @@ __global__ void __launch_bounds__(BLOCK) k_sample_fwd(SampleArgs a) {
       a.new_cnt[u] = __popc(bs);
       a.old_cnt[u] = __popc(bo);
     }
-    if (sel)
-      slots_insert(a.rev_new + (size_t)v * s, s,
-                   sampling_key(hash_prefix(a.seed, (uint64_t)a.t, STREAM_REV_NEW, (uint64_t)v),
-                                (int32_t)u));
-    if (isold)
-      slots_insert(a.rev_old + (size_t)v * s, s,
-                   sampling_key(hash_prefix(a.seed, (uint64_t)a.t, STREAM_REV_OLD, (uint64_t)v),
-                                (int32_t)u));
+    if (a.rcnt) {
+      // bucketed reverse lists: count the in-edges of (target, stream) here
+      if (sel) atomicAdd(&a.rcnt[2 * (size_t)v], 1);
+      if (isold) atomicAdd(&a.rcnt[2 * (size_t)v + 1], 1);
+    } else {
+      if (sel)
+        slots_insert(a.rev_new + (size_t)v * s, s,
+                     sampling_key(hash_prefix(a.seed, (uint64_t)a.t, STREAM_REV_NEW, (uint64_t)v),
+                                  (int32_t)u));
+      if (isold)
+        slots_insert(a.rev_old + (size_t)v * s, s,
+                     sampling_key(hash_prefix(a.seed, (uint64_t)a.t, STREAM_REV_OLD, (uint64_t)v),
+                                  (int32_t)u));
+    }
   }
+}
+
+// Moves each reverse edge's sampling key into its (target, stream) bucket;
+// the counts are consumed back to zero.
+__global__ void __launch_bounds__(BLOCK) k_sample_scatter(SampleArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
+  for (int64_t u = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5); u < a.N;
+       u += nwarps) {
+    const int nf = a.new_cnt[u], of = a.old_cnt[u];
+    if (lane < nf) {
+      const int32_t v = a.new_ids[(size_t)u * a.cap_new + lane];
+      const uint64_t key = sampling_key(
+          hash_prefix(a.seed, (uint64_t)a.t, STREAM_REV_NEW, (uint64_t)v), (int32_t)u);
+      const int pos = atomicSub(&a.rcnt[2 * (size_t)v], 1) - 1;
+      a.rbucket[a.roffs[2 * (size_t)v] + (uint64_t)pos] = key;
+    }
+    if (lane < of) {
+      const int32_t v = a.old_ids[(size_t)u * a.cap_old + lane];
+      const uint64_t key = sampling_key(
+          hash_prefix(a.seed, (uint64_t)a.t, STREAM_REV_OLD, (uint64_t)v), (int32_t)u);
+      const int pos = atomicSub(&a.rcnt[2 * (size_t)v + 1], 1) - 1;
+      a.rbucket[a.roffs[2 * (size_t)v + 1] + (uint64_t)pos] = key;
+    }
+  }
+}
+
+// The s smallest keys of bucket [b0, b1), ascending, lane j holding the j-th
+// (KEY_EMPTY beyond).  Keys in a bucket are distinct.
+__device__ __forceinline__ uint64_t warp_smallest(const uint64_t* bucket, uint64_t b0, uint64_t b1,
+                                                  int s) {
+  const int lane = threadIdx.x & 31;
+  uint64_t best = KEY_EMPTY;
+  for (uint64_t c = b0; c < b1; c += 32) {
+    uint64_t x = c + lane < b1 ? bucket[c + lane] : KEY_EMPTY;
+    const uint64_t kth = __shfl_sync(FULL, best, s - 1);
+    if (x >= kth) x = KEY_EMPTY;
+    unsigned live = __ballot_sync(FULL, x != KEY_EMPTY);
+    if (!live) continue;
+    if (__popc(live) <= 6) {
+      while (live) {
+        const int src = __ffs(live) - 1;
+        live &= live - 1u;
+        const uint64_t y = __shfl_sync(FULL, x, src);
+        if (y >= __shfl_sync(FULL, best, s - 1)) continue;
+        const int pos = __popc(__ballot_sync(FULL, best < y));
+        const uint64_t up = __shfl_up_sync(FULL, best, 1);
+        best = lane == pos ? y : (lane > pos ? up : best);
+        if (lane >= s) best = KEY_EMPTY;
+      }
+    } else {
+      uint64_t e0 = best, e1 = x;
+      warp_sort64(e0, e1);
+      best = lane < s ? e0 : KEY_EMPTY;
+    }
+  }
+  return best;
 }
 
 // new(u) = fwd_new u rev_new;  old(u) = (fwd_old u rev_old) \ new(u).
@@ -230,8 +296,14 @@ __global__ void __launch_bounds__(BLOCK) k_sample_rev(SampleArgs a) {
     const int nf = a.new_cnt[u], of = a.old_cnt[u];
     const int32_t fn = lane < nf ? a.new_ids[(size_t)u * a.cap_new + lane] : -1;
     const int32_t fo = lane < of ? a.old_ids[(size_t)u * a.cap_old + lane] : -2;
-    const uint64_t rk = lane < s ? a.rev_new[(size_t)u * s + lane] : KEY_EMPTY;
-    const uint64_t ok = lane < s ? a.rev_old[(size_t)u * s + lane] : KEY_EMPTY;
+    uint64_t rk, ok;
+    if (a.rcnt) {
+      rk = warp_smallest(a.rbucket, a.roffs[2 * u], a.roffs[2 * u + 1], s);
+      ok = warp_smallest(a.rbucket, a.roffs[2 * u + 1], a.roffs[2 * u + 2], s);
+    } else {
+      rk = lane < s ? a.rev_new[(size_t)u * s + lane] : KEY_EMPTY;
+      ok = lane < s ? a.rev_old[(size_t)u * s + lane] : KEY_EMPTY;
+    }
     const int32_t rn = rk != KEY_EMPTY ? key_id(rk) : -3;
     const int32_t ro = ok != KEY_EMPTY ? key_id(ok) : -4;
     bool rn_dup = false, fo_in_rn = false, ro_drop = false;
@@ -447,7 +519,23 @@ __global__ void __launch_bounds__(BLOCK) k_merge_lists(MergeArgs a) {
       uint64_t x = c + lane < b1 ? a.bucket[c + lane] : KEY_EMPTY;
       const uint64_t kth = __shfl_sync(FULL, cur, K - 1);
       if (x >= kth) x = KEY_EMPTY;
-      if (!__any_sync(FULL, x != KEY_EMPTY)) continue;
+      unsigned live = __ballot_sync(FULL, x != KEY_EMPTY);
+      if (!live) continue;
+      if (__popc(live) <= 6) {
+        // few survivors: insert them one by one (rank insertion across the warp)
+        while (live) {
+          const int src = __ffs(live) - 1;
+          live &= live - 1u;
+          const uint64_t y = __shfl_sync(FULL, x, src);
+          const uint64_t kk = __shfl_sync(FULL, cur, K - 1);
+          if (y >= kk || __any_sync(FULL, cur == y)) continue;
+          const int pos = __popc(__ballot_sync(FULL, cur < y));
+          const uint64_t up = __shfl_up_sync(FULL, cur, 1);
+          cur = lane == pos ? y : (lane > pos ? up : cur);
+          if (lane >= K) cur = KEY_EMPTY;
+        }
+        continue;
+      }
       uint64_t e0 = cur, e1 = x;
       warp_sort64(e0, e1);
       uint64_t p0 = __shfl_up_sync(FULL, e0, 1);
@@ -595,6 +683,16 @@ cudaError_t launch_sample(const SampleArgs& a, cudaStream_t st) {
   k_sample_fwd<<<grid, BLOCK, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (a.rcnt) {
+    const int64_t n2 = 2 * a.N;
+    const int64_t ntiles = (n2 + SCAN_TILE - 1) / SCAN_TILE;
+    k_scan_tiles<<<(unsigned)ntiles, 256, 0, st>>>(a.rcnt, n2, a.tile_sum);
+    k_scan_sums<<<1, 1024, 0, st>>>(a.tile_sum, ntiles, a.total);
+    k_scan_apply<<<(unsigned)ntiles, 256, 0, st>>>(a.rcnt, n2, a.tile_sum, a.roffs, a.total);
+    k_sample_scatter<<<grid, BLOCK, 0, st>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   k_sample_rev<<<grid, BLOCK, 0, st>>>(a);
   return cudaGetLastError();
 }
