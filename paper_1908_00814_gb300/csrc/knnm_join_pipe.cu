@@ -181,7 +181,6 @@ __device__ __forceinline__ void cp16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
                : "memory");
 }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 struct Rec {
@@ -227,6 +226,194 @@ __device__ __forceinline__ int list_pairs(const JoinArgs& a, const Rec& rc, uint
   return np;
 }
 
+// cp.async completions of this lane arrive on `bar` (counted in its 32 arrivals).
+__device__ __forceinline__ void cp_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// One node's distances and proposals, rows read through row_ptr(r).
+// ---------------------------------------------------------------------------
+template <int METRIC, typename RowPtr>
+__device__ __forceinline__ void node_fp32(const JoinArgs& a, const Rec& rc, int np,
+                                          const uint16_t* pairs, RowPtr row_ptr, int* fill) {
+  const int lane = threadIdx.x & 31;
+  const int d = a.rows.d;
+  for (int q0 = 0; q0 < np;) {
+    const int pl = (np - q0 > 32) ? 2 : 1;
+    const float* ra[2];
+    const float* rb[2];
+    float acc[2] = {0.0f, 0.0f};
+    int pi[2], pj[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int q = q0 + t * 32 + lane;
+      const uint16_t pr = (t < pl && q < np) ? pairs[q] : pairs[q0];
+      pi[t] = pr >> 8;
+      pj[t] = pr & 0xFF;
+      ra[t] = (const float*)row_ptr(pi[t]);
+      rb[t] = (const float*)row_ptr(pj[t]);
+    }
+    if (pl == 2) {
+      for (int x = 0; x < d; x += 4) {
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          const float4 p4 = *reinterpret_cast<const float4*>(ra[t] + x);
+          const float4 q4 = *reinterpret_cast<const float4*>(rb[t] + x);
+          acc[t] = Canon<METRIC>::step(acc[t], p4.x, q4.x);
+          acc[t] = Canon<METRIC>::step(acc[t], p4.y, q4.y);
+          acc[t] = Canon<METRIC>::step(acc[t], p4.z, q4.z);
+          acc[t] = Canon<METRIC>::step(acc[t], p4.w, q4.w);
+        }
+      }
+    } else {
+      for (int x = 0; x < d; x += 4) {
+        const float4 p4 = *reinterpret_cast<const float4*>(ra[0] + x);
+        const float4 q4 = *reinterpret_cast<const float4*>(rb[0] + x);
+        acc[0] = Canon<METRIC>::step(acc[0], p4.x, q4.x);
+        acc[0] = Canon<METRIC>::step(acc[0], p4.y, q4.y);
+        acc[0] = Canon<METRIC>::step(acc[0], p4.z, q4.z);
+        acc[0] = Canon<METRIC>::step(acc[0], p4.w, q4.w);
+      }
+    }
+    bool has[4];
+    int32_t tgt[4];
+    uint64_t key[4];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int q = q0 + t * 32 + lane;
+      const bool live = t < pl && q < np;
+      const int i = pi[t], jj = pj[t];
+      const float dist = canon_finish<METRIC>(acc[t], METRIC == COS ? rc.cn[i] : 0.f,
+                                              METRIC == COS ? rc.cn[jj] : 0.f);
+      const int32_t ci = rc.cid[i], cj = rc.cid[jj];
+      key[2 * t] = make_key(dist, cj);
+      key[2 * t + 1] = make_key(dist, ci);
+      tgt[2 * t] = ci;
+      tgt[2 * t + 1] = cj;
+      has[2 * t] = live && key[2 * t] < rc.kth[i];
+      has[2 * t + 1] = live && key[2 * t + 1] < rc.kth[jj];
+    }
+    emit_many<4>(a, fill, has, tgt, key);
+    q0 += 32 * pl;
+  }
+}
+
+// BF16: the Gram block is computed one 16-row tile of new candidates at a time
+// into a 16 x GSTR buffer; pairs come sorted by their first index, so tile mt
+// serves the pairs [split(mt), split(mt + 1)).
+template <int METRIC, typename RowPtr>
+__device__ __forceinline__ void node_tc(const JoinArgs& a, const Rec& rc, int np,
+                                        uint16_t* pairs, int np0, RowPtr row_ptr, float* G,
+                                        int* fill, unsigned long long& reranked) {
+  const int lane = threadIdx.x & 31;
+  const int d = a.rows.d;
+  const int dpad = (d + 15) & ~15;
+  const int mtiles = (rc.nn + 15) >> 4, ntiles = (rc.M + 7) >> 3;
+  int nr = 0;  // re-rank pairs, compacted to the front of the pair list
+  for (int mt = 0; mt < mtiles; ++mt) {
+    const unsigned char* pa = row_ptr(mt * 16 + (lane & 15)) + (lane >> 4) * 16;
+    for (int nt = 0; nt < ntiles; nt += 2) {
+      const bool second = nt + 1 < ntiles;
+      float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
+      const unsigned char* pb0 = row_ptr(nt * 8 + (lane & 7)) + ((lane >> 3) & 1) * 16;
+      const unsigned char* pb1 =
+          row_ptr((second ? nt + 1 : nt) * 8 + (lane & 7)) + ((lane >> 3) & 1) * 16;
+#pragma unroll 8
+      for (int k0 = 0; k0 < dpad; k0 += 16) {
+        uint32_t x0, x1, x2, x3, y0, y1, w0, w1;
+        ldm_x4(x0, x1, x2, x3, pa + k0 * 2);
+        ldm_x2(y0, y1, pb0 + k0 * 2);
+        ldm_x2(w0, w1, pb1 + k0 * 2);
+        mma16816(c0, x0, x1, x2, x3, y0, y1);
+        mma16816(c1, x0, x1, x2, x3, w0, w1);
+      }
+      const int r0 = lane >> 2, col = nt * 8 + 2 * (lane & 3);
+      G[r0 * GSTR + col] = c0[0];
+      G[r0 * GSTR + col + 1] = c0[1];
+      G[(r0 + 8) * GSTR + col] = c0[2];
+      G[(r0 + 8) * GSTR + col + 1] = c0[3];
+      if (second) {
+        G[r0 * GSTR + col + 8] = c1[0];
+        G[r0 * GSTR + col + 9] = c1[1];
+        G[(r0 + 8) * GSTR + col + 8] = c1[2];
+        G[(r0 + 8) * GSTR + col + 9] = c1[3];
+      }
+    }
+    __syncwarp();
+    const int q_lo = mt == 0 ? 0 : np0, q_hi = mt == 0 ? np0 : np;
+    for (int q0 = q_lo; q0 < q_hi; q0 += 32) {
+      const int q = q0 + lane;
+      bool has[2] = {false, false};
+      int32_t tgt[2] = {0, 0};
+      uint64_t key[2] = {0ull, 0ull};
+      bool mark = false;
+      uint16_t pr = 0;
+      if (q < q_hi) {
+        pr = pairs[q];
+        const int i = pr >> 8, jj = pr & 0xFF;
+        const float g = G[(i & 15) * GSTR + jj];
+        const unsigned char* ti = row_ptr(i) + dpad * 2;
+        const unsigned char* tj = row_ptr(jj) + dpad * 2;
+        const float4 ai = *(const float4*)ti;
+        const float4 aj = *(const float4*)tj;
+        const float ri = *(const float*)(ti + 16), rj = *(const float*)(tj + 16);
+        tgt[0] = rc.cid[i];
+        tgt[1] = rc.cid[jj];
+        if (exact_rows(ri, rj, d)) {
+          const float dist = exact_value<METRIC>(g, ai, aj);
+          key[0] = make_key(dist, tgt[1]);
+          key[1] = make_key(dist, tgt[0]);
+          has[0] = key[0] < rc.kth[i];
+          has[1] = key[1] < rc.kth[jj];
+        } else {
+          float est;
+          const float E = bound_tc<METRIC>(g, ai, aj, d, &est);
+          mark = est - E <= fmaxf(key_dist(rc.kth[i]), key_dist(rc.kth[jj]));
+        }
+      }
+      emit_many<2>(a, fill, has, tgt, key);
+      // entries up to q0 + 31 are consumed, so the front of the list is free
+      const unsigned b = __ballot_sync(FULL, mark);
+      if (mark) pairs[nr + __popc(b & ((1u << lane) - 1u))] = pr;
+      nr += __popc(b);
+      __syncwarp();
+    }
+    __syncwarp();
+  }
+  if (lane == 0) reranked += (unsigned long long)nr;
+  for (int q0 = 0; q0 < nr; q0 += 32) {
+    const int q = q0 + lane;
+    bool hp = false, hq = false;
+    int32_t tp = 0, tq = 0;
+    uint64_t kp = 0, kq = 0;
+    if (q < nr) {
+      const uint16_t pr = pairs[q];
+      const int i = pr >> 8, jj = pr & 0xFF;
+      tp = rc.cid[i];
+      tq = rc.cid[jj];
+      const float4 ai = *(const float4*)(row_ptr(i) + dpad * 2);
+      const float4 aj = *(const float4*)(row_ptr(jj) + dpad * 2);
+      const float dist = canon_dist_global<METRIC>(a.rows.row(tp), a.rows.row(tq), d, ai.w, aj.w);
+      kp = make_key(dist, tq);
+      kq = make_key(dist, tp);
+      hp = kp < rc.kth[i];
+      hq = kq < rc.kth[jj];
+    }
+    emit_props(a, fill, hp, tp, kp, hq, tq, kq);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The kernel.  Per warp: NREC record slots, each with two mbarriers (record
+// landed, rows landed) completed by the lanes' cp.async arrivals; a FIFO ring
+// of R rows.  Rows of up to AHEAD nodes beyond the current one are in flight
+// whenever the ring has room.
+// ---------------------------------------------------------------------------
+constexpr int NREC = 4;
+constexpr int AHEAD = 1;
+
 template <int METRIC, bool TC>
 __global__ void __launch_bounds__(256, 1) k_join_ring(JoinArgs a, PipeArgs P) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -238,260 +425,142 @@ __global__ void __launch_bounds__(256, 1) k_join_ring(JoinArgs a, PipeArgs P) {
   unsigned char* my = smem + (size_t)warp * P.warp_bytes;
   unsigned char* ring = my;
   unsigned char* recs = ring + (size_t)R * stride;
-  uint16_t* pairs = (uint16_t*)(recs + 3 * RB);
+  uint64_t* recbar = (uint64_t*)(recs + (size_t)NREC * RB);
+  uint64_t* rowbar = recbar + NREC;
+  uint16_t* pairs = (uint16_t*)(rowbar + NREC);
   float* G = (float*)((unsigned char*)pairs + (((size_t)P.pair_cap * 2 + 15) & ~(size_t)15));
   int* fill = (int*)(smem + (size_t)W * P.warp_bytes);
   unsigned long long* red = (unsigned long long*)(fill + 4);
+  if (lane == 0) {
+    for (int x = 0; x < NREC; ++x) {
+      mbar_init(recbar + x, 32);
+      mbar_init(rowbar + x, 32);
+    }
+    fence_mbar_init();
+  }
   if (threadIdx.x == 0) {
     *fill = 0;
     red[0] = red[1] = red[2] = 0ull;
   }
   __syncthreads();
 
-  const int d = a.rows.d;
-  const int dpad = (d + 15) & ~15;
   const int cpr = P.row_bytes >> 4;  // 16-byte chunks per row
   const int64_t GW = (int64_t)gridDim.x * W;
   const int64_t g0 = (int64_t)blockIdx.x * W + warp;
+  const int64_t count = a.N > g0 ? (a.N - 1 - g0) / GW + 1 : 0;  // nodes of this warp
   unsigned long long evals = 0, gathered = 0, reranked = 0;
+  bool failed = false;
 
-  auto rec_slot = [&](int64_t j) { return recs + (size_t)(j % 3) * RB; };
-  auto fetch_rec = [&](int64_t u, unsigned char* dst) {
-    const unsigned char* src = P.rec + (size_t)u * RB;
+  auto slot_of = [&](int64_t j) { return (int)(j % NREC); };
+  auto par_of = [&](int64_t j) { return (uint32_t)((j / NREC) & 1); };
+  auto rec_at = [&](int64_t j) { return recs + (size_t)slot_of(j) * RB; };
+  auto fetch_rec = [&](int64_t j) {
+    const unsigned char* src = P.rec + (size_t)(g0 + j * GW) * RB;
+    unsigned char* dst = rec_at(j);
     for (int c = lane; c < (RB >> 4); c += 32) cp16(dst + c * 16, src + c * 16);
+    cp_arrive(recbar + slot_of(j));
   };
-  auto fetch_rows = [&](const unsigned char* rslot, int base, int M) {
-    const int32_t* cid = (const int32_t*)(rslot + 16);
-    const int total = M * cpr;
-    for (int c = lane; c < total; c += 32) {
-      const int r = (int)(((unsigned long long)c * P.cpr_inv) >> 32);
-      const int o = c - r * cpr;
-      int32_t id = cid[r];
-      if (id < 0 || id >= a.N) id = 0;
-      const unsigned char* src = TC ? (const unsigned char*)(P.Xe + (size_t)id * P.dx)
-                                    : (const unsigned char*)a.rows.row(id);
-      int slot = base + r;
-      if (slot >= R) slot -= R;
-      cp16(ring + (size_t)slot * stride + o * 16, src + o * 16);
-    }
-  };
-
-  int64_t u = g0;
-  int base = 0, M = 0, nn = 0;
-  if (u < a.N) {
-    fetch_rec(u, rec_slot(0));
-    cp_commit();
-    cp_wait_all();
-    __syncwarp();
-    const Rec r0 = read_rec(a, rec_slot(0), P.cap);
-    M = r0.M;
-    nn = r0.nn;
-    if (nn > 0 && M > 1) fetch_rows(rec_slot(0), 0, M);
-    cp_commit();
-    if (u + GW < a.N) fetch_rec(u + GW, rec_slot(1));
-    cp_commit();
-  }
-  for (int64_t j = 0; u < a.N; ++j, u += GW) {
-    cp_wait_all();
-    __syncwarp();
-    const Rec rc = read_rec(a, rec_slot(j), P.cap);
-    const bool staged = rc.nn > 0 && rc.M > 1;
-    // next node: rows now if they fit behind this node's, else after it
-    const bool has_next = u + GW < a.N;
-    int nbase = base + (staged ? M : 0);
-    if (nbase >= R) nbase -= R;
-    int Mn = 0, nnn = 0;
-    bool deferred = false;
-    if (has_next) {
-      const Rec rn = read_rec(a, rec_slot(j + 1), P.cap);
-      Mn = rn.M;
-      nnn = rn.nn;
-      if (nnn > 0 && Mn > 1) {
-        if ((staged ? M : 0) + Mn <= R)
-          fetch_rows(rec_slot(j + 1), nbase, Mn);
-        else
-          deferred = true;
+  auto fetch_rows = [&](int64_t j, int base, int M, bool staged) {
+    if (staged) {
+      const int32_t* cid = (const int32_t*)(rec_at(j) + 16);
+      const int total = M * cpr;
+      for (int c = lane; c < total; c += 32) {
+        const int r = (int)(((unsigned long long)c * P.cpr_inv) >> 32);
+        const int o = c - r * cpr;
+        int32_t id = cid[r];
+        if (id < 0 || id >= a.N) id = 0;
+        const unsigned char* src = TC ? (const unsigned char*)(P.Xe + (size_t)id * P.dx)
+                                      : (const unsigned char*)a.rows.row(id);
+        int slot = base + r;
+        if (slot >= R) slot -= R;
+        cp16(ring + (size_t)slot * stride + o * 16, src + o * 16);
       }
     }
-    cp_commit();
-    if (u + 2 * GW < a.N) fetch_rec(u + 2 * GW, rec_slot(j + 2));
-    cp_commit();
+    cp_arrive(rowbar + slot_of(j));
+  };
 
-    if (staged) {
+  // prologue: records of the first NREC - 1 nodes
+  for (int64_t j = 0; j < count && j < NREC - 1; ++j) fetch_rec(j);
+  int64_t next_rows = 0;     // next node whose rows are to be fetched
+  int64_t ring_head = 0, ring_tail = 0;  // rows of finished / fetched nodes
+  int base_of[NREC];         // ring base of each slot's node
+  int used_of[NREC];         // rows each slot's node occupies in the ring
+#pragma unroll
+  for (int x = 0; x < NREC; ++x) base_of[x] = used_of[x] = 0;
+
+  for (int64_t j = 0; j < count; ++j) {
+    // fetch rows of nodes j .. j + AHEAD while their records are in and the ring has room
+    while (next_rows < count && next_rows <= j + AHEAD) {
+      const int sl = slot_of(next_rows);
+      if (!mbar_wait_bounded(recbar + sl, par_of(next_rows), WAIT_LIMIT)) {
+        failed = true;
+        break;
+      }
+      __syncwarp();
+      const Rec rn = read_rec(a, rec_at(next_rows), P.cap);
+      const bool st = rn.nn > 0 && rn.M > 1;
+      const int need = st ? rn.M : 0;
+      if (next_rows > j && ring_tail - ring_head + need > R) break;  // no room yet
+      const int base = (int)(ring_tail % R);
+      fetch_rows(next_rows, base, rn.M, st);
+#pragma unroll
+      for (int x = 0; x < NREC; ++x)
+        if (x == sl) {
+          base_of[x] = base;
+          used_of[x] = need;
+        }
+      ring_tail += need;
+      ++next_rows;
+    }
+    if (failed) break;
+    const int sl = slot_of(j);
+    if (!mbar_wait_bounded(rowbar + sl, par_of(j), WAIT_LIMIT)) {
+      failed = true;
+      break;
+    }
+    __syncwarp();
+    // the record slot of node j - 1 is free: fetch the record of node j + NREC - 1
+    if (j + NREC - 1 < count) fetch_rec(j + NREC - 1);
+    const Rec rc = read_rec(a, rec_at(j), P.cap);
+    int base = 0, used = 0;
+#pragma unroll
+    for (int x = 0; x < NREC; ++x)
+      if (x == sl) {
+        base = base_of[x];
+        used = used_of[x];
+      }
+    if (rc.nn > 0 && rc.M > 1) {
       if (lane == 0) gathered += (unsigned long long)rc.M;
-      const int np = list_pairs(a, rc, pairs);
-      if (lane == 0) evals += (unsigned long long)np;
       auto row_ptr = [&](int r) {
         int slot = base + r;
         if (slot >= R) slot -= R;
-        return ring + (size_t)slot * stride;
+        return (const unsigned char*)(ring + (size_t)slot * stride);
       };
-      if (!TC) {
-        for (int q0 = 0; q0 < np;) {
-          const int pl = (np - q0 > 32) ? 2 : 1;
-          const float* ra[2];
-          const float* rb[2];
-          float acc[2] = {0.0f, 0.0f};
-          int pi[2], pj[2];
+      const int np = list_pairs(a, rc, pairs);
+      if (lane == 0) evals += (unsigned long long)np;
+      if (TC) {
+        // pairs with first index < 16 come first: their count is lane 16's offset
+        int np0 = 0;
+        {
+          const bool lo = lane < rc.M && rc.cid[lane] < a.n1;
+          const bool hi = lane + 32 < rc.M && rc.cid[lane + 32] < a.n1;
+          const uint64_t s1 =
+              (uint64_t)__ballot_sync(FULL, lo) | ((uint64_t)__ballot_sync(FULL, hi) << 32);
+          const int cnt = lane < 16 && lane < rc.nn ? __popcll(partner_mask(a.mode, lane, rc.M, s1)) : 0;
+          int sum = cnt;
 #pragma unroll
-          for (int t = 0; t < 2; ++t) {
-            const int q = q0 + t * 32 + lane;
-            const uint16_t pr = (t < pl && q < np) ? pairs[q] : pairs[q0];
-            pi[t] = pr >> 8;
-            pj[t] = pr & 0xFF;
-            ra[t] = (const float*)row_ptr(pi[t]);
-            rb[t] = (const float*)row_ptr(pj[t]);
-          }
-          if (pl == 2) {
-            for (int x = 0; x < d; x += 4) {
-#pragma unroll
-              for (int t = 0; t < 2; ++t) {
-                const float4 p4 = *reinterpret_cast<const float4*>(ra[t] + x);
-                const float4 q4 = *reinterpret_cast<const float4*>(rb[t] + x);
-                acc[t] = Canon<METRIC>::step(acc[t], p4.x, q4.x);
-                acc[t] = Canon<METRIC>::step(acc[t], p4.y, q4.y);
-                acc[t] = Canon<METRIC>::step(acc[t], p4.z, q4.z);
-                acc[t] = Canon<METRIC>::step(acc[t], p4.w, q4.w);
-              }
-            }
-          } else {
-            for (int x = 0; x < d; x += 4) {
-              const float4 p4 = *reinterpret_cast<const float4*>(ra[0] + x);
-              const float4 q4 = *reinterpret_cast<const float4*>(rb[0] + x);
-              acc[0] = Canon<METRIC>::step(acc[0], p4.x, q4.x);
-              acc[0] = Canon<METRIC>::step(acc[0], p4.y, q4.y);
-              acc[0] = Canon<METRIC>::step(acc[0], p4.z, q4.z);
-              acc[0] = Canon<METRIC>::step(acc[0], p4.w, q4.w);
-            }
-          }
-          bool has[4];
-          int32_t tgt[4];
-          uint64_t key[4];
-#pragma unroll
-          for (int t = 0; t < 2; ++t) {
-            const int q = q0 + t * 32 + lane;
-            const bool live = t < pl && q < np;
-            const int i = pi[t], jj = pj[t];
-            const float dist = canon_finish<METRIC>(acc[t], METRIC == COS ? rc.cn[i] : 0.f,
-                                                    METRIC == COS ? rc.cn[jj] : 0.f);
-            const int32_t ci = rc.cid[i], cj = rc.cid[jj];
-            key[2 * t] = make_key(dist, cj);
-            key[2 * t + 1] = make_key(dist, ci);
-            tgt[2 * t] = ci;
-            tgt[2 * t + 1] = cj;
-            has[2 * t] = live && key[2 * t] < rc.kth[i];
-            has[2 * t + 1] = live && key[2 * t + 1] < rc.kth[jj];
-          }
-          emit_many<4>(a, fill, has, tgt, key);
-          q0 += 32 * pl;
+          for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
+          np0 = sum;
         }
+        node_tc<METRIC>(a, rc, np, pairs, np0, row_ptr, G, fill, reranked);
       } else {
-        // Gram block rows 0..min(nn,32), all candidate columns, into G
-        const int mtiles = (rc.nn + 15) >> 4, ntiles = (rc.M + 7) >> 3;
-        for (int mt = 0; mt < mtiles; ++mt) {
-          const unsigned char* pa = row_ptr(mt * 16 + (lane & 15)) + (lane >> 4) * 16;
-          for (int nt = 0; nt < ntiles; nt += 2) {
-            const bool second = nt + 1 < ntiles;
-            float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
-            const unsigned char* pb0 = row_ptr(nt * 8 + (lane & 7)) + ((lane >> 3) & 1) * 16;
-            const unsigned char* pb1 =
-                row_ptr((second ? nt + 1 : nt) * 8 + (lane & 7)) + ((lane >> 3) & 1) * 16;
-#pragma unroll 8
-            for (int k0 = 0; k0 < dpad; k0 += 16) {
-              uint32_t x0, x1, x2, x3, y0, y1, w0, w1;
-              ldm_x4(x0, x1, x2, x3, pa + k0 * 2);
-              ldm_x2(y0, y1, pb0 + k0 * 2);
-              ldm_x2(w0, w1, pb1 + k0 * 2);
-              mma16816(c0, x0, x1, x2, x3, y0, y1);
-              mma16816(c1, x0, x1, x2, x3, w0, w1);
-            }
-            const int r0 = mt * 16 + (lane >> 2), col = nt * 8 + 2 * (lane & 3);
-            G[r0 * GSTR + col] = c0[0];
-            G[r0 * GSTR + col + 1] = c0[1];
-            G[(r0 + 8) * GSTR + col] = c0[2];
-            G[(r0 + 8) * GSTR + col + 1] = c0[3];
-            if (second) {
-              G[r0 * GSTR + col + 8] = c1[0];
-              G[r0 * GSTR + col + 9] = c1[1];
-              G[(r0 + 8) * GSTR + col + 8] = c1[2];
-              G[(r0 + 8) * GSTR + col + 9] = c1[3];
-            }
-          }
-        }
-        __syncwarp();
-        int nr = 0;
-        for (int q0 = 0; q0 < np; q0 += 32) {
-          const int q = q0 + lane;
-          bool has[2] = {false, false};
-          int32_t tgt[2] = {0, 0};
-          uint64_t key[2] = {0ull, 0ull};
-          bool mark = false;
-          uint16_t pr = 0;
-          if (q < np) {
-            pr = pairs[q];
-            const int i = pr >> 8, jj = pr & 0xFF;
-            const float g = G[i * GSTR + jj];
-            const unsigned char* ti = row_ptr(i) + dpad * 2;
-            const unsigned char* tj = row_ptr(jj) + dpad * 2;
-            const float4 ai = *(const float4*)ti;
-            const float4 aj = *(const float4*)tj;
-            const float ri = *(const float*)(ti + 16), rj = *(const float*)(tj + 16);
-            tgt[0] = rc.cid[i];
-            tgt[1] = rc.cid[jj];
-            if (exact_rows(ri, rj, d)) {
-              const float dist = exact_value<METRIC>(g, ai, aj);
-              key[0] = make_key(dist, tgt[1]);
-              key[1] = make_key(dist, tgt[0]);
-              has[0] = key[0] < rc.kth[i];
-              has[1] = key[1] < rc.kth[jj];
-            } else {
-              float est;
-              const float E = bound_tc<METRIC>(g, ai, aj, d, &est);
-              mark = est - E <= fmaxf(key_dist(rc.kth[i]), key_dist(rc.kth[jj]));
-            }
-          }
-          emit_many<2>(a, fill, has, tgt, key);
-          // re-rank list reuses the front of the pair list (already consumed)
-          const unsigned b = __ballot_sync(FULL, mark);
-          if (mark) pairs[nr + __popc(b & ((1u << lane) - 1u))] = pr;
-          nr += __popc(b);
-          __syncwarp();
-        }
-        if (lane == 0) reranked += (unsigned long long)nr;
-        for (int q0 = 0; q0 < nr; q0 += 32) {
-          const int q = q0 + lane;
-          bool hp = false, hq = false;
-          int32_t tp = 0, tq = 0;
-          uint64_t kp = 0, kq = 0;
-          if (q < nr) {
-            const uint16_t pr = pairs[q];
-            const int i = pr >> 8, jj = pr & 0xFF;
-            tp = rc.cid[i];
-            tq = rc.cid[jj];
-            const float4 ai = *(const float4*)(row_ptr(i) + dpad * 2);
-            const float4 aj = *(const float4*)(row_ptr(jj) + dpad * 2);
-            const float dist =
-                canon_dist_global<METRIC>(a.rows.row(tp), a.rows.row(tq), d, ai.w, aj.w);
-            kp = make_key(dist, tq);
-            kq = make_key(dist, tp);
-            hp = kp < rc.kth[i];
-            hq = kq < rc.kth[jj];
-          }
-          emit_props(a, fill, hp, tp, kp, hq, tq, kq);
-        }
+        node_fp32<METRIC>(a, rc, np, pairs, row_ptr, fill);
       }
     }
     __syncwarp();
-    if (deferred) {
-      // the next node did not fit behind this one: load it now into the same place
-      nbase = base;
-      fetch_rows(rec_slot(j + 1), nbase, Mn);
-      cp_commit();
-    }
-    base = nbase;
-    M = Mn;
-    nn = nnn;
+    ring_head += used;
   }
+  if (failed && lane == 0) atomicOr(&a.ctr->err, (unsigned long long)DERR_WAIT_TIMEOUT);
   cp_wait_all();
   for (int o = 16; o > 0; o >>= 1) {
     evals += __shfl_xor_sync(FULL, evals, o);
@@ -586,13 +655,14 @@ cudaError_t plan_pipe(int precision, int metric, int cap_new, int cap_old, int d
   const int cpr = P->row_bytes / 16;
   P->cpr_inv = (0x100000000ull + cpr - 1) / cpr;
   P->pair_cap = cap_new * (cap_new + cap_old);
-  size_t wb = (size_t)ring * P->row_stride + 3 * RB + (((size_t)P->pair_cap * 2 + 15) & ~(size_t)15);
-  if (tc) wb += (size_t)32 * GSTR * 4;
+  size_t wb = (size_t)ring * P->row_stride + (size_t)NREC * RB + 2 * NREC * 8 +
+              (((size_t)P->pair_cap * 2 + 15) & ~(size_t)15);
+  if (tc) wb += (size_t)16 * GSTR * 4;
   wb = (wb + 127) & ~(size_t)127;
   P->warp_bytes = (int)wb;
   // warps per block: as many as fit 200 KB (at most 8), one block per SM
   int w = 8;
-  while (w > 1 && (size_t)w * wb + 64 > 200 * 1024) --w;
+  while (w > 1 && (size_t)w * wb + 64 > 220 * 1024) --w;
   if ((size_t)w * wb + 64 > 227 * 1024) return cudaErrorInvalidValue;
   P->cw = w;
   P->nstages = 0;
