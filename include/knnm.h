@@ -100,6 +100,13 @@ int knnm_create(knnm_ctx** out, int device, void* cuda_stream);
 int knnm_destroy(knnm_ctx* ctx);
 /* Rebinds the context to another stream of the same device. */
 int knnm_set_stream(knnm_ctx* ctx, void* cuda_stream);
+/* Context options.  KNNM_OPT_GRAPHS (default 0): when 1, each local-join round
+ * of a whole-merge call (sampler, join, top-k update) is captured once into a
+ * CUDA graph and replayed, one graph launch per round.  Results are identical;
+ * knnm_stats then times each round as a whole (in ms_join; ms_sample and
+ * ms_update stay 0). */
+enum { KNNM_OPT_GRAPHS = 1 };
+int knnm_set_option(knnm_ctx* ctx, int option, int value);
 /* Message of the context's last failure ("" if none).  Owned by the context. */
 const char* knnm_last_error(const knnm_ctx* ctx);
 /* Static name of an error code. */
@@ -128,6 +135,110 @@ int knnm_merge_joint(knnm_ctx* ctx, const float* S1, int64_t n1, const int32_t* 
 /* NN-Descent build of S [n][d] (J-Merge with an empty graph); n >= K+1. */
 int knnm_build(knnm_ctx* ctx, const float* S, int64_t n, int d, const knnm_params* params,
                int32_t* out_ids, float* out_dists, knnm_stats* stats);
+
+/* Device scratch, in bytes, that one whole-merge call of these sizes takes
+ * from its context (all arrays on the device).  mode: 0 = S-Merge, 1 = J-Merge
+ * (n1 = 0 is the build).  Needs a context because the join configuration
+ * depends on the device. */
+int knnm_merge_scratch_bytes(knnm_ctx* ctx, int mode, int64_t n1, int64_t n2, int d,
+                             const knnm_params* params, uint64_t* bytes);
+
+/* ---------------------------------------------------------------------------
+ * Serving: J-Merge (Alg. 2, Sec. 3.2) applied to a stream of raw batches
+ * against a graph kept resident on one device.
+ *
+ * The server owns the resident vectors [capacity][d] and lists [capacity][K]
+ * (ids int32, canonical distances float32, sorted by (distance, id)).
+ * knnm_server_submit queues a batch and returns at once; worker slots, each
+ * with its own stream and scratch, take queued batches in submission order
+ * whenever a slot is idle and the memory the batch needs is free (the idle
+ * slot's own scratch plus the device's free memory, less hbm_reserve_bytes), so
+ * batches that arrive while others are on the device run concurrently with
+ * them.  Each batch r is one J-Merge:
+ *   - its snapshot is the resident state when it is admitted: rows
+ *     0..snapshot_rows-1 with their lists at that moment;
+ *   - it runs J-Merge(snapshot, batch) on private working lists with seed
+ *     H(seed, 0, 4, req_id, 0) (the library's counter-based hash), so its
+ *     result does not depend on what else is running;
+ *   - its commit appends the batch rows at rows commit_base.. (ids of the
+ *     batch in the result are moved there) and replaces each snapshot row's
+ *     list with the first K distinct entries of (current list, result list).
+ *     That update is commutative and associative, so the resident graph does
+ *     not depend on the order in which concurrent batches commit.
+ * Edges between two batches that are in flight at the same time are not
+ * searched for; later batches see both.  Each local-join round runs as one
+ * captured CUDA graph when use_graphs is set.
+ * ------------------------------------------------------------------------- */
+typedef struct knnm_server knnm_server;
+
+typedef struct {
+  int slots;                 /* concurrent batches (worker slots), >= 1 */
+  int use_graphs;            /* replay rounds as captured CUDA graphs */
+  int64_t capacity_rows;     /* resident rows the server can hold in total */
+  int64_t max_batch_rows;    /* largest batch submit accepts */
+  uint64_t hbm_reserve_bytes;/* device memory admission leaves free */
+} knnm_server_config;
+
+typedef struct {
+  uint64_t req_id;
+  int status;             /* KNNM_OK or the batch's error code */
+  int rounds;             /* local-join rounds of its J-Merge */
+  int64_t rows;           /* batch rows */
+  int64_t snapshot_rows;  /* resident rows its J-Merge saw */
+  int64_t snapshot_commits;/* commits applied before its snapshot */
+  int64_t commit_seq;     /* its position in the commit order (0-based) */
+  int64_t commit_base;    /* resident row of its first batch row */
+  int64_t dist_evals;     /* pairs compared over all rounds */
+  int slot;               /* worker slot that ran it */
+  double queue_ms;        /* submit -> admission */
+  double run_ms;          /* admission -> commit done */
+  double latency_ms;      /* submit -> commit done */
+} knnm_request_info;
+
+typedef struct {
+  int64_t submitted, completed, failed;
+  int64_t resident_rows;   /* rows committed so far */
+  int64_t rows_completed;  /* batch rows of completed requests */
+  int64_t max_concurrent;  /* most batches in flight at one time */
+  double p50_ms, p99_ms;   /* latency percentiles of completed requests */
+  double busy_s;           /* first admission -> last completion, seconds */
+} knnm_server_stats;
+
+/* Creates a server on `device` from S [n][d] (host or device) and its graph G
+ * [n][K] (ids in 0..n-1, host or device); the lists' distances are computed
+ * canonically and sorted.  params->k, metric, precision, max_iters,
+ * sample_rate, keep_ratio, delta and seed apply to every batch.  The server
+ * allocates the resident arrays for cfg->capacity_rows rows up front and
+ * starts cfg->slots worker threads.  n >= K+1. */
+int knnm_server_create(int device, const float* S, int64_t n, const int32_t* G, int d,
+                       const knnm_params* params, const knnm_server_config* cfg,
+                       knnm_server** out);
+/* Queues `batch` [rows][d] (host or device) under req_id, which must be new.
+ * The caller keeps the batch valid until knnm_server_wait for req_id returns.
+ * KNNM_ERR_NOMEM when the batch would not fit in capacity_rows or
+ * max_batch_rows; rows >= K - floor(r*K). */
+int knnm_server_submit(knnm_server* srv, const float* batch, int64_t rows, uint64_t req_id);
+/* Waits up to timeout_ms (< 0: no limit) for req_id.  On completion copies
+ * the batch rows' merged lists (resident ids) into ids_out/dists_out [rows][K]
+ * (host or device; either may be NULL), fills *info (may be NULL), forgets the
+ * request and returns its status.  KNNM_ERR_TIMEOUT when it has not completed
+ * in time (the request stays queued or running); KNNM_ERR_INVALID for an
+ * unknown id. */
+int knnm_server_wait(knnm_server* srv, uint64_t req_id, int timeout_ms, int32_t* ids_out,
+                     float* dists_out, knnm_request_info* info);
+/* Waits until no request is queued or running (timeout as above). */
+int knnm_server_drain(knnm_server* srv, int timeout_ms);
+int knnm_server_get_stats(knnm_server* srv, knnm_server_stats* out);
+/* Copies the first *rows resident rows (all of them if *rows < 0 or larger;
+ * *rows is set to the count copied) into vectors [rows][d], ids and dists
+ * [rows][K] (host or device; any may be NULL).  Waits for pending commits;
+ * call it after knnm_server_drain for a state no commit is racing. */
+int knnm_server_resident(knnm_server* srv, int64_t* rows, float* vectors, int32_t* ids,
+                         float* dists);
+/* Message of the server's last failure ("" if none). */
+const char* knnm_server_last_error(const knnm_server* srv);
+/* Drains, stops the workers and frees everything. */
+int knnm_server_destroy(knnm_server* srv);
 
 /* ---------------------------------------------------------------------------
  * Round steps.  Device pointers only.  Working state of a merge of N rows is

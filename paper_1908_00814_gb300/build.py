@@ -52,7 +52,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> Path:
     with ThreadPoolExecutor(max_workers=len(sources())) as ex:
         objs = list(ex.map(compile_one, sources()))
     tmp = LIB.with_suffix(f".{os.getpid()}.tmp")
-    cmd = [NVCC, "-shared", *ARCH, "-o", str(tmp), *map(str, objs)]
+    cmd = [NVCC, "-shared", *ARCH, "-o", str(tmp), *map(str, objs), "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -20,6 +20,8 @@ struct knnm_ctx {
   DevCounters* host_ctr = nullptr;  // pinned
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t rev[4] = {nullptr, nullptr, nullptr, nullptr};  // per-round phases
+  int use_graphs = 0;  // replay each round as one captured CUDA graph
+  cudaStream_t cap_stream = nullptr;  // private stream the round graph is captured on
   char err[512] = {0};
 };
 
@@ -164,8 +166,10 @@ struct MergeIn {
   int d;
 };
 
+// With size_only set, nothing runs: the scratch the call would take (every
+// array on the device) is written there.
 int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32_t* out_ids,
-              float* out_dists, knnm_stats* stats) {
+              float* out_dists, knnm_stats* stats, uint64_t* size_only = nullptr) {
   auto t_wall0 = std::chrono::steady_clock::now();
   if (!ctx) return KNNM_ERR_INVALID;
   ctx->err[0] = 0;
@@ -178,21 +182,22 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   if (d < 1) return fail(ctx, KNNM_ERR_INVALID, "d=%d", d);
   if (in.n1 < 0 || in.n2 < 0 || N > 0x7FFFFFFFLL)
     return fail(ctx, KNNM_ERR_INVALID, "row counts out of range");
-  if (!out_ids || !out_dists) return fail(ctx, KNNM_ERR_INVALID, "output arrays are NULL");
+  if (!size_only && (!out_ids || !out_dists))
+    return fail(ctx, KNNM_ERR_INVALID, "output arrays are NULL");
   if (in.mode == SYMMETRIC) {
     if (in.n1 < K + 1 || in.n2 < K + 1)
       return fail(ctx, KNNM_ERR_INVALID, "S-Merge needs n1, n2 >= k+1 (n1=%lld n2=%lld k=%d)",
                   (long long)in.n1, (long long)in.n2, K);
     if (in.n1 < D.Kr || in.n2 < D.Kr)
       return fail(ctx, KNNM_ERR_INVALID, "each set needs at least k - floor(r*k) = %d rows", D.Kr);
-    if (!in.S1 || !in.S2 || !in.G1 || !in.G2)
+    if (!size_only && (!in.S1 || !in.S2 || !in.G1 || !in.G2))
       return fail(ctx, KNNM_ERR_INVALID, "NULL input array");
   } else {
     if (N < K + 1) return fail(ctx, KNNM_ERR_INVALID, "n1+n2 must be >= k+1");
-    if (in.n1 > 0 && (in.n1 < K + 1 || in.n2 < D.Kr || !in.G1 || !in.S1))
+    if (in.n1 > 0 && (in.n1 < K + 1 || in.n2 < D.Kr || (!size_only && (!in.G1 || !in.S1))))
       return fail(ctx, KNNM_ERR_INVALID,
                   "J-Merge needs n1 >= k+1, n2 >= k - floor(r*k) and G1 when n1 > 0");
-    if (in.n2 > 0 && !in.S2) return fail(ctx, KNNM_ERR_INVALID, "S_new is NULL");
+    if (in.n2 > 0 && !in.S2 && !size_only) return fail(ctx, KNNM_ERR_INVALID, "S_new is NULL");
   }
   const int precision = (params->precision == KNNM_BF16_RERANK && params->metric != KNNM_L1)
                             ? KNNM_BF16_RERANK
@@ -204,15 +209,15 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   KNNM_CUDA(cudaSetDevice(ctx->device));
 
   // Where does each array live?
-  const bool s1_dev = in.n1 == 0 || is_device_ptr(in.S1);
-  const bool s2_dev = in.n2 == 0 || is_device_ptr(in.S2);
-  const bool g1_dev = !in.G1 || is_device_ptr(in.G1);
-  const bool g2_dev = !in.G2 || is_device_ptr(in.G2);
-  const bool oi_dev = is_device_ptr(out_ids);
-  const bool od_dev = is_device_ptr(out_dists);
+  const bool s1_dev = size_only || in.n1 == 0 || is_device_ptr(in.S1);
+  const bool s2_dev = size_only || in.n2 == 0 || is_device_ptr(in.S2);
+  const bool g1_dev = size_only || !in.G1 || is_device_ptr(in.G1);
+  const bool g2_dev = size_only || !in.G2 || is_device_ptr(in.G2);
+  const bool oi_dev = size_only || is_device_ptr(out_ids);
+  const bool od_dev = size_only || is_device_ptr(out_dists);
 
   // rows staged from the caller's device arrays need 16-byte alignment for bulk copies
-  const bool rows_aligned = d % 4 == 0 && (!s1_dev || !s2_dev ||
+  const bool rows_aligned = d % 4 == 0 && (size_only || !s1_dev || !s2_dev ||
                                            ((in.n1 == 0 || aligned16(in.S1)) &&
                                             (in.n2 == 0 || aligned16(in.S2))));
   JoinPath jp;
@@ -246,6 +251,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     int32_t* rcnt;
     unsigned long long *roffs, *rtile, *rtotal;
     uint64_t* rbucket;
+    int* tdev;
   } P;
   auto carve = [&](Carver& c) {
     P.X = (!s1_dev || !s2_dev) ? c.take<float>((size_t)N * d) : nullptr;
@@ -261,6 +267,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     P.rbucket = c.take<uint64_t>((size_t)N * K);
     P.rtile = c.take<unsigned long long>((size_t)(2 * N + 1023) / 1024 + 1);
     P.rtotal = c.take<unsigned long long>(1);
+    P.tdev = c.take<int>(1);
     P.flags = c.take<uint8_t>((size_t)N * K);
     P.new_ids = c.take<int32_t>((size_t)N * D.cap_new);
     P.new_cnt = c.take<int32_t>((size_t)N);
@@ -284,6 +291,10 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   };
   Carver sizer;
   carve(sizer);
+  if (size_only) {
+    *size_only = sizer.off;
+    return KNNM_OK;
+  }
   rc = ensure_arena(ctx, sizer.off);
   if (rc) return rc;
   Carver real;
@@ -429,39 +440,95 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   KNNM_CUDA(cudaMemsetAsync(P.rcnt, 0, (size_t)N * 8, st));
 
   const double stop_at = (double)params->delta * (double)N * (double)K;
-  for (int t = 1; t <= params->max_iters; ++t) {
-    KNNM_CUDA(cudaMemsetAsync(P.ctr, 0, sizeof(DevCounters), st));
-    KNNM_CUDA(cudaMemsetAsync(&P.ctr->err_row, 0xFF, 8, st));
+  // One round: counters reset, sampler, join, bucketed update (plus, in graph
+  // mode, the round-index bump that the next replay reads).
+  // Phase events are recorded only when launching directly; a replayed graph
+  // is timed as a whole.
+  auto enqueue_round = [&](int t, cudaStream_t rs) -> int {
+    const bool timed = t > 0;
+    KNNM_CUDA(cudaMemsetAsync(P.ctr, 0, sizeof(DevCounters), rs));
+    KNNM_CUDA(cudaMemsetAsync(&P.ctr->err_row, 0xFF, 8, rs));
     sa.t = t;
-    KNNM_CUDA(cudaEventRecord(ctx->rev[0], st));
-    KNNM_CUDA(launch_sample(sa, st));
-    KNNM_CUDA(cudaEventRecord(ctx->rev[1], st));
+    if (timed) KNNM_CUDA(cudaEventRecord(ctx->rev[0], rs));
+    KNNM_CUDA(launch_sample(sa, rs));
+    if (timed) KNNM_CUDA(cudaEventRecord(ctx->rev[1], rs));
     if (jp.pipe)
-      KNNM_CUDA(launch_pipe(precision, ja, jp.pa, jp.smem, jp.grid, st));
+      KNNM_CUDA(launch_pipe(precision, ja, jp.pa, jp.smem, jp.grid, rs));
     else
-      KNNM_CUDA(launch_join(precision, ja, jp.plan, st));
-    KNNM_CUDA(cudaEventRecord(ctx->rev[2], st));
+      KNNM_CUDA(launch_join(precision, ja, jp.plan, rs));
+    if (timed) KNNM_CUDA(cudaEventRecord(ctx->rev[2], rs));
     KNNM_CUDA(launch_bucket_update(ma, P.prop_tgt, P.prop_key, P.region_cnt, region_cap,
-                                   regions, P.tile_sum, P.total, st));
-    KNNM_CUDA(cudaEventRecord(ctx->rev[3], st));
+                                   regions, P.tile_sum, P.total, rs));
+    if (timed) KNNM_CUDA(cudaEventRecord(ctx->rev[3], rs));
+    if (sa.t_dev) KNNM_CUDA(launch_bump_int(P.tdev, rs));
+    KNNM_CUDA(cudaMemcpyAsync(ctx->host_ctr, P.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost,
+                              rs));
+    return KNNM_OK;
+  };
+  cudaGraphExec_t round_exec = nullptr;
+  if (ctx->use_graphs && params->max_iters > 0) {
+    sa.t_dev = P.tdev;
+    KNNM_CUDA(launch_set_int(P.tdev, 1, st));
+    cudaGraph_t graph = nullptr;
+    // captured on the context's own stream (the caller's may be the legacy
+    // default stream, which cannot capture); replayed on the caller's stream
+    if (!ctx->cap_stream)
+      KNNM_CUDA(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    KNNM_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int crc = enqueue_round(0, ctx->cap_stream);  // t is read from P.tdev
+    cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    if (crc) {
+      if (graph) cudaGraphDestroy(graph);
+      return crc;
+    }
+    if (ce != cudaSuccess) return fail(ctx, KNNM_ERR_CUDA, "round capture: %s", cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&round_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess)
+      return fail(ctx, KNNM_ERR_CUDA, "round graph instantiate: %s", cudaGetErrorString(ce));
+  }
+  for (int t = 1; t <= params->max_iters; ++t) {
+    if (round_exec) {
+      cudaEventRecord(ctx->rev[0], st);
+      cudaError_t le = cudaGraphLaunch(round_exec, st);
+      cudaEventRecord(ctx->rev[3], st);
+      if (le != cudaSuccess) {
+        cudaGraphExecDestroy(round_exec);
+        return fail(ctx, KNNM_ERR_CUDA, "round graph launch: %s", cudaGetErrorString(le));
+      }
+    } else {
+      rc = enqueue_round(t, st);
+      if (rc) return rc;
+    }
     launches += 12;
-    KNNM_CUDA(cudaMemcpyAsync(ctx->host_ctr, P.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
-    KNNM_CUDA(cudaStreamSynchronize(st));
+    cudaError_t se = cudaStreamSynchronize(st);
+    if (se != cudaSuccess) {
+      if (round_exec) cudaGraphExecDestroy(round_exec);
+      return fail(ctx, KNNM_ERR_CUDA, "round %d: %s", t, cudaGetErrorString(se));
+    }
     const DevCounters& h = *ctx->host_ctr;
-    if (h.err)
+    if (h.err) {
+      if (round_exec) cudaGraphExecDestroy(round_exec);
       return fail(ctx, KNNM_ERR_DEVICE, "round %d: device error bits 0x%llx (row %llu)", t,
                   (unsigned long long)h.err, (unsigned long long)h.err_row);
+    }
     local.updates[t - 1] = (int64_t)h.updates;
     local.dist_evals[t - 1] = (int64_t)h.dist_evals;
     local.proposals[t - 1] = (int64_t)h.proposals;
     local.reranked[t - 1] = (int64_t)h.reranked;
     local.gathered[t - 1] = (int64_t)h.gathered;
-    cudaEventElapsedTime(&local.ms_sample[t - 1], ctx->rev[0], ctx->rev[1]);
-    cudaEventElapsedTime(&local.ms_join[t - 1], ctx->rev[1], ctx->rev[2]);
-    cudaEventElapsedTime(&local.ms_update[t - 1], ctx->rev[2], ctx->rev[3]);
+    if (round_exec) {
+      cudaEventElapsedTime(&local.ms_join[t - 1], ctx->rev[0], ctx->rev[3]);
+    } else {
+      cudaEventElapsedTime(&local.ms_sample[t - 1], ctx->rev[0], ctx->rev[1]);
+      cudaEventElapsedTime(&local.ms_join[t - 1], ctx->rev[1], ctx->rev[2]);
+      cudaEventElapsedTime(&local.ms_update[t - 1], ctx->rev[2], ctx->rev[3]);
+    }
+    cudaGetLastError();  // a timing query that failed leaves no error behind
     local.rounds = t;
     if ((double)h.updates <= stop_at) break;
   }
+  if (round_exec) cudaGraphExecDestroy(round_exec);
   KNNM_CUDA(cudaEventRecord(ctx->ev[2], st));
   int32_t* oi = P.oi ? P.oi : out_ids;
   float* od = P.od ? P.od : out_dists;
@@ -537,6 +604,7 @@ extern "C" int knnm_destroy(knnm_ctx* c) {
     if (e) cudaEventDestroy(e);
   for (auto& e : c->rev)
     if (e) cudaEventDestroy(e);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
   return KNNM_OK;
 }
@@ -548,6 +616,15 @@ extern "C" int knnm_set_stream(knnm_ctx* c, void* s) {
 }
 
 extern "C" const char* knnm_last_error(const knnm_ctx* c) { return c ? c->err : "no context"; }
+
+extern "C" int knnm_set_option(knnm_ctx* c, int option, int value) {
+  if (!c) return KNNM_ERR_INVALID;
+  if (option == KNNM_OPT_GRAPHS) {
+    c->use_graphs = value ? 1 : 0;
+    return KNNM_OK;
+  }
+  return KNNM_ERR_INVALID;
+}
 
 extern "C" const char* knnm_strerror(int code) {
   switch (code) {
@@ -599,6 +676,22 @@ extern "C" int knnm_build(knnm_ctx* ctx, const float* S, int64_t n, int d,
   MergeIn in{JOINT, nullptr, 0, nullptr, S, n, nullptr, d};
   return run_merge(ctx, in, params, out_ids, out_dists, stats);
 }
+
+extern "C" int knnm_merge_scratch_bytes(knnm_ctx* ctx, int mode, int64_t n1, int64_t n2, int d,
+                                        const knnm_params* params, uint64_t* bytes) {
+  if (!ctx || !bytes || (mode != SYMMETRIC && mode != JOINT)) return KNNM_ERR_INVALID;
+  // the sizes are what count; the arrays are taken to be on the device
+  MergeIn in{mode, nullptr, n1, nullptr, nullptr, n2, nullptr, d};
+  return run_merge(ctx, in, params, nullptr, nullptr, nullptr, bytes);
+}
+
+namespace knnm {
+
+int ctx_reserve(knnm_ctx* ctx, uint64_t bytes) { return ensure_arena(ctx, (size_t)bytes); }
+
+uint64_t ctx_scratch_bytes(const knnm_ctx* ctx) { return ctx ? ctx->arena_bytes : 0; }
+
+}  // namespace knnm
 
 // ---------------------------------------------------------------------------
 // Round steps (device pointers)

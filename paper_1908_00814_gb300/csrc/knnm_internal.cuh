@@ -6,6 +6,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+struct knnm_ctx;
+
 namespace knnm {
 
 // ---------------------------------------------------------------------------
@@ -336,6 +338,7 @@ struct SampleArgs {
   int K, s;
   uint64_t seed;
   int t;
+  const int* t_dev = nullptr;  // when set, the round index is read from here (graph replay)
   const uint64_t* keys;   // [N][K]
   uint8_t* flags;         // [N][K], sampled entries flipped to old
   uint64_t* prev_keys;    // [N][K] snapshot for the finalize step (may be null)
@@ -360,6 +363,23 @@ struct SampleArgs {
   unsigned long long* total = nullptr;     // scan total
 };
 cudaError_t launch_sample(const SampleArgs& a, cudaStream_t st);
+// Context internals used by the serving loop (knnm_api.cu): grow the
+// context's scratch to at least `bytes`; bytes it holds now.
+int ctx_reserve(knnm_ctx* ctx, uint64_t bytes);
+uint64_t ctx_scratch_bytes(const knnm_ctx* ctx);
+
+// Canonical distances of the K listed neighbours of each row, sorted by
+// (distance, id); rows with an id out of range, self or repeated raise an error.
+cudaError_t launch_list_dists(Rows rows, int64_t n, const int32_t* G, int K, int metric,
+                              const float* norms, int32_t* ids, float* dists, DevCounters* ctr,
+                              cudaStream_t st);
+// Serving commit of one request's merged rows into the resident lists.
+cudaError_t launch_commit(int64_t n_snap, int64_t rows, int K, int32_t* res_ids,
+                          float* res_dists, const int32_t* out_ids, const float* out_dists,
+                          int64_t base, cudaStream_t st);
+// *p = v (one thread); *p += 1 (one thread).
+cudaError_t launch_set_int(int* p, int v, cudaStream_t st);
+cudaError_t launch_bump_int(int* p, cudaStream_t st);
 
 // Candidate record of one node, read by the pipelined join with one bulk copy:
 //   int32 {nn, no, 0, 0} | int32 ids[cap] (new first) | uint64 kth[cap] | float cn[cap]

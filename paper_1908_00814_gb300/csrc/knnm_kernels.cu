@@ -5,6 +5,8 @@
 //
 // Lists are packed 64-bit keys (distance order bits << 32 | id), K <= 32, so a
 // whole list fits one warp with one entry per lane.
+#include <atomic>
+
 #include "knnm_internal.cuh"
 
 namespace knnm {
@@ -26,12 +28,14 @@ __device__ __forceinline__ void raise_err(DevCounters* c, unsigned bits, int64_t
 }
 
 int grid_for_warps(int64_t nwarps) {
-  static int sms = 0;
+  static std::atomic<int> sms_cached{0};  // launches come from several host threads
+  int sms = sms_cached.load(std::memory_order_relaxed);
   if (!sms) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 148;
+    sms_cached.store(sms, std::memory_order_relaxed);
   }
   int64_t blocks = (nwarps + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
   int64_t cap = (int64_t)sms * 8;  // persistent: at most 8 resident blocks per SM
@@ -177,6 +181,31 @@ __global__ void __launch_bounds__(BLOCK) k_init(InitArgs a) {
   }
 }
 
+template <int METRIC>
+__global__ void __launch_bounds__(BLOCK) k_list_dists(Rows R, int64_t n, const int32_t* G, int K,
+                                                      const float* norms, int vec4, int32_t* ids,
+                                                      float* dists, DevCounters* ctr) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
+  for (int64_t i = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5); i < n;
+       i += nwarps) {
+    const int32_t g = lane < K ? G[(size_t)i * K + lane] : -1;
+    const bool bad = lane < K && (g < 0 || g >= n || g == i);
+    uint64_t key = KEY_EMPTY;
+    if (lane < K && !bad) key = make_key(dist_rows<METRIC>(R, i, g, norms, vec4), g);
+    key = warp_sort32(key);
+    // a repeated id has a bit-identical distance, so its copies end up adjacent
+    const uint64_t prev = __shfl_up_sync(FULL, key, 1);
+    const bool dup = lane > 0 && lane < K && key != KEY_EMPTY && key == prev;
+    if (__any_sync(FULL, bad) && lane == 0) raise_err(ctr, DERR_BAD_ID, i);
+    if (__any_sync(FULL, dup) && lane == 0) raise_err(ctr, DERR_DUP_ID, i);
+    if (lane < K) {
+      ids[(size_t)i * K + lane] = key_id(key);
+      dists[(size_t)i * K + lane] = key_dist(key);
+    }
+  }
+}
+
 __global__ void k_norms(Rows R, int64_t N, float* norms) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < N) norms[i] = canon_norm_global(R.row(i), R.d);
@@ -191,6 +220,7 @@ __global__ void __launch_bounds__(BLOCK) k_sample_fwd(SampleArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
   const int K = a.K, s = a.s;
+  const uint64_t t = (uint64_t)(a.t_dev ? *a.t_dev : a.t);
   for (int64_t u = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5); u < a.N;
        u += nwarps) {
     uint64_t key = lane < K ? a.keys[(size_t)u * K + lane] : KEY_EMPTY;
@@ -199,7 +229,7 @@ __global__ void __launch_bounds__(BLOCK) k_sample_fwd(SampleArgs a) {
     const int32_t v = key_id(key);
     const bool isnew = lane < K && f == FLAG_NEW;
     const bool isold = lane < K && f != FLAG_NEW;
-    const uint64_t pre = hash_prefix(a.seed, (uint64_t)a.t, STREAM_FWD_NEW, (uint64_t)u);
+    const uint64_t pre = hash_prefix(a.seed, t, STREAM_FWD_NEW, (uint64_t)u);
     const uint64_t sk = isnew ? sampling_key(pre, v) : KEY_EMPTY;
     int rank = 0;
     for (int m = 0; m < K; ++m) rank += (__shfl_sync(FULL, sk, m) < sk) ? 1 : 0;
@@ -219,11 +249,11 @@ __global__ void __launch_bounds__(BLOCK) k_sample_fwd(SampleArgs a) {
     } else {
       if (sel)
         slots_insert(a.rev_new + (size_t)v * s, s,
-                     sampling_key(hash_prefix(a.seed, (uint64_t)a.t, STREAM_REV_NEW, (uint64_t)v),
+                     sampling_key(hash_prefix(a.seed, t, STREAM_REV_NEW, (uint64_t)v),
                                   (int32_t)u));
       if (isold)
         slots_insert(a.rev_old + (size_t)v * s, s,
-                     sampling_key(hash_prefix(a.seed, (uint64_t)a.t, STREAM_REV_OLD, (uint64_t)v),
+                     sampling_key(hash_prefix(a.seed, t, STREAM_REV_OLD, (uint64_t)v),
                                   (int32_t)u));
     }
   }
@@ -234,20 +264,21 @@ __global__ void __launch_bounds__(BLOCK) k_sample_fwd(SampleArgs a) {
 __global__ void __launch_bounds__(BLOCK) k_sample_scatter(SampleArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
+  const uint64_t t = (uint64_t)(a.t_dev ? *a.t_dev : a.t);
   for (int64_t u = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5); u < a.N;
        u += nwarps) {
     const int nf = a.new_cnt[u], of = a.old_cnt[u];
     if (lane < nf) {
       const int32_t v = a.new_ids[(size_t)u * a.cap_new + lane];
-      const uint64_t key = sampling_key(
-          hash_prefix(a.seed, (uint64_t)a.t, STREAM_REV_NEW, (uint64_t)v), (int32_t)u);
+      const uint64_t key =
+          sampling_key(hash_prefix(a.seed, t, STREAM_REV_NEW, (uint64_t)v), (int32_t)u);
       const int pos = atomicSub(&a.rcnt[2 * (size_t)v], 1) - 1;
       a.rbucket[a.roffs[2 * (size_t)v] + (uint64_t)pos] = key;
     }
     if (lane < of) {
       const int32_t v = a.old_ids[(size_t)u * a.cap_old + lane];
-      const uint64_t key = sampling_key(
-          hash_prefix(a.seed, (uint64_t)a.t, STREAM_REV_OLD, (uint64_t)v), (int32_t)u);
+      const uint64_t key =
+          sampling_key(hash_prefix(a.seed, t, STREAM_REV_OLD, (uint64_t)v), (int32_t)u);
       const int pos = atomicSub(&a.rcnt[2 * (size_t)v + 1], 1) - 1;
       a.rbucket[a.roffs[2 * (size_t)v + 1] + (uint64_t)pos] = key;
     }
@@ -612,6 +643,57 @@ __global__ void __launch_bounds__(BLOCK) k_final(int64_t N, int K, const uint64_
   }
 }
 
+// Serving commit: resident rows v < n_snap become the first K distinct keys of
+// (resident list, request row); request rows for the new points are written
+// to base + r.  Request ids >= n_snap are remapped to base + (id - n_snap).
+__global__ void __launch_bounds__(BLOCK) k_commit(int64_t n_snap, int64_t rows, int K,
+                                                  int32_t* res_ids, float* res_dists,
+                                                  const int32_t* out_ids, const float* out_dists,
+                                                  int64_t base) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
+  for (int64_t v = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5); v < n_snap + rows;
+       v += nwarps) {
+    uint64_t e1 = KEY_EMPTY;
+    if (lane < K) {
+      int32_t id = out_ids[(size_t)v * K + lane];
+      if (id >= n_snap) id = (int32_t)(base + (id - n_snap));
+      e1 = make_key(out_dists[(size_t)v * K + lane], id);
+    }
+    const int64_t dst = v < n_snap ? v : base + (v - n_snap);
+    if (v >= n_snap) {
+      if (lane < K) {
+        res_ids[(size_t)dst * K + lane] = key_id(e1);
+        res_dists[(size_t)dst * K + lane] = key_dist(e1);
+      }
+      continue;
+    }
+    uint64_t e0 = lane < K ? make_key(res_dists[(size_t)v * K + lane], res_ids[(size_t)v * K + lane])
+                           : KEY_EMPTY;
+    warp_sort64(e0, e1);
+    uint64_t p0 = __shfl_up_sync(FULL, e0, 1);
+    uint64_t p1 = __shfl_up_sync(FULL, e1, 1);
+    const uint64_t last0 = __shfl_sync(FULL, e0, 31);
+    if (lane == 0) p1 = last0;
+    const bool k0 = e0 != KEY_EMPTY && (lane == 0 || e0 != p0);
+    const bool k1 = e1 != KEY_EMPTY && e1 != p1;
+    const unsigned b0 = __ballot_sync(FULL, k0), b1 = __ballot_sync(FULL, k1);
+    const int pos0 = __popc(b0 & lanemask_lt());
+    const int pos1 = __popc(b0) + __popc(b1 & lanemask_lt());
+    if (k0 && pos0 < K) {
+      res_ids[(size_t)v * K + pos0] = key_id(e0);
+      res_dists[(size_t)v * K + pos0] = key_dist(e0);
+    }
+    if (k1 && pos1 < K) {
+      res_ids[(size_t)v * K + pos1] = key_id(e1);
+      res_dists[(size_t)v * K + pos1] = key_dist(e1);
+    }
+  }
+}
+
+__global__ void k_set_int(int* p, int v) { *p = v; }
+__global__ void k_bump_int(int* p) { *p += 1; }
+
 __global__ void k_pack(int64_t count, const int32_t* ids, const float* dists, uint64_t* keys) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < count) keys[i] = ids[i] < 0 ? KEY_EMPTY : make_key(dists[i], ids[i]);
@@ -726,6 +808,39 @@ cudaError_t launch_bucket_update(const MergeArgs& a, const int32_t* prop_tgt,
 cudaError_t launch_final(int64_t N, int K, const uint64_t* keys, int Kr, const uint64_t* rear,
                          int32_t* out_ids, float* out_dists, cudaStream_t st) {
   k_final<<<grid_for_warps(N), BLOCK, 0, st>>>(N, K, keys, Kr, rear, out_ids, out_dists);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_list_dists(Rows rows, int64_t n, const int32_t* G, int K, int metric,
+                              const float* norms, int32_t* ids, float* dists, DevCounters* ctr,
+                              cudaStream_t st) {
+  const int grid = grid_for_warps(n);
+  const int vec4 = (rows.d % 4 == 0 && ((uintptr_t)rows.X1 & 15u) == 0 &&
+                    ((uintptr_t)rows.X2 & 15u) == 0) ? 1 : 0;
+  switch (metric) {
+    case L2: k_list_dists<L2><<<grid, BLOCK, 0, st>>>(rows, n, G, K, norms, vec4, ids, dists, ctr); break;
+    case IP: k_list_dists<IP><<<grid, BLOCK, 0, st>>>(rows, n, G, K, norms, vec4, ids, dists, ctr); break;
+    case COS: k_list_dists<COS><<<grid, BLOCK, 0, st>>>(rows, n, G, K, norms, vec4, ids, dists, ctr); break;
+    default: k_list_dists<L1><<<grid, BLOCK, 0, st>>>(rows, n, G, K, norms, vec4, ids, dists, ctr); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_commit(int64_t n_snap, int64_t rows, int K, int32_t* res_ids,
+                          float* res_dists, const int32_t* out_ids, const float* out_dists,
+                          int64_t base, cudaStream_t st) {
+  k_commit<<<grid_for_warps(n_snap + rows), BLOCK, 0, st>>>(n_snap, rows, K, res_ids, res_dists,
+                                                           out_ids, out_dists, base);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_int(int* p, int v, cudaStream_t st) {
+  k_set_int<<<1, 1, 0, st>>>(p, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bump_int(int* p, cudaStream_t st) {
+  k_bump_int<<<1, 1, 0, st>>>(p);
   return cudaGetLastError();
 }
 

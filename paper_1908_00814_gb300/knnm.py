@@ -56,6 +56,35 @@ class Stats(ctypes.Structure):
         return out
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int), ("use_graphs", ctypes.c_int),
+                ("capacity_rows", ctypes.c_int64), ("max_batch_rows", ctypes.c_int64),
+                ("hbm_reserve_bytes", ctypes.c_uint64)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("req_id", ctypes.c_uint64), ("status", ctypes.c_int), ("rounds", ctypes.c_int),
+                ("rows", ctypes.c_int64), ("snapshot_rows", ctypes.c_int64),
+                ("snapshot_commits", ctypes.c_int64), ("commit_seq", ctypes.c_int64),
+                ("commit_base", ctypes.c_int64), ("dist_evals", ctypes.c_int64),
+                ("slot", ctypes.c_int), ("queue_ms", ctypes.c_double),
+                ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("resident_rows", ctypes.c_int64),
+                ("rows_completed", ctypes.c_int64), ("max_concurrent", ctypes.c_int64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("busy_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _lib = None
 
 # name -> (restype, argtypes) of every entry point in include/knnm.h
@@ -65,6 +94,7 @@ SIGNATURES = {
     "knnm_destroy": (_I, [_P]),
     "knnm_set_stream": (_I, [_P, _P]),
     "knnm_last_error": (ctypes.c_char_p, [_P]),
+    "knnm_set_option": (_I, [_P, _I, _I]),
     "knnm_strerror": (ctypes.c_char_p, [_I]),
     "knnm_default_params": (None, [ctypes.POINTER(Params)]),
     "knnm_merge_symmetric": (_I, [_P, _P, _I64, _P, _P, _I64, _P, _I, ctypes.POINTER(Params),
@@ -82,6 +112,17 @@ SIGNATURES = {
     "knnm_step_final": (_I, [_P, _I64, _I, _P, _P, _I, _P, _P, _P, _P]),
     "knnm_step_sample_noalloc": (_I, [_P, _I64, _I, _P, _P, _P, _U64, _I, _I, _I, _I, _P, _P,
                                       _P, _P]),
+    "knnm_merge_scratch_bytes": (_I, [_P, _I, _I64, _I64, _I, ctypes.POINTER(Params),
+                                      ctypes.POINTER(ctypes.c_uint64)]),
+    "knnm_server_create": (_I, [_I, _P, _I64, _P, _I, ctypes.POINTER(Params),
+                                ctypes.POINTER(ServerConfig), ctypes.POINTER(ctypes.c_void_p)]),
+    "knnm_server_submit": (_I, [_P, _P, _I64, _U64]),
+    "knnm_server_wait": (_I, [_P, _U64, _I, _P, _P, ctypes.POINTER(RequestInfo)]),
+    "knnm_server_drain": (_I, [_P, _I]),
+    "knnm_server_get_stats": (_I, [_P, ctypes.POINTER(ServerStats)]),
+    "knnm_server_resident": (_I, [_P, ctypes.POINTER(ctypes.c_int64), _P, _P, _P]),
+    "knnm_server_last_error": (ctypes.c_char_p, [_P]),
+    "knnm_server_destroy": (_I, [_P]),
 }
 
 
@@ -157,6 +198,10 @@ class Context:
             raise KnnmError(rc, "knnm_create failed")
         self.h = h
 
+    def set_graphs(self, on: bool = True):
+        """Replay each merge round as one captured CUDA graph."""
+        self._check(lib().knnm_set_option(self.h, 1, int(on)))
+
     def close(self):
         if getattr(self, "h", None):
             lib().knnm_destroy(self.h)
@@ -210,6 +255,13 @@ class Context:
                                            ctypes.byref(p), _ptr(ids), _ptr(dists),
                                            ctypes.byref(st)))
         return ids, dists, st.as_dict()
+
+    def scratch_bytes(self, mode, n1, n2, d, p: Params) -> int:
+        """Device scratch one whole-merge call of these sizes takes."""
+        out = ctypes.c_uint64(0)
+        self._check(lib().knnm_merge_scratch_bytes(self.h, mode, n1, n2, d, ctypes.byref(p),
+                                                   ctypes.byref(out)))
+        return int(out.value)
 
     def build(self, S, p: Params):
         n, d = S.shape
@@ -300,3 +352,85 @@ def step_sample_noalloc(ids, dists, flags, seed, t, s, new_ids, new_cnt, old_ids
                                           _ptr(flags), seed, t, s, new_ids.shape[1],
                                           old_ids.shape[1], _ptr(new_ids), _ptr(new_cnt),
                                           _ptr(old_ids), _ptr(old_cnt))
+
+
+class Server:
+    """knnm_server_*: J-Merge of raw batches into a graph resident on one device.
+
+    submit() returns at once; worker slots inside the library run queued
+    batches concurrently as slots and device memory allow.  The binding keeps
+    each submitted batch alive until its wait() returns."""
+
+    def __init__(self, S, G, p: Params, slots=2, capacity_rows=None, max_batch_rows=65536,
+                 use_graphs=True, hbm_reserve_bytes=1 << 30, device=0):
+        n, d = S.shape
+        self.d, self.k = d, p.k
+        cfg = ServerConfig()
+        cfg.slots = slots
+        cfg.use_graphs = int(use_graphs)
+        cfg.capacity_rows = capacity_rows or 2 * n
+        cfg.max_batch_rows = max_batch_rows
+        cfg.hbm_reserve_bytes = hbm_reserve_bytes
+        h = ctypes.c_void_p()
+        rc = lib().knnm_server_create(device, _ptr(S), n, _ptr(G), d, ctypes.byref(p),
+                                      ctypes.byref(cfg), ctypes.byref(h))
+        if rc != 0:
+            raise KnnmError(rc, "knnm_server_create failed")
+        self.h = h
+        self._batches = {}
+
+    def _check(self, rc):
+        if rc != 0:
+            raise KnnmError(rc, lib().knnm_server_last_error(self.h).decode())
+
+    def submit(self, batch, req_id: int):
+        self._check(lib().knnm_server_submit(self.h, _ptr(batch), batch.shape[0], req_id))
+        self._batches[req_id] = batch
+
+    def wait(self, req_id: int, timeout_ms: int = -1, out=True):
+        """Returns (ids, dists, info) of a completed batch: its rows' merged
+        lists in resident numbering (numpy) and its request info."""
+        rows = self._batches[req_id].shape[0]
+        ids = np.empty((rows, self.k), np.int32) if out else None
+        dists = np.empty((rows, self.k), np.float32) if out else None
+        info = RequestInfo()
+        rc = lib().knnm_server_wait(self.h, req_id, timeout_ms, _ptr(ids), _ptr(dists),
+                                    ctypes.byref(info))
+        if rc == -4:
+            raise TimeoutError(f"request {req_id} not complete after {timeout_ms} ms")
+        self._batches.pop(req_id, None)
+        self._check(rc)
+        return ids, dists, info.as_dict()
+
+    def drain(self, timeout_ms: int = -1):
+        self._check(lib().knnm_server_drain(self.h, timeout_ms))
+
+    def stats(self):
+        st = ServerStats()
+        self._check(lib().knnm_server_get_stats(self.h, ctypes.byref(st)))
+        return st.as_dict()
+
+    def resident(self, rows: int = -1, vectors=True):
+        """Copies of the resident rows: (vectors, ids, dists) as numpy arrays."""
+        st = self.stats()
+        n = st["resident_rows"] if rows < 0 else min(rows, st["resident_rows"])
+        X = np.empty((n, self.d), np.float32) if vectors else None
+        ids = np.empty((n, self.k), np.int32)
+        dists = np.empty((n, self.k), np.float32)
+        cnt = ctypes.c_int64(n)
+        self._check(lib().knnm_server_resident(self.h, ctypes.byref(cnt), _ptr(X), _ptr(ids),
+                                               _ptr(dists)))
+        n = int(cnt.value)
+        return (X[:n] if vectors else None), ids[:n], dists[:n]
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().knnm_server_destroy(self.h)
+            self.h = None
+            self._batches.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -359,3 +359,30 @@ def test_join_parity_integer_extremes(torch, km, ctx, orc, d, hi):
     assert (c, e) == (c_ref, e_ref)
     assert_same(host(ids), ref.ids, "ids")
     assert_same(host(dists), ref.dists, "dists")
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_graph_replay_matches_stream_launches(torch, km, ctx, orc, precision):
+    """Rounds replayed from one captured CUDA graph give the same graph, counters and
+    stopping round as rounds launched one kernel at a time."""
+    X = datagen.sift_like(3000, 64, seed=21)
+    n1, K = 1600, 16
+    G1, _ = orc.bruteforce_knn(X[:n1], K)
+    G2, _ = orc.bruteforce_knn(X[n1:], K)
+    g = km.Context(0)
+    g.set_graphs(True)
+    for delta in (0.0, 0.01):
+        p = km.params(k=K, precision=precision, max_iters=9, delta=delta, seed=5)
+        args = (cuda(torch, X[:n1]), cuda(torch, G1), cuda(torch, X[n1:]), cuda(torch, G2), p)
+        ai, ad, ast = ctx.merge_symmetric(*args)
+        bi, bd, bst = g.merge_symmetric(*args)
+        assert ast["rounds"] == bst["rounds"]
+        assert ast["updates"] == bst["updates"] and ast["dist_evals"] == bst["dist_evals"]
+        assert_same(host(ai), host(bi), "ids")
+        assert_same(host(ad), host(bd), "dists")
+    ji, jd, jst = g.merge_joint(cuda(torch, X[:n1]), cuda(torch, G1), cuda(torch, X[n1:]),
+                                km.params(k=K, precision=precision, max_iters=5, delta=0.0))
+    ref_i, ref_d, ref_st = orc.merge_joint(X[:n1], G1, X[n1:], K, max_iters=5)
+    assert jst["updates"] == ref_st["updates"]
+    assert_same(host(ji), ref_i, "jmerge ids")
+    assert_same(host(jd), ref_d, "jmerge dists")
