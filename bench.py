@@ -211,6 +211,109 @@ def exact_recall(torch, X_dev, ids_dev, queries, K=10, chunk=131072, extra=48):
     return hits / (len(queries) * K)
 
 
+SERVE = "serve_sift_2m_d128_k16"
+
+
+def run_serving(args, torch, knnm, ctx):
+    """Serving loop (J-Merge of raw batches into a resident graph): a closed-loop
+    run gives the saturation rate, then an open-loop run with Poisson arrivals
+    at 0.8 x that rate gives the batch latencies."""
+    import threading
+    w = datagen.WORKLOADS[SERVE]
+    n0 = args.serve_resident or w["n"]
+    K, d = w["k"], w["d"]
+    nb, slots = args.serve_batches, args.serve_slots
+    sizes = {"warm": datagen.serve_batch_sizes(slots, seed=w["seed"] + 1),
+             "closed": datagen.serve_batch_sizes(nb, seed=w["seed"] + 2),
+             "open": datagen.serve_batch_sizes(nb, seed=w["seed"] + 3)}
+    total = n0 + sum(int(v.sum()) for v in sizes.values())
+    X = datagen.generate(SERVE, n=total)
+    X0 = torch.from_numpy(X[:n0]).cuda()
+    G0, _, _ = ctx.build(X0, knnm.params(k=K, precision="bf16", max_iters=10, delta=0.001,
+                                         seed=21))
+    p = knnm.params(k=K, precision="bf16", max_iters=w["rounds"], sample_rate=w["sample_rate"],
+                    delta=0.001, seed=0)
+    srv = knnm.Server(X0, G0, p, slots=slots, capacity_rows=total, max_batch_rows=64000,
+                      use_graphs=True)
+    del X0, G0
+    off = n0
+    next_id = [1]
+
+    def cut(kind):
+        nonlocal off
+        out = []
+        for b in sizes[kind]:
+            out.append((next_id[0], X[off:off + int(b)]))
+            next_id[0] += 1
+            off += int(b)
+        return out
+
+    def closed(batch_list):
+        t0 = time.perf_counter()
+        for rid, B in batch_list:
+            srv.submit(B, rid)
+        infos = [srv.wait(rid, out=False)[2] for rid, _ in batch_list]
+        return time.perf_counter() - t0, infos
+
+    closed(cut("warm"))
+    wall, infos_c = closed(cut("closed"))
+    rows_c = int(sizes["closed"].sum())
+    sat_rate = nb / wall
+    lam = 0.8 * sat_rate
+    arrivals = datagen.poisson_arrivals(nb, lam, seed=w["seed"] + 4)
+    batch_list = cut("open")
+    submitted = [threading.Event() for _ in batch_list]
+
+    def submitter(t0):
+        for i, (rid, B) in enumerate(batch_list):
+            delay = t0 + arrivals[i] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            srv.submit(B, rid)
+            submitted[i].set()
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    t0 = time.perf_counter()
+    th = threading.Thread(target=submitter, args=(t0,))
+    th.start()
+    infos_o = []
+    for i, (rid, _) in enumerate(batch_list):
+        submitted[i].wait()
+        infos_o.append(srv.wait(rid, out=False)[2])
+    wall_o = time.perf_counter() - t0
+    th.join()
+    clocks = sampler.stop()
+    stats = srv.stats()
+    lat = np.array([i["latency_ms"] for i in infos_o])
+
+    def nearest_rank(v, q):
+        v = np.sort(v)
+        return float(v[max(1, int(math.ceil(q * len(v)))) - 1])
+
+    Xr, idr, _ = srv.resident(device="cuda")
+    srv.close()
+    queries = datagen.sample_nodes(Xr.shape[0], args.recall_queries, seed=1)
+    recall = exact_recall(torch, Xr, idr, queries, K=10)
+    rows_o = int(sizes["open"].sum())
+    return {
+        "workload": SERVE, "resident_rows_start": n0, "resident_rows_end": int(Xr.shape[0]),
+        "d": d, "k": K, "metric": "l2", "precision": "bf16_rerank", "graphs": True,
+        "slots": slots, "batch_sizes": "lognormal, median 8000, sigma 0.75, clipped 1000-64000",
+        "closed_loop": {"batches": nb, "rows": rows_c, "wall_s": wall,
+                        "rows_per_s": rows_c / wall, "batches_per_s": sat_rate,
+                        "mean_rounds": float(np.mean([i["rounds"] for i in infos_c]))},
+        "open_loop": {"batches": nb, "rows": rows_o, "arrival_rate_per_s": lam,
+                      "arrivals": "Poisson, 0.8 x closed-loop batches/s", "wall_s": wall_o,
+                      "rows_per_s": rows_o / wall_o, "p50_ms": nearest_rank(lat, 0.50),
+                      "p99_ms": nearest_rank(lat, 0.99), "max_ms": float(lat.max()),
+                      "mean_queue_ms": float(np.mean([i["queue_ms"] for i in infos_o])),
+                      "clocks": clocks},
+        "max_concurrent": stats["max_concurrent"], "failed": stats["failed"],
+        "recall_at_10_end": recall,
+    }
+
+
 def run_ours(args, w):
     import torch
     from paper_1908_00814_gb300 import build as kbuild, knnm
@@ -366,6 +469,8 @@ def run_ours(args, w):
     line["ms_init"] = st_bf[-1]["ms_init"]
     line["ms_final"] = st_bf[-1]["ms_final"]
     line["valid"] = recall >= 0.95
+    if not args.no_serving:
+        line["serving"] = run_serving(args, torch, knnm, ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -387,6 +492,11 @@ def main():
     ap.add_argument("--recall-queries", type=int, default=1000)
     ap.add_argument("--cpu-rows", type=int, default=20000)
     ap.add_argument("--reference-rows", type=int, default=5000)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-batches", type=int, default=16)
+    ap.add_argument("--serve-slots", type=int, default=3)
+    ap.add_argument("--serve-resident", type=int, default=None,
+                    help="resident rows of the serving run (profiling only)")
     ap.add_argument("--rows", type=int, default=None,
                     help="run the same workload cut to this many points (profiling only)")
     args = ap.parse_args()

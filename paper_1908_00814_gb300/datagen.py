@@ -99,6 +99,21 @@ WORKLOADS = {
 }
 
 
+def serve_batch_sizes(count: int, seed: int, median: int = 8000, sigma: float = 0.75,
+                      lo: int = 1000, hi: int = 64000) -> np.ndarray:
+    """Raw-batch sizes of the serving workload: lognormal around `median`,
+    clipped to [lo, hi]."""
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(np.log(median) + sigma * rng.standard_normal(count))
+    return np.clip(np.rint(sizes), lo, hi).astype(np.int64)
+
+
+def poisson_arrivals(count: int, rate_per_s: float, seed: int) -> np.ndarray:
+    """Arrival times (seconds from 0) of a Poisson process of the given rate."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate_per_s, count))
+
+
 def generate(name: str, n: int | None = None) -> np.ndarray:
     w = WORKLOADS[name]
     gen = {"gaussian_mixture": gaussian_mixture, "sift_like": sift_like,

@@ -410,13 +410,20 @@ class Server:
         self._check(lib().knnm_server_get_stats(self.h, ctypes.byref(st)))
         return st.as_dict()
 
-    def resident(self, rows: int = -1, vectors=True):
-        """Copies of the resident rows: (vectors, ids, dists) as numpy arrays."""
+    def resident(self, rows: int = -1, vectors=True, device=None):
+        """Copies of the resident rows: (vectors, ids, dists), numpy arrays, or
+        torch tensors on `device` when it is given."""
         st = self.stats()
         n = st["resident_rows"] if rows < 0 else min(rows, st["resident_rows"])
-        X = np.empty((n, self.d), np.float32) if vectors else None
-        ids = np.empty((n, self.k), np.int32)
-        dists = np.empty((n, self.k), np.float32)
+        if device is not None:
+            import torch
+            X = torch.empty((n, self.d), dtype=torch.float32, device=device) if vectors else None
+            ids = torch.empty((n, self.k), dtype=torch.int32, device=device)
+            dists = torch.empty((n, self.k), dtype=torch.float32, device=device)
+        else:
+            X = np.empty((n, self.d), np.float32) if vectors else None
+            ids = np.empty((n, self.k), np.int32)
+            dists = np.empty((n, self.k), np.float32)
         cnt = ctypes.c_int64(n)
         self._check(lib().knnm_server_resident(self.h, ctypes.byref(cnt), _ptr(X), _ptr(ids),
                                                _ptr(dists)))
