@@ -201,6 +201,26 @@ __device__ __forceinline__ uint64_t warp_sort32(uint64_t v) {
   return v;
 }
 
+// A bitonic sequence of 32 keys (one per lane) put in ascending order.
+__device__ __forceinline__ uint64_t warp_bitonic_clean32(uint64_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 16; j > 0; j >>= 1) {
+    const uint64_t o = __shfl_xor_sync(FULL, v, j);
+    const uint64_t mn = v < o ? v : o, mx = v < o ? o : v;
+    v = (lane & j) == 0 ? mn : mx;
+  }
+  return v;
+}
+
+// The 32 smallest of the union of two ascending 32-key sequences, ascending:
+// min(a[i], b[31-i]) keeps exactly those 32 and is bitonic.
+__device__ __forceinline__ uint64_t warp_merge_lo32(uint64_t a, uint64_t b) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t br = __shfl_sync(FULL, b, 31 - lane);
+  return warp_bitonic_clean32(a < br ? a : br);
+}
+
 // Ascending bitonic sort of 64 keys, element e = h*32 + lane held in v[h].
 __device__ __forceinline__ void warp_sort64(uint64_t& v0, uint64_t& v1) {
   const int lane = threadIdx.x & 31;

@@ -309,9 +309,8 @@ __device__ __forceinline__ uint64_t warp_smallest(const uint64_t* bucket, uint64
         if (lane >= s) best = KEY_EMPTY;
       }
     } else {
-      uint64_t e0 = best, e1 = x;
-      warp_sort64(e0, e1);
-      best = lane < s ? e0 : KEY_EMPTY;
+      best = warp_merge_lo32(best, warp_sort32(x));
+      if (lane >= s) best = KEY_EMPTY;
     }
   }
   return best;
@@ -431,6 +430,7 @@ __global__ void __launch_bounds__(BLOCK) k_build_records(int64_t N, int K, const
 // ---------------------------------------------------------------------------
 
 constexpr int SCAN_TILE = 1024;  // elements per scan block (256 threads x 4)
+constexpr int SCATTER_SPLIT = 8;  // blocks per proposal region in the scatter
 
 __global__ void __launch_bounds__(256) k_scan_tiles(const int32_t* cnt, int64_t n,
                                                     unsigned long long* tile_sum) {
@@ -517,14 +517,16 @@ __global__ void __launch_bounds__(256) k_scan_apply(const int32_t* cnt, int64_t 
   if (blockIdx.x == 0 && threadIdx.x == 0) offs[n] = *total;
 }
 
-// One block per proposal region: moves each key into its target's bucket.
+// SCATTER_SPLIT blocks per proposal region: moves each key into its target's
+// bucket.
 // Counts are consumed (decremented back to zero) to find the slot.
 __global__ void k_scatter(const int32_t* prop_tgt, const uint64_t* prop_key,
                           const unsigned long long* region_cnt, uint64_t region_cap,
                           int32_t* cnt, const unsigned long long* offs, uint64_t* bucket) {
   const uint64_t n = region_cnt[blockIdx.x];
   const uint64_t base = (uint64_t)blockIdx.x * region_cap;
-  for (uint64_t o = threadIdx.x; o < n; o += blockDim.x) {
+  const uint64_t stride = (uint64_t)blockDim.x * gridDim.y;
+  for (uint64_t o = (uint64_t)blockIdx.y * blockDim.x + threadIdx.x; o < n; o += stride) {
     const int32_t tgt = prop_tgt[base + o];
     const uint64_t key = prop_key[base + o];
     const int pos = atomicSub(&cnt[tgt], 1) - 1;
@@ -566,6 +568,25 @@ __global__ void __launch_bounds__(BLOCK) k_merge_lists(MergeArgs a) {
           if (lane >= K) cur = KEY_EMPTY;
         }
         continue;
+      }
+      {
+        // many survivors: drop repeats inside the chunk, sort it, keep the 32
+        // smallest of (list, chunk) and remove keys the list already holds;
+        // that is the answer unless repeats pushed distinct keys past 32
+        const bool first = (__match_any_sync(FULL, x) & lanemask_lt()) == 0;
+        const uint64_t m = warp_merge_lo32(cur, warp_sort32(first ? x : KEY_EMPTY));
+        const uint64_t mp = __shfl_up_sync(FULL, m, 1);
+        const bool keep = m != KEY_EMPTY && (lane == 0 || m != mp);
+        const unsigned km = __ballot_sync(FULL, keep);
+        if (__popc(km) >= K || __shfl_sync(FULL, m, 31) == KEY_EMPTY) {
+          stage[w][lane] = KEY_EMPTY;
+          __syncwarp();
+          if (keep) stage[w][__popc(km & lanemask_lt())] = m;
+          __syncwarp();
+          cur = lane < K ? stage[w][lane] : KEY_EMPTY;
+          __syncwarp();
+          continue;
+        }
       }
       uint64_t e0 = cur, e1 = x;
       warp_sort64(e0, e1);
@@ -799,8 +820,8 @@ cudaError_t launch_bucket_update(const MergeArgs& a, const int32_t* prop_tgt,
   k_scan_sums<<<1, 1024, 0, st>>>(tile_sum, ntiles, total);
   k_scan_apply<<<(unsigned)ntiles, 256, 0, st>>>(a.cnt, a.N, tile_sum,
                                                  (unsigned long long*)a.offs, total);
-  k_scatter<<<regions, 256, 0, st>>>(prop_tgt, prop_key, region_cnt, region_cap, a.cnt, a.offs,
-                                     a.bucket);
+  k_scatter<<<dim3((unsigned)regions, SCATTER_SPLIT), 256, 0, st>>>(
+      prop_tgt, prop_key, region_cnt, region_cap, a.cnt, a.offs, a.bucket);
   k_merge_lists<<<grid_for_warps(a.N), BLOCK, 0, st>>>(a);
   return cudaGetLastError();
 }
