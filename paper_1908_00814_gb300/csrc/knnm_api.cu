@@ -252,6 +252,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     unsigned long long *roffs, *rtile, *rtotal;
     uint64_t* rbucket;
     int* tdev;
+    uint64_t* kth;
   } P;
   auto carve = [&](Carver& c) {
     P.X = (!s1_dev || !s2_dev) ? c.take<float>((size_t)N * d) : nullptr;
@@ -268,6 +269,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     P.rtile = c.take<unsigned long long>((size_t)(2 * N + 1023) / 1024 + 1);
     P.rtotal = c.take<unsigned long long>(1);
     P.tdev = c.take<int>(1);
+    P.kth = jp.pipe ? c.take<uint64_t>((size_t)N) : nullptr;
     P.flags = c.take<uint8_t>((size_t)N * K);
     P.new_ids = c.take<int32_t>((size_t)N * D.cap_new);
     P.new_cnt = c.take<int32_t>((size_t)N);
@@ -406,6 +408,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     sa.rec_cap = jp.pa.cap;
     sa.norms = P.norms;
     sa.K_list = K;
+    sa.kth = P.kth;
     jp.pa.rec = P.rec;
     jp.pa.Xe = P.Xe;
   }

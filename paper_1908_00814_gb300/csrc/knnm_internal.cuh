@@ -375,6 +375,7 @@ struct SampleArgs {
   int rec_cap = 0;               // ids per record (multiple of 4)
   const float* norms = nullptr;  // canonical norms (COS) copied into the records, else null
   int K_list = 0;                // list length, for the k-th key of each candidate
+  uint64_t* kth = nullptr;       // [N] round-start k-th key of every list (small: stays in L2)
   // Bucketed reverse sampling (used when rcnt is set; rev_new/rev_old unused):
   int32_t* rcnt = nullptr;             // [2N] in-edges per (target, stream); zero on entry and exit
   unsigned long long* roffs = nullptr;  // [2N+1] bucket offsets

@@ -226,6 +226,7 @@ __global__ void __launch_bounds__(BLOCK) k_sample_fwd(SampleArgs a) {
     uint64_t key = lane < K ? a.keys[(size_t)u * K + lane] : KEY_EMPTY;
     uint8_t f = lane < K ? a.flags[(size_t)u * K + lane] : FLAG_OLD;
     if (a.prev_keys && lane < K) a.prev_keys[(size_t)u * K + lane] = key;
+    if (a.kth && lane == K - 1) a.kth[u] = key;
     const int32_t v = key_id(key);
     const bool isnew = lane < K && f == FLAG_NEW;
     const bool isold = lane < K && f != FLAG_NEW;
@@ -369,7 +370,7 @@ __global__ void __launch_bounds__(BLOCK) k_sample_rev(SampleArgs a) {
       float* rcn = (float*)(R + 16 + 12 * a.rec_cap);
       auto put = [&](int pos, int32_t id) {
         rid[pos] = id;
-        rkth[pos] = a.keys[(size_t)id * a.K_list + (a.K_list - 1)];
+        rkth[pos] = a.kth ? a.kth[id] : a.keys[(size_t)id * a.K_list + (a.K_list - 1)];
         if (a.norms) rcn[pos] = a.norms[id];
       };
       if (lane < nf) put(lane, fn);
