@@ -314,31 +314,38 @@ __device__ __forceinline__ void node_tc(const JoinArgs& a, const Rec& rc, int np
   int nr = 0;  // re-rank pairs, compacted to the front of the pair list
   for (int mt = 0; mt < mtiles; ++mt) {
     const unsigned char* pa = row_ptr(mt * 16 + (lane & 15)) + (lane >> 4) * 16;
-    for (int nt = 0; nt < ntiles; nt += 2) {
-      const bool second = nt + 1 < ntiles;
-      float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
-      const unsigned char* pb0 = row_ptr(nt * 8 + (lane & 7)) + ((lane >> 3) & 1) * 16;
-      const unsigned char* pb1 =
-          row_ptr((second ? nt + 1 : nt) * 8 + (lane & 7)) + ((lane >> 3) & 1) * 16;
-#pragma unroll 8
-      for (int k0 = 0; k0 < dpad; k0 += 16) {
-        uint32_t x0, x1, x2, x3, y0, y1, w0, w1;
-        ldm_x4(x0, x1, x2, x3, pa + k0 * 2);
-        ldm_x2(y0, y1, pb0 + k0 * 2);
-        ldm_x2(w0, w1, pb1 + k0 * 2);
-        mma16816(c0, x0, x1, x2, x3, y0, y1);
-        mma16816(c1, x0, x1, x2, x3, w0, w1);
+    // columns j > i only: the first 8-column tile that can hold one is 2 * mt;
+    // four independent accumulator tiles per pass
+    for (int nt = 2 * mt; nt < ntiles; nt += 4) {
+      float c[4][4];
+      const unsigned char* pb[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        c[t][0] = c[t][1] = c[t][2] = c[t][3] = 0.f;
+        const int tile = nt + t < ntiles ? nt + t : ntiles - 1;
+        pb[t] = row_ptr(tile * 8 + (lane & 7)) + ((lane >> 3) & 1) * 16;
       }
-      const int r0 = lane >> 2, col = nt * 8 + 2 * (lane & 3);
-      G[r0 * GSTR + col] = c0[0];
-      G[r0 * GSTR + col + 1] = c0[1];
-      G[(r0 + 8) * GSTR + col] = c0[2];
-      G[(r0 + 8) * GSTR + col + 1] = c0[3];
-      if (second) {
-        G[r0 * GSTR + col + 8] = c1[0];
-        G[r0 * GSTR + col + 9] = c1[1];
-        G[(r0 + 8) * GSTR + col + 8] = c1[2];
-        G[(r0 + 8) * GSTR + col + 9] = c1[3];
+#pragma unroll 4
+      for (int k0 = 0; k0 < dpad; k0 += 16) {
+        uint32_t x0, x1, x2, x3;
+        ldm_x4(x0, x1, x2, x3, pa + k0 * 2);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          uint32_t y0, y1;
+          ldm_x2(y0, y1, pb[t] + k0 * 2);
+          mma16816(c[t], x0, x1, x2, x3, y0, y1);
+        }
+      }
+      const int r0 = lane >> 2;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if (nt + t < ntiles) {
+          const int col = (nt + t) * 8 + 2 * (lane & 3);
+          G[r0 * GSTR + col] = c[t][0];
+          G[r0 * GSTR + col + 1] = c[t][1];
+          G[(r0 + 8) * GSTR + col] = c[t][2];
+          G[(r0 + 8) * GSTR + col + 1] = c[t][3];
+        }
       }
     }
     __syncwarp();
@@ -411,11 +418,13 @@ __device__ __forceinline__ void node_tc(const JoinArgs& a, const Rec& rc, int np
 // of R rows.  Rows of up to AHEAD nodes beyond the current one are in flight
 // whenever the ring has room.
 // ---------------------------------------------------------------------------
-constexpr int NREC = 4;
+constexpr int NREC = 3;
 constexpr int AHEAD = 1;
+constexpr int MAX_WARPS = 12;  // warps per block (one block per SM)
+constexpr int RING_EXTRA = 4;  // ring rows beyond the largest candidate set
 
 template <int METRIC, bool TC>
-__global__ void __launch_bounds__(256, 1) k_join_ring(JoinArgs a, PipeArgs P) {
+__global__ void __launch_bounds__(MAX_WARPS * 32, 1) k_join_ring(JoinArgs a, PipeArgs P) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int W = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -639,13 +648,13 @@ cudaError_t plan_pipe(int precision, int metric, int cap_new, int cap_old, int d
   if (!tc && d % 4 != 0) return cudaErrorInvalidValue;
   P->cap = cap;
   const int RB = rec_bytes(cap);
-  int ring = ((cap + 12) + 7) & ~7;
+  int ring = ((cap + RING_EXTRA) + 7) & ~7;
   if (tc) {
     const int dpad = (d + 15) & ~15;
     P->dx = dpad + 16;
     P->row_bytes = P->dx * 2;
-    P->row_stride = P->row_bytes + 16;
-    if (ring < 64) ring = 64;
+    P->row_stride = P->row_bytes + 16;  // 16-byte skew: conflict-free ldmatrix
+    if (ring < 32) ring = 32;           // the 16-row A tiles reach row 31
   } else {
     P->dx = 0;
     P->row_bytes = d * 4;
@@ -660,8 +669,8 @@ cudaError_t plan_pipe(int precision, int metric, int cap_new, int cap_old, int d
   if (tc) wb += (size_t)16 * GSTR * 4;
   wb = (wb + 127) & ~(size_t)127;
   P->warp_bytes = (int)wb;
-  // warps per block: as many as fit 200 KB (at most 8), one block per SM
-  int w = 8;
+  // warps per block: as many as fit 220 KB (at most MAX_WARPS), one block per SM
+  int w = MAX_WARPS;
   while (w > 1 && (size_t)w * wb + 64 > 220 * 1024) --w;
   if ((size_t)w * wb + 64 > 227 * 1024) return cudaErrorInvalidValue;
   P->cw = w;
