@@ -233,7 +233,8 @@ __global__ void __launch_bounds__(BLOCK) k_sample_fwd(SampleArgs a) {
     const uint64_t pre = hash_prefix(a.seed, t, STREAM_FWD_NEW, (uint64_t)u);
     const uint64_t sk = isnew ? sampling_key(pre, v) : KEY_EMPTY;
     int rank = 0;
-    for (int m = 0; m < K; ++m) rank += (__shfl_sync(FULL, sk, m) < sk) ? 1 : 0;
+    for (unsigned nb = __ballot_sync(FULL, isnew); nb; nb &= nb - 1u)
+      rank += (__shfl_sync(FULL, sk, __ffs(nb) - 1) < sk) ? 1 : 0;
     const bool sel = isnew && rank < s;
     if (sel) a.flags[(size_t)u * K + lane] = FLAG_OLD;
     const unsigned bs = __ballot_sync(FULL, sel), bo = __ballot_sync(FULL, isold);
@@ -287,11 +288,27 @@ __global__ void __launch_bounds__(BLOCK) k_sample_scatter(SampleArgs a) {
 }
 
 // The s smallest keys of bucket [b0, b1), ascending, lane j holding the j-th
-// (KEY_EMPTY beyond).  Keys in a bucket are distinct.
+// (KEY_EMPTY beyond).  Keys in a bucket are distinct.  `stage` is 32 keys of
+// the warp's shared memory.
 __device__ __forceinline__ uint64_t warp_smallest(const uint64_t* bucket, uint64_t b0, uint64_t b1,
-                                                  int s) {
+                                                  int s, uint64_t* stage) {
   const int lane = threadIdx.x & 31;
   uint64_t best = KEY_EMPTY;
+  if (b1 - b0 <= 32) {
+    // one chunk: each key's rank among the chunk is its place
+    const uint64_t x = b0 + lane < b1 ? bucket[b0 + lane] : KEY_EMPTY;
+    const unsigned live = __ballot_sync(FULL, x != KEY_EMPTY);
+    int rank = 0;
+    for (unsigned m = live; m; m &= m - 1u)
+      rank += (__shfl_sync(FULL, x, __ffs(m) - 1) < x) ? 1 : 0;
+    stage[lane] = KEY_EMPTY;
+    __syncwarp();
+    if (x != KEY_EMPTY && rank < s) stage[rank] = x;
+    __syncwarp();
+    best = stage[lane];
+    __syncwarp();
+    return best;
+  }
   for (uint64_t c = b0; c < b1; c += 32) {
     uint64_t x = c + lane < b1 ? bucket[c + lane] : KEY_EMPTY;
     const uint64_t kth = __shfl_sync(FULL, best, s - 1);
@@ -319,6 +336,7 @@ __device__ __forceinline__ uint64_t warp_smallest(const uint64_t* bucket, uint64
 
 // new(u) = fwd_new u rev_new;  old(u) = (fwd_old u rev_old) \ new(u).
 __global__ void __launch_bounds__(BLOCK) k_sample_rev(SampleArgs a) {
+  __shared__ uint64_t stage[WARPS_PER_BLOCK][32];
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
   const int s = a.s;
@@ -329,8 +347,9 @@ __global__ void __launch_bounds__(BLOCK) k_sample_rev(SampleArgs a) {
     const int32_t fo = lane < of ? a.old_ids[(size_t)u * a.cap_old + lane] : -2;
     uint64_t rk, ok;
     if (a.rcnt) {
-      rk = warp_smallest(a.rbucket, a.roffs[2 * u], a.roffs[2 * u + 1], s);
-      ok = warp_smallest(a.rbucket, a.roffs[2 * u + 1], a.roffs[2 * u + 2], s);
+      uint64_t* st = stage[threadIdx.x >> 5];
+      rk = warp_smallest(a.rbucket, a.roffs[2 * u], a.roffs[2 * u + 1], s, st);
+      ok = warp_smallest(a.rbucket, a.roffs[2 * u + 1], a.roffs[2 * u + 2], s, st);
     } else {
       rk = lane < s ? a.rev_new[(size_t)u * s + lane] : KEY_EMPTY;
       ok = lane < s ? a.rev_old[(size_t)u * s + lane] : KEY_EMPTY;
