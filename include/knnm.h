@@ -59,9 +59,14 @@ typedef enum { KNNM_L2 = 0, KNNM_IP = 1, KNNM_COS = 2, KNNM_L1 = 3 } knnm_metric
  * on the CUDA cores.  KNNM_BF16_RERANK: distances are first estimated from
  * BF16 copies of the vectors on the tensor cores (FP32 accumulation); a pair is
  * re-computed canonically in FP32 whenever a proven error bound cannot rule it
- * out, so the merged graph is identical to the KNNM_FP32 one.  L1 has no
- * tensor-core form and always runs as KNNM_FP32. */
-typedef enum { KNNM_FP32 = 0, KNNM_BF16_RERANK = 1 } knnm_precision;
+ * out, so the merged graph is identical to the KNNM_FP32 one.
+ * KNNM_FP16_RERANK: the same with FP16 copies: 3 more mantissa bits, so the
+ * bound is about 8x tighter and far fewer pairs need the re-rank on data of
+ * moderate range (a row with a value beyond +-65504 re-ranks every pair).  Rows
+ * of small non-negative integers (<= 256 in BF16, <= 2048 in FP16) are exact
+ * on the tensor cores and never re-ranked.  L1 has no tensor-core form and
+ * always runs as KNNM_FP32. */
+typedef enum { KNNM_FP32 = 0, KNNM_BF16_RERANK = 1, KNNM_FP16_RERANK = 2 } knnm_precision;
 
 typedef struct {
   int k;             /* list length K, 1..32 (Alg. 1 Data line: k-NN graphs) */

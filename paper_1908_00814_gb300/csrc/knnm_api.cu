@@ -98,7 +98,7 @@ int derive(knnm_ctx* ctx, const knnm_params* p, int mode, int64_t n1, Derived* o
   if (!p) return fail(ctx, KNNM_ERR_INVALID, "params is NULL");
   if (p->k < 1 || p->k > 32) return fail(ctx, KNNM_ERR_INVALID, "k=%d outside 1..32", p->k);
   if (p->metric < 0 || p->metric > 3) return fail(ctx, KNNM_ERR_INVALID, "bad metric %d", p->metric);
-  if (p->precision < 0 || p->precision > 1)
+  if (p->precision < KNNM_FP32 || p->precision > KNNM_FP16_RERANK)
     return fail(ctx, KNNM_ERR_INVALID, "bad precision %d", p->precision);
   if (p->max_iters < 0 || p->max_iters > KNNM_MAX_ROUNDS)
     return fail(ctx, KNNM_ERR_INVALID, "max_iters=%d outside 0..%d", p->max_iters, KNNM_MAX_ROUNDS);
@@ -132,7 +132,7 @@ struct JoinPath {
 
 int choose_join(knnm_ctx* ctx, int precision, int metric, int cap_new, int cap_old, int d,
                 bool rows_aligned, JoinPath* jp) {
-  const bool tc = precision == KNNM_BF16_RERANK && metric != KNNM_L1;
+  const bool tc = precision != KNNM_FP32 && metric != KNNM_L1;
   if (tc || rows_aligned) {
     if (plan_pipe(precision, metric, cap_new, cap_old, d, &jp->pa, &jp->smem, &jp->grid) ==
         cudaSuccess) {
@@ -199,11 +199,10 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
                   "J-Merge needs n1 >= k+1, n2 >= k - floor(r*k) and G1 when n1 > 0");
     if (in.n2 > 0 && !in.S2 && !size_only) return fail(ctx, KNNM_ERR_INVALID, "S_new is NULL");
   }
-  const int precision = (params->precision == KNNM_BF16_RERANK && params->metric != KNNM_L1)
-                            ? KNNM_BF16_RERANK
-                            : KNNM_FP32;
-  if (precision == KNNM_BF16_RERANK && d % 8 != 0)
-    return fail(ctx, KNNM_ERR_INVALID, "the BF16 path needs d %% 8 == 0 (d=%d)", d);
+  // L1 has no tensor-core form
+  const int precision = params->metric != KNNM_L1 ? params->precision : KNNM_FP32;
+  if (precision != KNNM_FP32 && d % 8 != 0)
+    return fail(ctx, KNNM_ERR_INVALID, "the tensor-core paths need d %% 8 == 0 (d=%d)", d);
 
   cudaStream_t st = ctx->stream;
   KNNM_CUDA(cudaSetDevice(ctx->device));
@@ -224,7 +223,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   rc = choose_join(ctx, precision, params->metric, D.cap_new, D.cap_old, d, rows_aligned, &jp);
   if (rc) return rc;
   const int regions = jp.regions();
-  const bool tc = precision == KNNM_BF16_RERANK;
+  const bool tc = precision != KNNM_FP32;
   const uint64_t per_node = 256;
   uint64_t region_cap = ((uint64_t)N * per_node + regions - 1) / regions;
   if (region_cap < 1024) region_cap = 1024;
@@ -345,11 +344,11 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     ++launches;
   }
   if (P.Xb) {
-    KNNM_CUDA(launch_bf16_prep(rows, N, P.Xb, P.aux, P.rmax, st));
+    KNNM_CUDA(launch_bf16_prep(rows, N, P.Xb, P.aux, P.rmax, precision == KNNM_FP16_RERANK, st));
     ++launches;
   }
   if (P.Xe) {
-    KNNM_CUDA(launch_bf16_ext(rows, N, jp.pa.dx, P.Xe, st));
+    KNNM_CUDA(launch_bf16_ext(rows, N, jp.pa.dx, P.Xe, precision == KNNM_FP16_RERANK, st));
     ++launches;
   }
 
@@ -861,11 +860,9 @@ extern "C" int knnm_step_join(knnm_ctx* ctx, int mode, const float* X1, int64_t 
       (mode != SYMMETRIC && mode != JOINT))
     return fail(ctx, KNNM_ERR_INVALID, "bad capacities, split or mode");
   const int K = params->k;
-  const int precision = (params->precision == KNNM_BF16_RERANK && params->metric != KNNM_L1)
-                            ? KNNM_BF16_RERANK
-                            : KNNM_FP32;
-  if (precision == KNNM_BF16_RERANK && d % 8 != 0)
-    return fail(ctx, KNNM_ERR_INVALID, "the BF16 path needs d %% 8 == 0");
+  const int precision = params->metric != KNNM_L1 ? params->precision : KNNM_FP32;
+  if (precision != KNNM_FP32 && d % 8 != 0)
+    return fail(ctx, KNNM_ERR_INVALID, "the tensor-core paths need d %% 8 == 0");
   cudaStream_t st = ctx->stream;
   KNNM_CUDA(cudaSetDevice(ctx->device));
   JoinPath jp;
@@ -873,7 +870,7 @@ extern "C" int knnm_step_join(knnm_ctx* ctx, int mode, const float* X1, int64_t 
                    d % 4 == 0 && aligned16(X1) && aligned16(X2 ? X2 : X1), &jp);
   if (rc) return rc;
   const int regions = jp.regions();
-  const bool tc = precision == KNNM_BF16_RERANK;
+  const bool tc = precision != KNNM_FP32;
   uint64_t per_node = (uint64_t)2 * cap_new * (cap_new + cap_old);
   if (per_node > 512) per_node = 512;
   uint64_t region_cap = ((uint64_t)N * per_node + regions - 1) / regions;
@@ -920,8 +917,8 @@ extern "C" int knnm_step_join(knnm_ctx* ctx, int mode, const float* X1, int64_t 
   KNNM_CUDA(launch_pack((int64_t)N * K, ids, dists, keys, st));
   KNNM_CUDA(cudaMemcpyAsync(prev, keys, (size_t)N * K * 8, cudaMemcpyDeviceToDevice, st));
   if (params->metric == KNNM_COS) KNNM_CUDA(launch_norms(rows, N, norms, st));
-  if (Xb) KNNM_CUDA(launch_bf16_prep(rows, N, Xb, aux, rmax, st));
-  if (Xe) KNNM_CUDA(launch_bf16_ext(rows, N, jp.pa.dx, Xe, st));
+  if (Xb) KNNM_CUDA(launch_bf16_prep(rows, N, Xb, aux, rmax, precision == KNNM_FP16_RERANK, st));
+  if (Xe) KNNM_CUDA(launch_bf16_ext(rows, N, jp.pa.dx, Xe, precision == KNNM_FP16_RERANK, st));
   JoinArgs ja;
   ja.mode = mode;
   ja.rows = rows;

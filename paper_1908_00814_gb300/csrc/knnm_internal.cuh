@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 struct knnm_ctx;
@@ -465,7 +466,10 @@ cudaError_t plan_pipe(int precision, int metric, int cap_new, int cap_old, int d
                       size_t* smem, int* grid);
 cudaError_t launch_pipe(int precision, const JoinArgs& a, const PipeArgs& P, size_t smem,
                         int grid, cudaStream_t st);
-cudaError_t launch_bf16_ext(Rows rows, int64_t N, int dx, __nv_bfloat16* Xe, cudaStream_t st);
+// 16-bit rows (BF16, or FP16 when half != 0; stored through __nv_bfloat16
+// pointers as raw 16-bit elements) with their error-data tails.
+cudaError_t launch_bf16_ext(Rows rows, int64_t N, int dx, __nv_bfloat16* Xe, int half,
+                            cudaStream_t st);
 
 // Persistent join kernels: `grid` blocks loop over the nodes.
 struct JoinPlan {
@@ -507,6 +511,6 @@ cudaError_t launch_unpack(int64_t count, const uint64_t* keys, int32_t* ids, flo
 // BF16 shadow copy and per-row error data for the tensor-core path.
 // rmax[i] = max |x| of row i when BF16 holds the row exactly as integers, else -1.
 cudaError_t launch_bf16_prep(Rows rows, int64_t N, __nv_bfloat16* Xb, float4* aux, float* rmax,
-                             cudaStream_t st);
+                             int half, cudaStream_t st);
 
 }  // namespace knnm

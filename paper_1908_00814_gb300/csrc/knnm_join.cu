@@ -307,13 +307,22 @@ __device__ __forceinline__ void ldmatrix_x2(uint32_t& r0, uint32_t& r1, const vo
                : "=r"(r0), "=r"(r1)
                : "r"(smem_u32(p)));
 }
+// 16-bit inputs (both BF16, or both FP16), FP32 accumulation.
+template <bool HALF>
 __device__ __forceinline__ void mma_bf16(float* c, uint32_t a0, uint32_t a1, uint32_t a2,
                                          uint32_t a3, uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+  if (HALF)
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+  else
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
 // Upper bound on |estimate - canonical distance| for one pair.
@@ -377,7 +386,7 @@ __device__ __forceinline__ float exact_estimate(float g, float4 ai, float4 aj) {
   return canon_finish<METRIC>(g, ai.w, aj.w);
 }
 
-template <int METRIC>
+template <int METRIC, bool HALF>
 __global__ void __launch_bounds__(JT) k_join_bf16(JoinArgs a, int pair_cap) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int d = a.rows.d;
@@ -453,7 +462,7 @@ __global__ void __launch_bounds__(JT) k_join_bf16(JoinArgs a, int pair_cap) {
             const unsigned char* pb =
                 srows + (size_t)(n0 + (lane & 7)) * bstride + (k0 + ((lane >> 3) & 1) * 8) * 2;
             ldmatrix_x2(b0, b1, pb);
-            mma_bf16(c[x], a0, a1, a2, a3, b0, b1);
+            mma_bf16<HALF>(c[x], a0, a1, a2, a3, b0, b1);
           }
         }
         // C fragment: c[x][0..1] at row lane/4, cols 2*(lane%4)+{0,1};
@@ -509,7 +518,10 @@ __global__ void __launch_bounds__(JT) k_join_bf16(JoinArgs a, int pair_cap) {
         const uint16_t pr = cand[q];
         const int i = pr >> 8, j = pr & 0xFF;
         const int32_t pi = S.cid[i], pj = S.cid[j];
-        const float dist = canon_dist_global<METRIC>(a.rows.row(pi), a.rows.row(pj), d,
+        const float dist =
+            a.use_bulk ? canon_dist_global4<METRIC>(a.rows.row(pi), a.rows.row(pj), d,
+                                                     saux[i].w, saux[j].w)
+                       : canon_dist_global<METRIC>(a.rows.row(pi), a.rows.row(pj), d,
                                                      saux[i].w, saux[j].w);
         kp = make_key(dist, pj);
         kq = make_key(dist, pi);
@@ -576,10 +588,11 @@ template <int METRIC>
 cudaError_t plan_metric(int precision, int cap_new, int cap_old, int d, JoinPlan* out) {
   const int cap_rows = cap_new + cap_old;
   const int pair_cap = cap_new * cap_rows;
-  if (precision == 1 && METRIC != L1) {
+  if (precision != 0 && METRIC != L1) {
     out->chunk = d;
     out->smem = bf16_smem_bytes(d, pair_cap);
-    return occupancy_grid(k_join_bf16<METRIC>, out->smem, &out->grid);
+    return precision == 2 ? occupancy_grid(k_join_bf16<METRIC, true>, out->smem, &out->grid)
+                          : occupancy_grid(k_join_bf16<METRIC, false>, out->smem, &out->grid);
   }
   // FP32: stage whole rows when they fit in ~56 KB, else chunks of dimensions
   const size_t budget = 56 * 1024;
@@ -602,7 +615,7 @@ cudaError_t plan_metric(int precision, int cap_new, int cap_old, int d, JoinPlan
 
 cudaError_t plan_join(int precision, int metric, int cap_new, int cap_old, int d, JoinPlan* out) {
   if (cap_new + cap_old > 255) return cudaErrorInvalidValue;
-  if (precision == 1 && metric != L1 && (cap_new > TC_NEW || cap_new + cap_old > TC_ROWS))
+  if (precision != 0 && metric != L1 && (cap_new > TC_NEW || cap_new + cap_old > TC_ROWS))
     return cudaErrorInvalidValue;
   switch (metric) {
     case L2: return plan_metric<L2>(precision, cap_new, cap_old, d, out);
@@ -614,11 +627,17 @@ cudaError_t plan_join(int precision, int metric, int cap_new, int cap_old, int d
 
 cudaError_t launch_join(int precision, const JoinArgs& a, const JoinPlan& plan, cudaStream_t st) {
   const int pair_cap = a.cap_new * (a.cap_new + a.cap_old);
-  if (precision == 1 && a.metric != L1) {
+  if (precision == 2 && a.metric != L1) {
     switch (a.metric) {
-      case L2: k_join_bf16<L2><<<plan.grid, JT, plan.smem, st>>>(a, pair_cap); break;
-      case IP: k_join_bf16<IP><<<plan.grid, JT, plan.smem, st>>>(a, pair_cap); break;
-      default: k_join_bf16<COS><<<plan.grid, JT, plan.smem, st>>>(a, pair_cap); break;
+      case L2: k_join_bf16<L2, true><<<plan.grid, JT, plan.smem, st>>>(a, pair_cap); break;
+      case IP: k_join_bf16<IP, true><<<plan.grid, JT, plan.smem, st>>>(a, pair_cap); break;
+      default: k_join_bf16<COS, true><<<plan.grid, JT, plan.smem, st>>>(a, pair_cap); break;
+    }
+  } else if (precision == 1 && a.metric != L1) {
+    switch (a.metric) {
+      case L2: k_join_bf16<L2, false><<<plan.grid, JT, plan.smem, st>>>(a, pair_cap); break;
+      case IP: k_join_bf16<IP, false><<<plan.grid, JT, plan.smem, st>>>(a, pair_cap); break;
+      default: k_join_bf16<COS, false><<<plan.grid, JT, plan.smem, st>>>(a, pair_cap); break;
     }
   } else {
     switch (a.metric) {

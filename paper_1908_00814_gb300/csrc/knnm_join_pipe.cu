@@ -38,13 +38,22 @@ __device__ __forceinline__ void ldm_x2(uint32_t& r0, uint32_t& r1, const void* p
                : "=r"(r0), "=r"(r1)
                : "r"(smem_u32(p)));
 }
+// D += A * B with 16-bit inputs (both BF16, or both FP16) and FP32 accumulation.
+template <bool HALF>
 __device__ __forceinline__ void mma16816(float* c, uint32_t a0, uint32_t a1, uint32_t a2,
                                          uint32_t a3, uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+  if (HALF)
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+  else
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
 // Error bound of a tensor-core estimate (see knnm_join.cu for the derivation):
@@ -303,7 +312,7 @@ __device__ __forceinline__ void node_fp32(const JoinArgs& a, const Rec& rc, int 
 // BF16: the Gram block is computed one 16-row tile of new candidates at a time
 // into a 16 x GSTR buffer; pairs come sorted by their first index, so tile mt
 // serves the pairs [split(mt), split(mt + 1)).
-template <int METRIC, typename RowPtr>
+template <int METRIC, bool HALF, typename RowPtr>
 __device__ __forceinline__ void node_tc(const JoinArgs& a, const Rec& rc, int np,
                                         uint16_t* pairs, int np0, RowPtr row_ptr, float* G,
                                         int* fill, unsigned long long& reranked) {
@@ -333,7 +342,7 @@ __device__ __forceinline__ void node_tc(const JoinArgs& a, const Rec& rc, int np
         for (int t = 0; t < 4; ++t) {
           uint32_t y0, y1;
           ldm_x2(y0, y1, pb[t] + k0 * 2);
-          mma16816(c[t], x0, x1, x2, x3, y0, y1);
+          mma16816<HALF>(c[t], x0, x1, x2, x3, y0, y1);
         }
       }
       const int r0 = lane >> 2;
@@ -402,7 +411,9 @@ __device__ __forceinline__ void node_tc(const JoinArgs& a, const Rec& rc, int np
       tq = rc.cid[jj];
       const float4 ai = *(const float4*)(row_ptr(i) + dpad * 2);
       const float4 aj = *(const float4*)(row_ptr(jj) + dpad * 2);
-      const float dist = canon_dist_global<METRIC>(a.rows.row(tp), a.rows.row(tq), d, ai.w, aj.w);
+      const float dist =
+          a.use_bulk ? canon_dist_global4<METRIC>(a.rows.row(tp), a.rows.row(tq), d, ai.w, aj.w)
+                     : canon_dist_global<METRIC>(a.rows.row(tp), a.rows.row(tq), d, ai.w, aj.w);
       kp = make_key(dist, tq);
       kq = make_key(dist, tp);
       hp = kp < rc.kth[i];
@@ -421,9 +432,10 @@ __device__ __forceinline__ void node_tc(const JoinArgs& a, const Rec& rc, int np
 constexpr int NREC = 3;
 constexpr int AHEAD = 1;
 constexpr int MAX_WARPS = 12;  // warps per block (one block per SM)
+constexpr int MIN_WARPS = 4;
 constexpr int RING_EXTRA = 4;  // ring rows beyond the largest candidate set
 
-template <int METRIC, bool TC>
+template <int METRIC, bool TC, bool HALF>
 __global__ void __launch_bounds__(MAX_WARPS * 32, 1) k_join_ring(JoinArgs a, PipeArgs P) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int W = blockDim.x >> 5;
@@ -561,7 +573,7 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) k_join_ring(JoinArgs a, Pip
           for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
           np0 = sum;
         }
-        node_tc<METRIC>(a, rc, np, pairs, np0, row_ptr, G, fill, reranked);
+        node_tc<METRIC, HALF>(a, rc, np, pairs, np0, row_ptr, G, fill, reranked);
       } else {
         node_fp32<METRIC>(a, rc, np, pairs, row_ptr, fill);
       }
@@ -597,6 +609,7 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) k_join_ring(JoinArgs a, Pip
 // BF16 rows with their error data in a 32-byte tail:
 //   bf16 x[0..d), zeros up to dpad = round_up(d, 16), then floats
 //   {|b|^2, |b - x| (upper), |b| (upper), canonical |x|, rmax, 0, 0, 0}.
+template <bool HALF>
 __global__ void k_bf16_ext(Rows R, int64_t N, int dx, __nv_bfloat16* Xe) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -604,36 +617,47 @@ __global__ void k_bf16_ext(Rows R, int64_t N, int dx, __nv_bfloat16* Xe) {
   const float* x = R.row(i);
   __nv_bfloat16* o = Xe + (size_t)i * dx;
   float nb2 = 0.f, e2 = 0.f, nx2 = 0.f, mx = 0.f;
-  bool exact = true;
+  bool exact = true, overflow = false;
   for (int t = 0; t < d; ++t) {
     const float v = __ldg(x + t);
-    const __nv_bfloat16 b = __float2bfloat16_rn(v);
-    const float bf = __bfloat162float(b);
-    o[t] = b;
+    float bf;
+    if (HALF) {
+      // saturated: a row with a value beyond FP16 range gets an infinite
+      // error bound below, so every pair with it is re-ranked
+      const float vs = fminf(fmaxf(v, -65504.0f), 65504.0f);
+      overflow = overflow || vs != v;
+      const __half h = __float2half_rn(vs);
+      bf = __half2float(h);
+      reinterpret_cast<__half*>(o)[t] = h;
+    } else {
+      const __nv_bfloat16 b = __float2bfloat16_rn(v);
+      bf = __bfloat162float(b);
+      o[t] = b;
+    }
     nb2 = __fmaf_rn(bf, bf, nb2);
-    const float e = __fsub_rn(bf, v);
+    const float e = __fsub_rn(bf, v);  // exact: bf and v are within a factor of two
     e2 = __fmaf_rn(e, e, e2);
     nx2 = __fmaf_rn(v, v, nx2);
-    exact = exact && v == rintf(v) && v >= 0.0f && v <= 256.0f;
+    exact = exact && v == rintf(v) && v >= 0.0f && v <= (HALF ? 2048.0f : 256.0f);
     mx = fmaxf(mx, fabsf(v));
   }
-  for (int t = d; t < dpad; ++t) o[t] = __float2bfloat16_rn(0.0f);
+  for (int t = d; t < dpad; ++t) o[t] = __float2bfloat16_rn(0.0f);  // +0 in both formats
   const float grow = 1.0f + (float)(d + 2) * 1.2e-7f;
   float* tail = (float*)(o + dpad);
   tail[0] = nb2;
-  tail[1] = __fsqrt_ru(e2 * grow) * 1.000001f;
+  tail[1] = overflow ? __int_as_float(0x7f800000) : __fsqrt_ru(e2 * grow) * 1.000001f;
   tail[2] = __fsqrt_ru(nb2 * grow) * 1.000001f;
   tail[3] = __fsqrt_rn(nx2);
   tail[4] = exact ? mx : -1.0f;
   tail[5] = tail[6] = tail[7] = 0.0f;
 }
 
-template <int METRIC, bool TC>
+template <int METRIC, bool TC, bool HALF>
 cudaError_t setup_ring(size_t smem, int threads, int* per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(k_join_ring<METRIC, TC>,
+  cudaError_t e = cudaFuncSetAttribute(k_join_ring<METRIC, TC, HALF>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_join_ring<METRIC, TC>, threads,
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_join_ring<METRIC, TC, HALF>, threads,
                                                        smem);
 }
 
@@ -641,7 +665,8 @@ cudaError_t setup_ring(size_t smem, int threads, int* per_sm) {
 
 cudaError_t plan_pipe(int precision, int metric, int cap_new, int cap_old, int d, PipeArgs* P,
                       size_t* smem, int* grid) {
-  const bool tc = precision == 1 && metric != L1;
+  const bool tc = precision != 0 && metric != L1;
+  const bool hf = precision == 2;
   const int cap = round_up4(cap_new + cap_old);
   if (cap_new + cap_old > 255 || cap > 64) return cudaErrorInvalidValue;
   if (tc && (cap_new > 32 || d % 8 != 0)) return cudaErrorInvalidValue;
@@ -672,7 +697,9 @@ cudaError_t plan_pipe(int precision, int metric, int cap_new, int cap_old, int d
   // warps per block: as many as fit 220 KB (at most MAX_WARPS), one block per SM
   int w = MAX_WARPS;
   while (w > 1 && (size_t)w * wb + 64 > 220 * 1024) --w;
-  if ((size_t)w * wb + 64 > 227 * 1024) return cudaErrorInvalidValue;
+  // long rows leave too few warps per SM to hide the gathers: the caller takes
+  // the single-stage kernel instead
+  if (w < MIN_WARPS || (size_t)w * wb + 64 > 227 * 1024) return cudaErrorInvalidValue;
   P->cw = w;
   P->nstages = 0;
   P->stage_bytes = 0;
@@ -680,10 +707,22 @@ cudaError_t plan_pipe(int precision, int metric, int cap_new, int cap_old, int d
   int per = 0;
   cudaError_t e;
   switch (metric) {
-    case L2: e = tc ? setup_ring<L2, true>(*smem, 32 * w, &per) : setup_ring<L2, false>(*smem, 32 * w, &per); break;
-    case IP: e = tc ? setup_ring<IP, true>(*smem, 32 * w, &per) : setup_ring<IP, false>(*smem, 32 * w, &per); break;
-    case COS: e = tc ? setup_ring<COS, true>(*smem, 32 * w, &per) : setup_ring<COS, false>(*smem, 32 * w, &per); break;
-    default: e = setup_ring<L1, false>(*smem, 32 * w, &per); break;
+    case L2:
+      e = !tc ? setup_ring<L2, false, false>(*smem, 32 * w, &per)
+              : hf ? setup_ring<L2, true, true>(*smem, 32 * w, &per)
+                   : setup_ring<L2, true, false>(*smem, 32 * w, &per);
+      break;
+    case IP:
+      e = !tc ? setup_ring<IP, false, false>(*smem, 32 * w, &per)
+              : hf ? setup_ring<IP, true, true>(*smem, 32 * w, &per)
+                   : setup_ring<IP, true, false>(*smem, 32 * w, &per);
+      break;
+    case COS:
+      e = !tc ? setup_ring<COS, false, false>(*smem, 32 * w, &per)
+              : hf ? setup_ring<COS, true, true>(*smem, 32 * w, &per)
+                   : setup_ring<COS, true, false>(*smem, 32 * w, &per);
+      break;
+    default: e = setup_ring<L1, false, false>(*smem, 32 * w, &per); break;
   }
   if (e != cudaSuccess) return e;
   if (per < 1) return cudaErrorInvalidConfiguration;
@@ -696,28 +735,38 @@ cudaError_t plan_pipe(int precision, int metric, int cap_new, int cap_old, int d
 
 cudaError_t launch_pipe(int precision, const JoinArgs& a, const PipeArgs& P, size_t smem,
                         int grid, cudaStream_t st) {
-  const bool tc = precision == 1 && a.metric != L1;
+  const bool tc = precision != 0 && a.metric != L1;
   const int threads = 32 * P.cw;
-  if (tc) {
+  if (tc && precision == 2) {
     switch (a.metric) {
-      case L2: k_join_ring<L2, true><<<grid, threads, smem, st>>>(a, P); break;
-      case IP: k_join_ring<IP, true><<<grid, threads, smem, st>>>(a, P); break;
-      default: k_join_ring<COS, true><<<grid, threads, smem, st>>>(a, P); break;
+      case L2: k_join_ring<L2, true, true><<<grid, threads, smem, st>>>(a, P); break;
+      case IP: k_join_ring<IP, true, true><<<grid, threads, smem, st>>>(a, P); break;
+      default: k_join_ring<COS, true, true><<<grid, threads, smem, st>>>(a, P); break;
+    }
+  } else if (tc) {
+    switch (a.metric) {
+      case L2: k_join_ring<L2, true, false><<<grid, threads, smem, st>>>(a, P); break;
+      case IP: k_join_ring<IP, true, false><<<grid, threads, smem, st>>>(a, P); break;
+      default: k_join_ring<COS, true, false><<<grid, threads, smem, st>>>(a, P); break;
     }
   } else {
     switch (a.metric) {
-      case L2: k_join_ring<L2, false><<<grid, threads, smem, st>>>(a, P); break;
-      case IP: k_join_ring<IP, false><<<grid, threads, smem, st>>>(a, P); break;
-      case COS: k_join_ring<COS, false><<<grid, threads, smem, st>>>(a, P); break;
-      default: k_join_ring<L1, false><<<grid, threads, smem, st>>>(a, P); break;
+      case L2: k_join_ring<L2, false, false><<<grid, threads, smem, st>>>(a, P); break;
+      case IP: k_join_ring<IP, false, false><<<grid, threads, smem, st>>>(a, P); break;
+      case COS: k_join_ring<COS, false, false><<<grid, threads, smem, st>>>(a, P); break;
+      default: k_join_ring<L1, false, false><<<grid, threads, smem, st>>>(a, P); break;
     }
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_bf16_ext(Rows rows, int64_t N, int dx, __nv_bfloat16* Xe, cudaStream_t st) {
+cudaError_t launch_bf16_ext(Rows rows, int64_t N, int dx, __nv_bfloat16* Xe, int half,
+                            cudaStream_t st) {
   if (N == 0) return cudaSuccess;
-  k_bf16_ext<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(rows, N, dx, Xe);
+  if (half)
+    k_bf16_ext<true><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(rows, N, dx, Xe);
+  else
+    k_bf16_ext<false><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(rows, N, dx, Xe);
   return cudaGetLastError();
 }
 

@@ -752,29 +752,42 @@ __global__ void k_unpack(int64_t count, const uint64_t* keys, int32_t* ids, floa
 // BF16 shadow copy; aux = {|b|^2, |b - x| (upper bound), |b| (upper bound),
 // canonical |x|}.  rmax = max |x_t| when every x_t is an integer of magnitude
 // <= 256 (BF16 holds it exactly), else -1.
+template <bool HALF>
 __global__ void k_bf16_prep(Rows R, int64_t N, __nv_bfloat16* Xb, float4* aux, float* rmax) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const float* x = R.row(i);
   __nv_bfloat16* o = Xb + (size_t)i * R.d;
   float nb2 = 0.f, e2 = 0.f, nx2 = 0.f, mx = 0.f;
-  bool exact = true;
+  bool exact = true, overflow = false;
   for (int t = 0; t < R.d; ++t) {
     float v = __ldg(x + t);
-    __nv_bfloat16 b = __float2bfloat16_rn(v);
-    float bf = __bfloat162float(b);
-    o[t] = b;
+    float bf;
+    if (HALF) {
+      // saturated; a row beyond FP16 range gets an infinite error bound
+      const float vs = fminf(fmaxf(v, -65504.0f), 65504.0f);
+      overflow = overflow || vs != v;
+      const __half h = __float2half_rn(vs);
+      bf = __half2float(h);
+      reinterpret_cast<__half*>(o)[t] = h;
+    } else {
+      __nv_bfloat16 b = __float2bfloat16_rn(v);
+      bf = __bfloat162float(b);
+      o[t] = b;
+    }
     nb2 = __fmaf_rn(bf, bf, nb2);
     float e = __fsub_rn(bf, v);  // exact: bf and v are within a factor of two
     e2 = __fmaf_rn(e, e, e2);
     nx2 = __fmaf_rn(v, v, nx2);
-    exact = exact && v == rintf(v) && fabsf(v) <= 256.0f;
+    exact = exact && v == rintf(v) && fabsf(v) <= (HALF ? 2048.0f : 256.0f);
     mx = fmaxf(mx, fabsf(v));
   }
   // sums of d non-negative terms carry at most d+1 relative roundings
   const float grow = 1.0f + (float)(R.d + 2) * 1.2e-7f;
-  aux[i] = make_float4(nb2, __fsqrt_ru(e2 * grow) * 1.000001f, __fsqrt_ru(nb2 * grow) * 1.000001f,
-                       __fsqrt_rn(nx2));
+  aux[i] = make_float4(nb2,
+                       overflow ? __int_as_float(0x7f800000)
+                                : __fsqrt_ru(e2 * grow) * 1.000001f,
+                       __fsqrt_ru(nb2 * grow) * 1.000001f, __fsqrt_rn(nx2));
   rmax[i] = exact ? mx : -1.0f;
 }
 
@@ -900,9 +913,12 @@ cudaError_t launch_unpack(int64_t count, const uint64_t* keys, int32_t* ids, flo
 }
 
 cudaError_t launch_bf16_prep(Rows rows, int64_t N, __nv_bfloat16* Xb, float4* aux, float* rmax,
-                             cudaStream_t st) {
+                             int half, cudaStream_t st) {
   if (N == 0) return cudaSuccess;
-  k_bf16_prep<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(rows, N, Xb, aux, rmax);
+  if (half)
+    k_bf16_prep<true><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(rows, N, Xb, aux, rmax);
+  else
+    k_bf16_prep<false><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(rows, N, Xb, aux, rmax);
   return cudaGetLastError();
 }
 

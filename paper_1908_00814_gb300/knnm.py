@@ -17,7 +17,7 @@ import numpy as np
 _LIB_PATH = Path(__file__).resolve().parent / "libknnm.so"
 
 L2, IP, COS, L1 = 0, 1, 2, 3
-FP32, BF16_RERANK = 0, 1
+FP32, BF16_RERANK, FP16_RERANK = 0, 1, 2
 SYMMETRIC, JOINT = 0, 1
 MAX_ROUNDS = 64
 METRICS = {"l2": L2, "ip": IP, "cos": COS, "l1": L1}
@@ -157,7 +157,8 @@ def params(k=20, metric="l2", precision="fp32", max_iters=10, sample_rate=0.5, k
     p = Params()
     p.k = k
     p.metric = METRICS[metric] if isinstance(metric, str) else int(metric)
-    p.precision = {"fp32": FP32, "bf16": BF16_RERANK}[precision] if isinstance(precision, str) \
+    p.precision = {"fp32": FP32, "bf16": BF16_RERANK, "fp16": FP16_RERANK}[precision] \
+        if isinstance(precision, str) \
         else int(precision)
     p.max_iters = max_iters
     p.sample_rate = sample_rate

@@ -166,7 +166,7 @@ def _join_case(orc, X, n1, K, mode, metric, seed=1, t=2, s=None):
     return st, cands
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
 @pytest.mark.parametrize("metric", [0, 1, 2, 3])
 @pytest.mark.parametrize("mode", ["symmetric", "joint", "build"])
 def test_join_parity(torch, km, ctx, orc, precision, metric, mode):
@@ -197,7 +197,7 @@ def test_join_parity_dims(torch, km, ctx, orc, d):
     ids, dists, flags = cuda(torch, st.ids), cuda(torch, st.dists), cuda(torch, st.flags)
     ref = st.copy()
     c_ref, e_ref = orc.join(orc.JOINT, X, 0, ref, cands)
-    for precision in (["fp32", "bf16"] if d % 8 == 0 else ["fp32"]):
+    for precision in (["fp32", "bf16", "fp16"] if d % 8 == 0 else ["fp32"]):
         i2, d2, f2 = ids.clone(), dists.clone(), flags.clone()
         c, e = ctx.step_join(km.JOINT, cuda(torch, X), 0, km.params(k=K, precision=precision),
                              i2, d2, f2, tuple(cuda(torch, a) for a in cands))
@@ -222,7 +222,7 @@ def test_final_parity(torch, km, ctx, orc):
 # ------------------------------------------------------------------ whole merges
 
 def _smerge_both(torch, km, ctx, orc, X, n1, K, rounds, metric=0, sample_rate=0.5, seed=0,
-                 delta=0.0, precisions=("fp32", "bf16")):
+                 delta=0.0, precisions=("fp32", "bf16", "fp16")):
     G1, _ = orc.bruteforce_knn(X[:n1], K, metric=metric)
     G2, _ = orc.bruteforce_knn(X[n1:], K, metric=metric)
     ref_i, ref_d, ref_st = orc.merge_symmetric(X[:n1], G1, X[n1:], G2, K, metric=metric,
@@ -251,7 +251,7 @@ def test_smerge_metrics_parity(torch, km, ctx, orc, metric):
     X = datagen.gaussian_mixture(1800, 24, n_comp=6, seed=40 + metric,
                                  normalize=(metric == 2))
     _smerge_both(torch, km, ctx, orc, X, 1000, 12, 5, metric=metric,
-                 precisions=("fp32",) if metric == 3 else ("fp32", "bf16"))
+                 precisions=("fp32",) if metric == 3 else ("fp32", "bf16", "fp16"))
 
 
 def test_smerge_sift_parity(torch, km, ctx, orc):
@@ -259,7 +259,7 @@ def test_smerge_sift_parity(torch, km, ctx, orc):
     _smerge_both(torch, km, ctx, orc, X, 2100, 20, 6, delta=0.001)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
 def test_jmerge_parity(torch, km, ctx, orc, precision):
     X = datagen.gaussian_mixture(3000, 32, n_comp=10, seed=8, normalize=True)
     n1, K = 2000, 16
@@ -272,7 +272,7 @@ def test_jmerge_parity(torch, km, ctx, orc, precision):
     assert_same(host(gd), ref_d, "dists")
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
 def test_build_parity(torch, km, ctx, orc, precision):
     X = datagen.sift_like(2500, 64, seed=12)
     ref_i, ref_d, ref_st = orc.build_graph(X, 20, max_iters=5, seed=3)
@@ -386,3 +386,11 @@ def test_graph_replay_matches_stream_launches(torch, km, ctx, orc, precision):
     assert jst["updates"] == ref_st["updates"]
     assert_same(host(ji), ref_i, "jmerge ids")
     assert_same(host(jd), ref_d, "jmerge dists")
+
+
+def test_fp16_out_of_range_rows_fall_back_to_fp32(torch, km, ctx, orc):
+    """Rows beyond the FP16 range get an infinite error bound: every pair with
+    them is re-ranked in canonical FP32, and the merge still equals the oracle."""
+    X = datagen.gaussian_mixture(1600, 16, n_comp=6, seed=77)
+    X[::7] *= 1.0e5   # some rows far beyond +-65504
+    _smerge_both(torch, km, ctx, orc, X, 800, 10, 4, precisions=("fp16",))
