@@ -177,18 +177,31 @@ def run_reference(args, w):
 
 # ----------------------------------------------------------------------------- GPU arm
 
-def exact_recall(torch, X_dev, ids_dev, queries, K=10, chunk=131072, extra=48):
-    """recall@K of the merged lists on `queries` against exact float64 neighbours."""
+def exact_recall(torch, X_dev, ids_dev, queries, K=10, chunk=131072, extra=48, metric="l2"):
+    """recall@K of the merged lists on `queries` against exact float64 neighbours
+    under `metric` ("l2", "cos" or "l1")."""
     q = torch.as_tensor(queries, device=X_dev.device, dtype=torch.long)
-    Q = X_dev[q]
-    qn = (Q.double() ** 2).sum(1)
+    Q = X_dev[q].double()
+    qn = (Q ** 2).sum(1)
     best_d = None
     best_i = None
     n = X_dev.shape[0]
+    if metric == "l1":
+        chunk = max(1024, chunk // 32)
+
+    def block(Xb):
+        Xd = Xb.double()
+        if metric == "l1":
+            return torch.cdist(Q, Xd, p=1)
+        dot = Q @ Xd.T
+        if metric == "cos":
+            den = qn.sqrt()[:, None] * (Xd ** 2).sum(1).sqrt()[None, :]
+            return 1.0 - dot / den.clamp_min(1e-300)
+        return qn[:, None] + (Xd ** 2).sum(1)[None, :] - 2.0 * dot
+
     for b in range(0, n, chunk):
         Xb = X_dev[b:b + chunk]
-        D = (qn[:, None] + (Xb.double() ** 2).sum(1)[None, :]
-             - 2.0 * (Q.double() @ Xb.double().T))
+        D = block(Xb)
         idx = torch.arange(b, b + Xb.shape[0], device=X_dev.device)
         D[idx[None, :] == q[:, None]] = float("inf")
         d2, i2 = torch.topk(D, min(K + extra, D.shape[1]), dim=1, largest=False)
@@ -200,15 +213,43 @@ def exact_recall(torch, X_dev, ids_dev, queries, K=10, chunk=131072, extra=48):
             ci = torch.cat([best_i, i2], 1)
             best_d, o = torch.topk(cd, K + extra, dim=1, largest=False)
             best_i = torch.gather(ci, 1, o)
+
     # exact float64 distances of the candidates and of the returned ids
     def direct(ids):
-        return ((X_dev[ids].double() - Q.double()[:, None, :]) ** 2).sum(-1)
+        R = X_dev[ids].double()
+        if metric == "l1":
+            return (R - Q[:, None, :]).abs().sum(-1)
+        if metric == "cos":
+            dot = (R * Q[:, None, :]).sum(-1)
+            den = qn.sqrt()[:, None] * (R ** 2).sum(-1).sqrt()
+            return 1.0 - dot / den.clamp_min(1e-300)
+        return ((R - Q[:, None, :]) ** 2).sum(-1)
     cd = direct(best_i)
     kth = torch.sort(cd, dim=1).values[:, K - 1]
     got = ids_dev[q][:, :K].long()
     gd = direct(got)
-    hits = (gd <= kth[:, None] * (1 + 1e-9)).sum().item()
+    hits = (gd <= kth[:, None] * (1 + 1e-9) + 1e-12).sum().item()
     return hits / (len(queries) * K)
+
+
+def distance_error(torch, X_dev, ids_dev, dists_dev, queries, metric="l2"):
+    """Relative error of the returned FP32 distances against float64 (max, p99)."""
+    q = torch.as_tensor(queries, device=X_dev.device, dtype=torch.long)
+    Q = X_dev[q].double()
+    ids = ids_dev[q].long()
+    R = X_dev[ids].double()
+    if metric == "l1":
+        ref = (R - Q[:, None, :]).abs().sum(-1)
+    elif metric == "cos":
+        dot = (R * Q[:, None, :]).sum(-1)
+        ref = 1.0 - dot / ((Q ** 2).sum(-1).sqrt()[:, None] * (R ** 2).sum(-1).sqrt())
+    else:
+        ref = ((R - Q[:, None, :]) ** 2).sum(-1)
+    got = dists_dev[q].double()
+    rel = ((got - ref).abs() / ref.abs().clamp_min(1e-30)).flatten()
+    return {"max_rel": float(rel.max().item()),
+            "p99_rel": float(torch.quantile(rel.float(), 0.99).item()),
+            "nodes": len(queries), "versus": "float64 recomputation of the returned neighbours"}
 
 
 SERVE = "serve_sift_2m_d128_k16"
@@ -314,6 +355,120 @@ def run_serving(args, torch, knnm, ctx):
     }
 
 
+def timed_call(torch, fn, steps, warmup):
+    """Device time of `fn` (ms, mean over steps) with CUDA events on the current stream."""
+    for _ in range(warmup):
+        out = fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    outs = [fn() for _ in range(steps)]
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, outs[-1], [o[2] for o in outs]
+
+
+def run_other(args, name):
+    """The other merge workloads, one JSON line each: the joint merge of 1M raw
+    cosine vectors into a 1M graph (96-d), and the 960-d GIST-like symmetric
+    merge (L1 on the FP32 path, L2 on every path) with its 64-part merge tree."""
+    import torch
+    from paper_1908_00814_gb300 import build as kbuild, knnm
+    kbuild.build()
+    torch.cuda.set_device(0)
+    ctx = knnm.Context(0)
+    w = dict(datagen.WORKLOADS[name])
+    if args.rows:
+        w["n"] = args.rows
+    n, d, K = w["n"], w["d"], w["k"]
+    X = datagen.generate(name, n=n)
+    Xd = torch.from_numpy(X).cuda()
+    n1 = n // 2
+    S1, S2 = Xd[:n1].contiguous(), Xd[n1:].contiguous()
+    queries = datagen.sample_nodes(n, args.recall_queries, seed=0)
+    steps, warmup = args.steps, args.warmup
+    runs = {}
+
+    def record(label, metric, ms, out, stats, points):
+        r = {"ms_per_step": ms, "points_per_s": points / (ms / 1000.0),
+             "recall_at_10": exact_recall(torch, Xd, out[0], queries, K=10, metric=metric),
+             "rounds": stats[-1]["rounds"],
+             "dist_evals": sum(stats[-1]["dist_evals"]),
+             "reranked": sum(stats[-1]["reranked"]),
+             "ms_join_per_step": sum(sum(s_["ms_join"]) for s_ in stats) / len(stats),
+             "ms_sample_per_step": sum(sum(s_["ms_sample"]) for s_ in stats) / len(stats),
+             "ms_update_per_step": sum(sum(s_["ms_update"]) for s_ in stats) / len(stats),
+             "distance_error": distance_error(torch, Xd, out[0], out[1], queries[:200], metric)}
+        r["rerank_fraction"] = r["reranked"] / max(r["dist_evals"], 1)
+        runs[label] = r
+        print(f"# {label}: {ms:.1f} ms, recall {r['recall_at_10']:.4f}", file=sys.stderr,
+              flush=True)
+
+    if w["kind"] == "joint":
+        metric = w["metric"]
+        G1, _, _ = ctx.build(S1, knnm.params(k=K, metric=metric, precision="fp32",
+                                             max_iters=10, delta=0.001, seed=11))
+        for prec in ("fp32", "fp16", "bf16"):
+            p = knnm.params(k=K, metric=metric, precision=prec, max_iters=w["rounds"],
+                            sample_rate=w["sample_rate"], delta=0.001, seed=0)
+            ms, out, stats = timed_call(torch, lambda: ctx.merge_joint(S1, G1, S2, p), steps,
+                                        warmup)
+            record(f"{metric}_{prec}", metric, ms, out, stats, n)
+            runs[f"{metric}_{prec}"]["raw_points_per_s"] = (n - n1) / (ms / 1000.0)
+        head = runs[f"{metric}_fp32"]
+        merge = "joint (Alg. 2)"
+    else:
+        for metric, precs in (("l1", ("fp32",)), ("l2", ("fp32", "fp16", "bf16"))):
+            bp = knnm.params(k=K, metric=metric, precision="fp32", max_iters=10, delta=0.001,
+                             seed=11)
+            G1, _, _ = ctx.build(S1, bp)
+            bp.seed = 12
+            G2, _, _ = ctx.build(S2, bp)
+            for prec in precs:
+                p = knnm.params(k=K, metric=metric, precision=prec, max_iters=w["rounds"],
+                                sample_rate=w["sample_rate"], delta=0.001, seed=0)
+                ms, out, stats = timed_call(
+                    torch, lambda: ctx.merge_symmetric(S1, G1, S2, G2, p), steps, warmup)
+                record(f"{metric}_{prec}", metric, ms, out, stats, n)
+        # merge tree: 64 exact part graphs (brute force, not timed), merged pairwise
+        parts = 64
+        rows = [n // parts + (1 if i < n % parts else 0) for i in range(parts)]
+        Gt = torch.empty((n, K), dtype=torch.int32, device="cuda")
+        off = 0
+        torch.backends.cuda.matmul.allow_tf32 = False
+        for r in rows:
+            P = Xd[off:off + r]
+            sq = (P ** 2).sum(1)
+            D = sq[:, None] + sq[None, :] - 2.0 * (P @ P.T)
+            D.fill_diagonal_(float("inf"))
+            Gt[off:off + r] = torch.topk(D, K, dim=1, largest=False).indices.int()
+            off += r
+            del P, D
+        p = knnm.params(k=K, metric="l2", precision="fp32", max_iters=w["rounds"],
+                        sample_rate=w["sample_rate"], delta=0.001, seed=0)
+        ms, out, stats = timed_call(torch, lambda: ctx.merge_tree(Xd, rows, Gt, p), 1, 1)
+        runs["tree_l2_fp32"] = {"parts": parts, "part_rows": rows[0], "levels": stats[-1]["rounds"],
+                                "merges": parts - 1, "ms": ms, "points_per_s": n / (ms / 1000.0),
+                                "recall_at_10": exact_recall(torch, Xd, out[0], queries, K=10),
+                                "leaf_graphs": "brute force (FP32 GEMM, not timed)"}
+        print(f"# tree: {ms:.1f} ms", file=sys.stderr, flush=True)
+        head = runs["l2_fp32"]
+        merge = "symmetric (Alg. 1) + merge tree"
+    line = {"metric": METRIC, "value": head["points_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": steps, "warmup": warmup, "ms_per_step": head["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": name, "merge": merge, "n": n, "d": d, "k": K,
+                       "metric": w["metric"], "max_rounds": w["rounds"],
+                       "sample_rate": w["sample_rate"], "delta": 0.001,
+                       "recall_queries": len(queries),
+                       "l2_flush": "inputs larger than L2"},
+            "runs": runs}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def run_ours(args, w):
     import torch
     from paper_1908_00814_gb300 import build as kbuild, knnm
@@ -386,6 +541,7 @@ def run_ours(args, w):
     # recall@10 on sampled nodes (not timed)
     queries = datagen.sample_nodes(w["n"], args.recall_queries, seed=0)
     recall = exact_recall(torch, Xd, out_bf[0], queries, K=10)
+    dist_err = distance_error(torch, Xd, out_bf[0], out_bf[1], queries[:500])
 
     # roofline of the dominant kernel (per-round device times from the library's events)
     tot = {"sample": 0.0, "join": 0.0, "update": 0.0}
@@ -453,6 +609,7 @@ def run_ours(args, w):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16+f32", "data": "synthetic", "config": workload_config(w, "bf16_rerank"),
             "recall_at_10": recall, "recall_queries": len(queries),
+            "distance_error": dist_err,
             "rounds": st_bf[-1]["rounds"], "updates_per_round": st_bf[-1]["updates"],
             "per_round": {k: st_bf[-1][k] for k in ("dist_evals", "proposals", "reranked",
                                                     "gathered", "ms_sample", "ms_join",
@@ -492,6 +649,9 @@ def main():
     ap.add_argument("--recall-queries", type=int, default=1000)
     ap.add_argument("--cpu-rows", type=int, default=20000)
     ap.add_argument("--reference-rows", type=int, default=5000)
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "jmerge_gmm_2m_d96_k16_cos", "smerge_gist_1m_d960_k20"],
+                    help="another merge workload (one JSON line of its own)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-batches", type=int, default=16)
     ap.add_argument("--serve-slots", type=int, default=3)
@@ -507,6 +667,8 @@ def main():
         w["n"] = args.rows
     if args.impl == "reference":
         return run_reference(args, w)
+    if args.workload != WORKLOAD:
+        return run_other(args, args.workload)
     return run_ours(args, w)
 
 

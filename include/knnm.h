@@ -94,6 +94,7 @@ typedef struct {
   float ms_update[KNNM_MAX_ROUNDS];       /* device time of the top-k insert + flag pass */
   float ms_init, ms_rounds, ms_final;     /* device time of init, all rounds, final merge */
   float ms_total;                         /* wall time of the call */
+  uint64_t tc_rounds;                     /* bit t-1 set: round t ran the tensor-core join */
 } knnm_stats;
 
 typedef struct knnm_ctx knnm_ctx;
@@ -140,6 +141,21 @@ int knnm_merge_joint(knnm_ctx* ctx, const float* S1, int64_t n1, const int32_t* 
 /* NN-Descent build of S [n][d] (J-Merge with an empty graph); n >= K+1. */
 int knnm_build(knnm_ctx* ctx, const float* S, int64_t n, int d, const knnm_params* params,
                int32_t* out_ids, float* out_dists, knnm_stats* stats);
+
+/* Merge tree (Sec. 1 and Sec. 3: a graph over a large set made from graphs
+ * built independently on its parts, by repeated two-graph merges).  S [n][d]
+ * is cut into `parts` consecutive parts of part_rows[p] rows each (every part
+ * >= K+1 rows); G [n][K] holds each part's graph with ids local to its part.
+ * Level by level, neighbouring blocks (0,1), (2,3), ... are joined by S-Merge
+ * (Alg. 1) into one block each; an odd last block waits for the next level.
+ * Merge j of level l runs with seed H(params->seed, l, 6, j, 0) (the library's
+ * counter-based hash).  out_ids/out_dists [n][K] hold global ids.  In `stats`,
+ * rounds is the number of levels and entry l of each per-round array sums the
+ * merges of level l; ms_* sum over all merges.  parts == 1 returns G with its
+ * canonical distances, sorted. */
+int knnm_merge_tree(knnm_ctx* ctx, const float* S, int64_t n, int d, int parts,
+                    const int64_t* part_rows, const int32_t* G, const knnm_params* params,
+                    int32_t* out_ids, float* out_dists, knnm_stats* stats);
 
 /* Device scratch, in bytes, that one whole-merge call of these sizes takes
  * from its context (all arrays on the device).  mode: 0 = S-Merge, 1 = J-Merge

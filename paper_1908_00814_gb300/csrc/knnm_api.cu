@@ -1,6 +1,7 @@
 // knnm_api.cu -- the C ABI of libknnm.so (include/knnm.h): argument checks,
 // scratch management, host/device pointer handling and the round loop that
 // drives the kernels of S-Merge (Alg. 1), J-Merge (Alg. 2) and the build.
+#include <algorithm>
 #include <chrono>
 #include <cstdarg>
 #include <cstdio>
@@ -222,10 +223,21 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   JoinPath jp;
   rc = choose_join(ctx, precision, params->metric, D.cap_new, D.cap_old, d, rows_aligned, &jp);
   if (rc) return rc;
-  const int regions = jp.regions();
   const bool tc = precision != KNNM_FP32;
+  // The tensor-core join settles a pair without FP32 work only when its
+  // estimate proves the pair is no proposal (or the rows are small integers);
+  // every other pair is re-ranked in canonical FP32 from global memory.  On
+  // rounds where most pairs are proposals the FP32 join is faster with the
+  // same result, so with a tensor-core precision both joins are planned and
+  // each round takes one (see the choice after each round below).
+  JoinPath jp32;
+  const bool adaptive = tc && choose_join(ctx, KNNM_FP32, params->metric, D.cap_new, D.cap_old,
+                                          d, rows_aligned, &jp32) == KNNM_OK;
+  if (tc && !adaptive) ctx->err[0] = 0;
+  const int regions = adaptive ? std::max(jp.regions(), jp32.regions()) : jp.regions();
+  const int min_regions = adaptive ? std::min(jp.regions(), jp32.regions()) : regions;
   const uint64_t per_node = 256;
-  uint64_t region_cap = ((uint64_t)N * per_node + regions - 1) / regions;
+  uint64_t region_cap = ((uint64_t)N * per_node + min_regions - 1) / min_regions;
   if (region_cap < 1024) region_cap = 1024;
 
   // Carve the scratch (two passes: size, then pointers).
@@ -268,7 +280,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     P.rtile = c.take<unsigned long long>((size_t)(2 * N + 1023) / 1024 + 1);
     P.rtotal = c.take<unsigned long long>(1);
     P.tdev = c.take<int>(1);
-    P.kth = jp.pipe ? c.take<uint64_t>((size_t)N) : nullptr;
+    P.kth = P.rec ? c.take<uint64_t>((size_t)N) : nullptr;
     P.flags = c.take<uint8_t>((size_t)N * K);
     P.new_ids = c.take<int32_t>((size_t)N * D.cap_new);
     P.new_cnt = c.take<int32_t>((size_t)N);
@@ -279,7 +291,9 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     P.aux = tc && !jp.pipe ? c.take<float4>((size_t)N) : nullptr;
     P.rmax = tc && !jp.pipe ? c.take<float>((size_t)N) : nullptr;
     P.Xe = tc && jp.pipe ? c.take<__nv_bfloat16>((size_t)N * jp.pa.dx) : nullptr;
-    P.rec = jp.pipe ? c.take<unsigned char>((size_t)N * rec_bytes(jp.pa.cap)) : nullptr;
+    P.rec = (jp.pipe || (adaptive && jp32.pipe))
+                ? c.take<unsigned char>((size_t)N * rec_bytes(jp.pipe ? jp.pa.cap : jp32.pa.cap))
+                : nullptr;
     P.prop_tgt = c.take<int32_t>(region_cap * regions);
     P.prop_key = c.take<uint64_t>(region_cap * regions);
     P.region_cnt = c.take<unsigned long long>((size_t)regions);
@@ -344,11 +358,13 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     ++launches;
   }
   if (P.Xb) {
-    KNNM_CUDA(launch_bf16_prep(rows, N, P.Xb, P.aux, P.rmax, precision == KNNM_FP16_RERANK, st));
+    KNNM_CUDA(launch_bf16_prep(rows, N, P.Xb, P.aux, P.rmax, precision == KNNM_FP16_RERANK,
+                               &P.ctr->inexact, st));
     ++launches;
   }
   if (P.Xe) {
-    KNNM_CUDA(launch_bf16_ext(rows, N, jp.pa.dx, P.Xe, precision == KNNM_FP16_RERANK, st));
+    KNNM_CUDA(launch_bf16_ext(rows, N, jp.pa.dx, P.Xe, precision == KNNM_FP16_RERANK,
+                              &P.ctr->inexact, st));
     ++launches;
   }
 
@@ -402,14 +418,16 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   sa.old_ids = P.old_ids;
   sa.old_cnt = P.old_cnt;
   sa.ctr = P.ctr;
-  if (jp.pipe) {
+  if (P.rec) {
     sa.rec = P.rec;
-    sa.rec_cap = jp.pa.cap;
+    sa.rec_cap = jp.pipe ? jp.pa.cap : jp32.pa.cap;
     sa.norms = P.norms;
     sa.K_list = K;
     sa.kth = P.kth;
     jp.pa.rec = P.rec;
     jp.pa.Xe = P.Xe;
+    jp32.pa.rec = P.rec;
+    jp32.pa.Xe = nullptr;
   }
   JoinArgs ja;
   ja.mode = in.mode;
@@ -446,18 +464,23 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   // mode, the round-index bump that the next replay reads).
   // Phase events are recorded only when launching directly; a replayed graph
   // is timed as a whole.
-  auto enqueue_round = [&](int t, cudaStream_t rs) -> int {
+  auto enqueue_round = [&](int t, cudaStream_t rs, bool use_tc) -> int {
     const bool timed = t > 0;
     KNNM_CUDA(cudaMemsetAsync(P.ctr, 0, sizeof(DevCounters), rs));
     KNNM_CUDA(cudaMemsetAsync(&P.ctr->err_row, 0xFF, 8, rs));
+    if (adaptive)  // the two joins fill different numbers of proposal regions
+      KNNM_CUDA(cudaMemsetAsync(P.region_cnt, 0, (size_t)regions * 8, rs));
     sa.t = t;
     if (timed) KNNM_CUDA(cudaEventRecord(ctx->rev[0], rs));
     KNNM_CUDA(launch_sample(sa, rs));
     if (timed) KNNM_CUDA(cudaEventRecord(ctx->rev[1], rs));
-    if (jp.pipe)
-      KNNM_CUDA(launch_pipe(precision, ja, jp.pa, jp.smem, jp.grid, rs));
+    const bool alt = adaptive && !use_tc;  // a tensor-core precision taking the FP32 join
+    const JoinPath& j = alt ? jp32 : jp;
+    const int jprec = alt ? KNNM_FP32 : precision;
+    if (j.pipe)
+      KNNM_CUDA(launch_pipe(jprec, ja, j.pa, j.smem, j.grid, rs));
     else
-      KNNM_CUDA(launch_join(precision, ja, jp.plan, rs));
+      KNNM_CUDA(launch_join(jprec, ja, j.plan, rs));
     if (timed) KNNM_CUDA(cudaEventRecord(ctx->rev[2], rs));
     KNNM_CUDA(launch_bucket_update(ma, P.prop_tgt, P.prop_key, P.region_cnt, region_cap,
                                    regions, P.tile_sum, P.total, rs));
@@ -467,50 +490,73 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
                               rs));
     return KNNM_OK;
   };
-  cudaGraphExec_t round_exec = nullptr;
-  if (ctx->use_graphs && params->max_iters > 0) {
-    sa.t_dev = P.tdev;
-    KNNM_CUDA(launch_set_int(P.tdev, 1, st));
+  // Which join each round takes: with a tensor-core precision, the tensor-core
+  // join while it pays (all rows small integers, or the last round re-ranked
+  // under 10% of its pairs), else the FP32 join.  A round that ran the FP32
+  // join predicts the re-rank share from its proposal share.
+  const bool all_exact = tc && ctx->host_ctr->inexact == 0;
+  bool use_tc = tc && (!adaptive || all_exact);
+  // In graph mode each join gets its own captured round, made when first used.
+  cudaGraphExec_t round_exec[2] = {nullptr, nullptr};
+  auto drop_graphs = [&]() {
+    for (auto& g : round_exec)
+      if (g) cudaGraphExecDestroy(g);
+  };
+  auto capture = [&](bool path_tc, cudaGraphExec_t* out) -> int {
     cudaGraph_t graph = nullptr;
     // captured on the context's own stream (the caller's may be the legacy
     // default stream, which cannot capture); replayed on the caller's stream
     if (!ctx->cap_stream)
       KNNM_CUDA(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
     KNNM_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-    int crc = enqueue_round(0, ctx->cap_stream);  // t is read from P.tdev
+    int crc = enqueue_round(0, ctx->cap_stream, path_tc);  // t is read from P.tdev
     cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &graph);
     if (crc) {
       if (graph) cudaGraphDestroy(graph);
       return crc;
     }
     if (ce != cudaSuccess) return fail(ctx, KNNM_ERR_CUDA, "round capture: %s", cudaGetErrorString(ce));
-    ce = cudaGraphInstantiate(&round_exec, graph, 0);
+    ce = cudaGraphInstantiate(out, graph, 0);
     cudaGraphDestroy(graph);
     if (ce != cudaSuccess)
       return fail(ctx, KNNM_ERR_CUDA, "round graph instantiate: %s", cudaGetErrorString(ce));
+    return KNNM_OK;
+  };
+  const bool graphs = ctx->use_graphs && params->max_iters > 0;
+  if (graphs) {
+    sa.t_dev = P.tdev;
+    KNNM_CUDA(launch_set_int(P.tdev, 1, st));
   }
   for (int t = 1; t <= params->max_iters; ++t) {
-    if (round_exec) {
+    if (graphs) {
+      cudaGraphExec_t& g = round_exec[use_tc ? 1 : 0];
+      if (!g) {
+        rc = capture(use_tc, &g);
+        if (rc) {
+          drop_graphs();
+          return rc;
+        }
+      }
       cudaEventRecord(ctx->rev[0], st);
-      cudaError_t le = cudaGraphLaunch(round_exec, st);
+      cudaError_t le = cudaGraphLaunch(g, st);
       cudaEventRecord(ctx->rev[3], st);
       if (le != cudaSuccess) {
-        cudaGraphExecDestroy(round_exec);
+        drop_graphs();
         return fail(ctx, KNNM_ERR_CUDA, "round graph launch: %s", cudaGetErrorString(le));
       }
     } else {
-      rc = enqueue_round(t, st);
+      rc = enqueue_round(t, st, use_tc);
       if (rc) return rc;
     }
     launches += 12;
     cudaError_t se = cudaStreamSynchronize(st);
     if (se != cudaSuccess) {
-      if (round_exec) cudaGraphExecDestroy(round_exec);
+      drop_graphs();
       return fail(ctx, KNNM_ERR_CUDA, "round %d: %s", t, cudaGetErrorString(se));
     }
     const DevCounters& h = *ctx->host_ctr;
     if (h.err) {
-      if (round_exec) cudaGraphExecDestroy(round_exec);
+      drop_graphs();
       return fail(ctx, KNNM_ERR_DEVICE, "round %d: device error bits 0x%llx (row %llu)", t,
                   (unsigned long long)h.err, (unsigned long long)h.err_row);
     }
@@ -519,7 +565,8 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     local.proposals[t - 1] = (int64_t)h.proposals;
     local.reranked[t - 1] = (int64_t)h.reranked;
     local.gathered[t - 1] = (int64_t)h.gathered;
-    if (round_exec) {
+    if (use_tc) local.tc_rounds |= 1ull << (t - 1);
+    if (graphs) {
       cudaEventElapsedTime(&local.ms_join[t - 1], ctx->rev[0], ctx->rev[3]);
     } else {
       cudaEventElapsedTime(&local.ms_sample[t - 1], ctx->rev[0], ctx->rev[1]);
@@ -529,8 +576,13 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     cudaGetLastError();  // a timing query that failed leaves no error behind
     local.rounds = t;
     if ((double)h.updates <= stop_at) break;
+    if (adaptive && !all_exact) {
+      const double ev = h.dist_evals > 0 ? (double)h.dist_evals : 1.0;
+      use_tc = use_tc ? (double)h.reranked / ev < 0.10
+                      : (double)h.proposals / (2.0 * ev) < 0.03;
+    }
   }
-  if (round_exec) cudaGraphExecDestroy(round_exec);
+  drop_graphs();
   KNNM_CUDA(cudaEventRecord(ctx->ev[2], st));
   int32_t* oi = P.oi ? P.oi : out_ids;
   float* od = P.od ? P.od : out_dists;
@@ -677,6 +729,173 @@ extern "C" int knnm_build(knnm_ctx* ctx, const float* S, int64_t n, int d,
                           knnm_stats* stats) {
   MergeIn in{JOINT, nullptr, 0, nullptr, S, n, nullptr, d};
   return run_merge(ctx, in, params, out_ids, out_dists, stats);
+}
+
+extern "C" int knnm_merge_tree(knnm_ctx* ctx, const float* S, int64_t n, int d, int parts,
+                               const int64_t* part_rows, const int32_t* G,
+                               const knnm_params* params, int32_t* out_ids, float* out_dists,
+                               knnm_stats* stats) {
+  auto t_wall0 = std::chrono::steady_clock::now();
+  if (!ctx) return KNNM_ERR_INVALID;
+  ctx->err[0] = 0;
+  if (!S || !G || !part_rows || !out_ids || !out_dists || parts < 1 || d < 1 || !params ||
+      n > 0x7FFFFFFFLL)
+    return fail(ctx, KNNM_ERR_INVALID, "bad merge-tree arguments");
+  const int K = params->k;
+  if (K < 1 || K > 32) return fail(ctx, KNNM_ERR_INVALID, "k=%d outside 1..32", K);
+  int64_t total = 0;
+  for (int p = 0; p < parts; ++p) {
+    if (part_rows[p] < K + 1)
+      return fail(ctx, KNNM_ERR_INVALID, "part %d has %lld rows (< k+1)", p,
+                  (long long)part_rows[p]);
+    total += part_rows[p];
+  }
+  if (total != n) return fail(ctx, KNNM_ERR_INVALID, "part rows sum to %lld, not n=%lld",
+                              (long long)total, (long long)n);
+  KNNM_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  // device copies: vectors (if on the host), two id buffers, distances
+  const bool s_dev = is_device_ptr(S), od_dev = is_device_ptr(out_dists),
+             oi_dev = is_device_ptr(out_ids);
+  float* Sd = nullptr;
+  int32_t* ids[2] = {nullptr, nullptr};
+  float* dists = nullptr;
+  DevCounters* ctr = nullptr;
+  auto release = [&]() {
+    cudaStreamSynchronize(st);
+    if (!s_dev) cudaFree(Sd);
+    cudaFree(ids[0]);
+    cudaFree(ids[1]);
+    cudaFree(dists);
+    cudaFree(ctr);
+  };
+  if ((!s_dev && cudaMalloc(&Sd, (size_t)n * d * 4) != cudaSuccess) ||
+      cudaMalloc(&ids[0], (size_t)n * K * 4) != cudaSuccess ||
+      cudaMalloc(&ids[1], (size_t)n * K * 4) != cudaSuccess ||
+      cudaMalloc(&dists, (size_t)n * K * 4) != cudaSuccess ||
+      cudaMalloc(&ctr, sizeof(DevCounters)) != cudaSuccess) {
+    cudaGetLastError();
+    release();
+    return fail(ctx, KNNM_ERR_NOMEM, "cannot allocate the merge-tree buffers");
+  }
+  int rc = KNNM_OK;
+  auto cuda_ok = [&](cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return true;
+    rc = fail(ctx, KNNM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return false;
+  };
+  if (s_dev) Sd = const_cast<float*>(S);
+  else if (!cuda_ok(cudaMemcpyAsync(Sd, S, (size_t)n * d * 4, cudaMemcpyHostToDevice, st), "copy S")) {
+    release();
+    return rc;
+  }
+  if (!cuda_ok(cudaMemcpyAsync(ids[0], G, (size_t)n * K * 4, cudaMemcpyDefault, st), "copy G")) {
+    release();
+    return rc;
+  }
+  knnm_stats total_st;
+  memset(&total_st, 0, sizeof(total_st));
+  struct Block {
+    int64_t start, rows;
+  };
+  std::vector<Block> blocks;
+  int64_t off = 0;
+  for (int p = 0; p < parts; ++p) {
+    blocks.push_back({off, part_rows[p]});
+    off += part_rows[p];
+  }
+  int cur = 0, level = 0;
+  if (parts == 1) {
+    // one part: its own lists, canonical distances, sorted
+    Rows rows{Sd, Sd, n, d};
+    float* norms = nullptr;
+    bool ok = cuda_ok(cudaMemsetAsync(ctr, 0, sizeof(DevCounters), st), "memset") &&
+              cuda_ok(cudaMemsetAsync(&ctr->err_row, 0xFF, 8, st), "memset");
+    if (ok && params->metric == KNNM_COS)
+      ok = cuda_ok(cudaMalloc(&norms, (size_t)n * 4), "norms") &&
+           cuda_ok(launch_norms(rows, n, norms, st), "norms");
+    ok = ok && cuda_ok(launch_list_dists(rows, n, ids[0], K, params->metric, norms, ids[1],
+                                         dists, ctr, st), "list distances");
+    ok = ok && cuda_ok(cudaMemcpyAsync(ctx->host_ctr, ctr, sizeof(DevCounters),
+                                       cudaMemcpyDeviceToHost, st), "counters") &&
+         cuda_ok(cudaStreamSynchronize(st), "sync");
+    cudaFree(norms);
+    if (!ok) {
+      release();
+      return rc;
+    }
+    if (ctx->host_ctr->err) {
+      release();
+      return fail(ctx, KNNM_ERR_INVALID, "input graph row %llu is malformed",
+                  (unsigned long long)ctx->host_ctr->err_row);
+    }
+    cur = 1;
+  }
+  while (blocks.size() > 1) {
+    if (level >= KNNM_MAX_ROUNDS) {
+      release();
+      return fail(ctx, KNNM_ERR_INVALID, "too many levels");
+    }
+    std::vector<Block> next;
+    const int nxt = cur ^ 1;
+    for (size_t j = 0; j < blocks.size(); j += 2) {
+      const Block a = blocks[j];
+      if (j + 1 == blocks.size()) {  // odd block: carried to the next level as it is
+        if (!cuda_ok(cudaMemcpyAsync(ids[nxt] + (size_t)a.start * K, ids[cur] + (size_t)a.start * K,
+                                     (size_t)a.rows * K * 4, cudaMemcpyDeviceToDevice, st),
+                     "carry")) {
+          release();
+          return rc;
+        }
+        next.push_back(a);
+        continue;
+      }
+      const Block b = blocks[j + 1];
+      knnm_params p = *params;
+      p.seed = mix_step(hash_prefix(params->seed, (uint64_t)level, 6, (uint64_t)(j / 2)) ^ 0ull);
+      MergeIn in{SYMMETRIC, Sd + (size_t)a.start * d, a.rows, ids[cur] + (size_t)a.start * K,
+                 Sd + (size_t)b.start * d, b.rows, ids[cur] + (size_t)b.start * K, d};
+      knnm_stats ms;
+      rc = run_merge(ctx, in, &p, ids[nxt] + (size_t)a.start * K, dists + (size_t)a.start * K,
+                     &ms);
+      if (rc) {
+        release();
+        return rc;
+      }
+      for (int t = 0; t < ms.rounds; ++t) {
+        total_st.updates[level] += ms.updates[t];
+        total_st.dist_evals[level] += ms.dist_evals[t];
+        total_st.proposals[level] += ms.proposals[t];
+        total_st.reranked[level] += ms.reranked[t];
+        total_st.gathered[level] += ms.gathered[t];
+        total_st.ms_sample[level] += ms.ms_sample[t];
+        total_st.ms_join[level] += ms.ms_join[t];
+        total_st.ms_update[level] += ms.ms_update[t];
+      }
+      total_st.kernel_launches += ms.kernel_launches;
+      total_st.ms_init += ms.ms_init;
+      total_st.ms_rounds += ms.ms_rounds;
+      total_st.ms_final += ms.ms_final;
+      next.push_back({a.start, a.rows + b.rows});
+    }
+    blocks.swap(next);
+    cur ^= 1;
+    ++level;
+  }
+  total_st.rounds = level;
+  bool ok = cuda_ok(cudaMemcpyAsync(out_ids, ids[cur], (size_t)n * K * 4,
+                                    oi_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st),
+                    "copy out ids") &&
+            cuda_ok(cudaMemcpyAsync(out_dists, dists, (size_t)n * K * 4,
+                                    od_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st),
+                    "copy out dists") &&
+            cuda_ok(cudaStreamSynchronize(st), "sync");
+  release();
+  if (!ok) return rc;
+  total_st.ms_total = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() -
+                                                               t_wall0).count();
+  if (stats) *stats = total_st;
+  return KNNM_OK;
 }
 
 extern "C" int knnm_merge_scratch_bytes(knnm_ctx* ctx, int mode, int64_t n1, int64_t n2, int d,
@@ -917,8 +1136,10 @@ extern "C" int knnm_step_join(knnm_ctx* ctx, int mode, const float* X1, int64_t 
   KNNM_CUDA(launch_pack((int64_t)N * K, ids, dists, keys, st));
   KNNM_CUDA(cudaMemcpyAsync(prev, keys, (size_t)N * K * 8, cudaMemcpyDeviceToDevice, st));
   if (params->metric == KNNM_COS) KNNM_CUDA(launch_norms(rows, N, norms, st));
-  if (Xb) KNNM_CUDA(launch_bf16_prep(rows, N, Xb, aux, rmax, precision == KNNM_FP16_RERANK, st));
-  if (Xe) KNNM_CUDA(launch_bf16_ext(rows, N, jp.pa.dx, Xe, precision == KNNM_FP16_RERANK, st));
+  if (Xb)
+    KNNM_CUDA(launch_bf16_prep(rows, N, Xb, aux, rmax, precision == KNNM_FP16_RERANK, nullptr, st));
+  if (Xe)
+    KNNM_CUDA(launch_bf16_ext(rows, N, jp.pa.dx, Xe, precision == KNNM_FP16_RERANK, nullptr, st));
   JoinArgs ja;
   ja.mode = mode;
   ja.rows = rows;

@@ -333,6 +333,7 @@ struct DevCounters {
   unsigned long long err;         // DevErr bits
   unsigned long long err_row;     // smallest offending row
   unsigned long long gathered;    // candidate rows staged by the join
+  unsigned long long inexact;     // rows that are not small integers (16-bit copies)
 };
 
 struct InitArgs {
@@ -469,7 +470,7 @@ cudaError_t launch_pipe(int precision, const JoinArgs& a, const PipeArgs& P, siz
 // 16-bit rows (BF16, or FP16 when half != 0; stored through __nv_bfloat16
 // pointers as raw 16-bit elements) with their error-data tails.
 cudaError_t launch_bf16_ext(Rows rows, int64_t N, int dx, __nv_bfloat16* Xe, int half,
-                            cudaStream_t st);
+                            unsigned long long* inexact, cudaStream_t st);
 
 // Persistent join kernels: `grid` blocks loop over the nodes.
 struct JoinPlan {
@@ -511,6 +512,6 @@ cudaError_t launch_unpack(int64_t count, const uint64_t* keys, int32_t* ids, flo
 // BF16 shadow copy and per-row error data for the tensor-core path.
 // rmax[i] = max |x| of row i when BF16 holds the row exactly as integers, else -1.
 cudaError_t launch_bf16_prep(Rows rows, int64_t N, __nv_bfloat16* Xb, float4* aux, float* rmax,
-                             int half, cudaStream_t st);
+                             int half, unsigned long long* inexact, cudaStream_t st);
 
 }  // namespace knnm

@@ -610,7 +610,8 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) k_join_ring(JoinArgs a, Pip
 //   bf16 x[0..d), zeros up to dpad = round_up(d, 16), then floats
 //   {|b|^2, |b - x| (upper), |b| (upper), canonical |x|, rmax, 0, 0, 0}.
 template <bool HALF>
-__global__ void k_bf16_ext(Rows R, int64_t N, int dx, __nv_bfloat16* Xe) {
+__global__ void k_bf16_ext(Rows R, int64_t N, int dx, __nv_bfloat16* Xe,
+                           unsigned long long* inexact) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const int d = R.d, dpad = (d + 15) & ~15;
@@ -649,6 +650,7 @@ __global__ void k_bf16_ext(Rows R, int64_t N, int dx, __nv_bfloat16* Xe) {
   tail[2] = __fsqrt_ru(nb2 * grow) * 1.000001f;
   tail[3] = __fsqrt_rn(nx2);
   tail[4] = exact ? mx : -1.0f;
+  if (!exact && inexact) atomicAdd(inexact, 1ull);
   tail[5] = tail[6] = tail[7] = 0.0f;
 }
 
@@ -761,12 +763,12 @@ cudaError_t launch_pipe(int precision, const JoinArgs& a, const PipeArgs& P, siz
 }
 
 cudaError_t launch_bf16_ext(Rows rows, int64_t N, int dx, __nv_bfloat16* Xe, int half,
-                            cudaStream_t st) {
+                            unsigned long long* inexact, cudaStream_t st) {
   if (N == 0) return cudaSuccess;
   if (half)
-    k_bf16_ext<true><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(rows, N, dx, Xe);
+    k_bf16_ext<true><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(rows, N, dx, Xe, inexact);
   else
-    k_bf16_ext<false><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(rows, N, dx, Xe);
+    k_bf16_ext<false><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(rows, N, dx, Xe, inexact);
   return cudaGetLastError();
 }
 

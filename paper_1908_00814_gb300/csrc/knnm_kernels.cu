@@ -753,7 +753,8 @@ __global__ void k_unpack(int64_t count, const uint64_t* keys, int32_t* ids, floa
 // canonical |x|}.  rmax = max |x_t| when every x_t is an integer of magnitude
 // <= 256 (BF16 holds it exactly), else -1.
 template <bool HALF>
-__global__ void k_bf16_prep(Rows R, int64_t N, __nv_bfloat16* Xb, float4* aux, float* rmax) {
+__global__ void k_bf16_prep(Rows R, int64_t N, __nv_bfloat16* Xb, float4* aux, float* rmax,
+                            unsigned long long* inexact) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const float* x = R.row(i);
@@ -789,6 +790,7 @@ __global__ void k_bf16_prep(Rows R, int64_t N, __nv_bfloat16* Xb, float4* aux, f
                                 : __fsqrt_ru(e2 * grow) * 1.000001f,
                        __fsqrt_ru(nb2 * grow) * 1.000001f, __fsqrt_rn(nx2));
   rmax[i] = exact ? mx : -1.0f;
+  if (!exact && inexact) atomicAdd(inexact, 1ull);
 }
 
 }  // namespace
@@ -913,12 +915,13 @@ cudaError_t launch_unpack(int64_t count, const uint64_t* keys, int32_t* ids, flo
 }
 
 cudaError_t launch_bf16_prep(Rows rows, int64_t N, __nv_bfloat16* Xb, float4* aux, float* rmax,
-                             int half, cudaStream_t st) {
+                             int half, unsigned long long* inexact, cudaStream_t st) {
   if (N == 0) return cudaSuccess;
   if (half)
-    k_bf16_prep<true><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(rows, N, Xb, aux, rmax);
+    k_bf16_prep<true><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(rows, N, Xb, aux, rmax, inexact);
   else
-    k_bf16_prep<false><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(rows, N, Xb, aux, rmax);
+    k_bf16_prep<false><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(rows, N, Xb, aux, rmax,
+                                                                    inexact);
   return cudaGetLastError();
 }
 

@@ -44,12 +44,14 @@ class Stats(ctypes.Structure):
                 ("ms_join", ctypes.c_float * MAX_ROUNDS),
                 ("ms_update", ctypes.c_float * MAX_ROUNDS),
                 ("ms_init", ctypes.c_float), ("ms_rounds", ctypes.c_float),
-                ("ms_final", ctypes.c_float), ("ms_total", ctypes.c_float)]
+                ("ms_final", ctypes.c_float), ("ms_total", ctypes.c_float),
+                ("tc_rounds", ctypes.c_uint64)]
 
     def as_dict(self):
         r = self.rounds
         out = {"rounds": r, "kernel_launches": self.kernel_launches, "ms_init": self.ms_init,
-               "ms_rounds": self.ms_rounds, "ms_final": self.ms_final, "ms_total": self.ms_total}
+               "ms_rounds": self.ms_rounds, "ms_final": self.ms_final, "ms_total": self.ms_total,
+               "tc_rounds": [bool((self.tc_rounds >> t) & 1) for t in range(r)]}
         for name in ("updates", "dist_evals", "proposals", "reranked", "gathered", "ms_sample",
                      "ms_join", "ms_update"):
             out[name] = list(getattr(self, name)[:r])
@@ -112,6 +114,8 @@ SIGNATURES = {
     "knnm_step_final": (_I, [_P, _I64, _I, _P, _P, _I, _P, _P, _P, _P]),
     "knnm_step_sample_noalloc": (_I, [_P, _I64, _I, _P, _P, _P, _U64, _I, _I, _I, _I, _P, _P,
                                       _P, _P]),
+    "knnm_merge_tree": (_I, [_P, _P, _I64, _I, _I, _P, _P, ctypes.POINTER(Params), _P, _P,
+                             ctypes.POINTER(Stats)]),
     "knnm_merge_scratch_bytes": (_I, [_P, _I, _I64, _I64, _I, ctypes.POINTER(Params),
                                       ctypes.POINTER(ctypes.c_uint64)]),
     "knnm_server_create": (_I, [_I, _P, _I64, _P, _I, ctypes.POINTER(Params),
@@ -255,6 +259,19 @@ class Context:
         self._check(lib().knnm_merge_joint(self.h, _ptr(S1), n1, _ptr(G1), _ptr(S_new), n2, d,
                                            ctypes.byref(p), _ptr(ids), _ptr(dists),
                                            ctypes.byref(st)))
+        return ids, dists, st.as_dict()
+
+    def merge_tree(self, S, part_rows, G, p: Params):
+        """Merge tree over consecutive parts of S (G: each part's graph, local ids).
+        Stats: rounds = levels, per-round arrays = per-level sums."""
+        n, d = S.shape
+        rows = np.ascontiguousarray(np.asarray(part_rows, dtype=np.int64))
+        ids, dists = self._outputs(S, n, p.k)
+        st = Stats()
+        self._sync_stream()
+        self._check(lib().knnm_merge_tree(self.h, _ptr(S), n, d, len(rows), _ptr(rows), _ptr(G),
+                                          ctypes.byref(p), _ptr(ids), _ptr(dists),
+                                          ctypes.byref(st)))
         return ids, dists, st.as_dict()
 
     def scratch_bytes(self, mode, n1, n2, d, p: Params) -> int:

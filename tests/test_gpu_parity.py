@@ -394,3 +394,71 @@ def test_fp16_out_of_range_rows_fall_back_to_fp32(torch, km, ctx, orc):
     X = datagen.gaussian_mixture(1600, 16, n_comp=6, seed=77)
     X[::7] *= 1.0e5   # some rows far beyond +-65504
     _smerge_both(torch, km, ctx, orc, X, 800, 10, 4, precisions=("fp16",))
+
+
+def _tree_oracle(orc, X, part_rows, G, K, seed, **kw):
+    """The merge tree composed from oracle S-Merges, same pairing and seeds."""
+    blocks, off = [], 0
+    for r in part_rows:
+        blocks.append((off, r, G[off:off + r]))
+        off += r
+    level = 0
+    while len(blocks) > 1:
+        nxt = []
+        for j in range(0, len(blocks), 2):
+            if j + 1 == len(blocks):
+                nxt.append(blocks[j])
+                continue
+            (a0, ar, ag), (b0, br, bg) = blocks[j], blocks[j + 1]
+            s = orc.hash64(seed, level, 6, j // 2, 0)
+            ids, dists, _ = orc.merge_symmetric(X[a0:a0 + ar], ag, X[b0:b0 + br], bg, K, seed=s,
+                                                **kw)
+            nxt.append((a0, ar + br, ids))
+            last = dists
+        blocks = nxt
+        level += 1
+    return blocks[0][2], last
+
+
+@pytest.mark.parametrize("parts", [8, 5])
+def test_merge_tree_parity(torch, km, ctx, orc, parts):
+    """Merge tree: levels of pairwise S-Merges over exact part graphs, bit-exact
+    with the same tree composed from oracle merges (odd blocks carried up)."""
+    K, rows = 8, 260
+    X = datagen.gaussian_mixture(parts * rows, 16, n_comp=10, seed=90 + parts)
+    part_rows = [rows] * parts
+    G = np.concatenate([orc.bruteforce_knn(X[p * rows:(p + 1) * rows], K)[0]
+                        for p in range(parts)])
+    ref_i, ref_d = _tree_oracle(orc, X, part_rows, G, K, seed=3, max_iters=4, delta=0.0)
+    for precision in ("fp32", "bf16"):
+        p = km.params(k=K, precision=precision, max_iters=4, delta=0.0, seed=3)
+        gi, gd, st = ctx.merge_tree(cuda(torch, X), part_rows, cuda(torch, G), p)
+        assert st["rounds"] == int(np.ceil(np.log2(parts)))
+        assert_same(host(gi), ref_i, f"tree ids {precision}")
+        assert_same(host(gd), ref_d, f"tree dists {precision}")
+    # one part: the input graph with canonical distances, sorted
+    gi, gd, st = ctx.merge_tree(cuda(torch, X[:rows]), [rows], cuda(torch, G[:rows]),
+                                km.params(k=K))
+    assert st["rounds"] == 0
+    for i in range(0, rows, 37):
+        assert sorted(host(gi)[i].tolist()) == sorted(G[i].tolist())
+        assert all(host(gd)[i, j] == orc.distance(0, X[i], X[host(gi)[i, j]]) for j in range(K))
+
+
+def test_tensor_core_rounds_follow_the_rerank_share(torch, km, ctx, orc):
+    """With a tensor-core precision every round of a merge of small-integer rows
+    runs the tensor-core join; on float rows the first round (almost every pair
+    a proposal) runs the FP32 join.  The graph equals the oracle either way."""
+    X = datagen.sift_like(3000, 64, seed=41)
+    _, _, st = ctx.merge_symmetric(cuda(torch, X[:1500]), cuda(torch, orc.bruteforce_knn(X[:1500], 12)[0]),
+                                   cuda(torch, X[1500:]), cuda(torch, orc.bruteforce_knn(X[1500:], 12)[0]),
+                                   km.params(k=12, precision="bf16", max_iters=5, delta=0.0))
+    assert all(st["tc_rounds"]) and sum(st["reranked"]) == 0
+    Xf = datagen.gaussian_mixture(3000, 32, n_comp=8, seed=42)
+    ref_i, ref_d, _ = _smerge_both(torch, km, ctx, orc, Xf, 1500, 12, 6, precisions=("fp16",))
+    G1, _ = orc.bruteforce_knn(Xf[:1500], 12)
+    G2, _ = orc.bruteforce_knn(Xf[1500:], 12)
+    _, _, st = ctx.merge_symmetric(cuda(torch, Xf[:1500]), cuda(torch, G1), cuda(torch, Xf[1500:]),
+                                   cuda(torch, G2), km.params(k=12, precision="fp16", max_iters=6,
+                                                              delta=0.0))
+    assert st["tc_rounds"][0] is False
