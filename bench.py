@@ -340,7 +340,7 @@ def run_serving(args, torch, knnm, ctx):
     return {
         "workload": SERVE, "resident_rows_start": n0, "resident_rows_end": int(Xr.shape[0]),
         "d": d, "k": K, "metric": "l2", "precision": "bf16_rerank", "graphs": True,
-        "slots": slots, "batch_sizes": "lognormal, median 8000, sigma 0.75, clipped 1000-64000",
+        "slots": slots, "batch_sizes": "lognormal, median 8000, sigma 1.0, clipped 1000-64000",
         "closed_loop": {"batches": nb, "rows": rows_c, "wall_s": wall,
                         "rows_per_s": rows_c / wall, "batches_per_s": sat_rate,
                         "mean_rounds": float(np.mean([i["rounds"] for i in infos_c]))},
@@ -491,10 +491,11 @@ def run_ours(args, w):
     S1, S2 = Xd[:n1].contiguous(), Xd[n1:].contiguous()
     bp = knnm.params(k=K, precision="bf16", max_iters=10, sample_rate=w["sample_rate"],
                      delta=0.001, seed=11)
-    G1, _, _ = ctx.build(S1, bp)
+    G1, _, b1 = ctx.build(S1, bp)
     bp.seed = 12
-    G2, _, _ = ctx.build(S2, bp)
+    G2, _, b2 = ctx.build(S2, bp)
     torch.cuda.synchronize()
+    build_rounds = [b1["rounds"], b2["rounds"]]
 
     def barrier():
         if world > 1:
@@ -615,7 +616,7 @@ def run_ours(args, w):
                                                     "gathered", "ms_sample", "ms_join",
                                                     "ms_update")},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": launches}
+            "gpu_launches": launches, "input_build_rounds": build_rounds}
     if not args.no_fp32:
         line["fp32_plain"] = {"value": world * w["n"] / (ms_fp / 1000.0), "ms_per_step": ms_fp,
                               "dtype": "f32", "identical_graph_to_bf16": same,

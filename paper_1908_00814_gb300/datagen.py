@@ -135,7 +135,7 @@ WORKLOADS = {
 }
 
 
-def serve_batch_sizes(count: int, seed: int, median: int = 8000, sigma: float = 0.75,
+def serve_batch_sizes(count: int, seed: int, median: int = 8000, sigma: float = 1.0,
                       lo: int = 1000, hi: int = 64000) -> np.ndarray:
     """Raw-batch sizes of the serving workload: lognormal around `median`,
     clipped to [lo, hi]."""
