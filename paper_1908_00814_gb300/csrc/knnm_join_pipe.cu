@@ -91,10 +91,11 @@ __device__ __forceinline__ float bound_tc(float g, float4 ai, float4 aj, int d, 
   }
 }
 
-__device__ __forceinline__ bool exact_rows(float ri, float rj, int d) {
-  if (ri < 0.f || rj < 0.f) return false;
-  const long long mi = (long long)ri, mj = (long long)rj;
-  return (long long)d * (mi * mi + mj * mj) < (1ll << 24);
+// Both rows are small non-negative integers and d * (max_i^2 + max_j^2) < 2^24:
+// every partial sum of the canonical accumulation is then an exact integer, and
+// so is the tensor-core Gram value.  w = d * max^2 rounded up, or -1 (tail[4]).
+__device__ __forceinline__ bool exact_rows(float wi, float wj) {
+  return wi >= 0.0f && wj >= 0.0f && __fadd_ru(wi, wj) < 16777216.0f;
 }
 
 template <int METRIC>
@@ -149,30 +150,29 @@ __device__ __forceinline__ uint64_t partner_mask(int mode, int i, int M, uint64_
 }
 
 // Writes the warp's proposals: each lane holds up to NP (target, key) slots
-// flagged in `has`; one shared atomic reserves the warp's span of the region.
+// flagged in `has`; slot x of every lane goes out with one ballot, and one
+// shared atomic reserves the warp's span of the region.
 template <int NP>
 __device__ __forceinline__ void emit_many(const JoinArgs& a, int* fill, const bool (&has)[NP],
                                           const int32_t (&tgt)[NP], const uint64_t (&key)[NP]) {
   const int lane = threadIdx.x & 31;
-  int c = 0;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned b[NP];
+  int total = 0;
 #pragma unroll
-  for (int x = 0; x < NP; ++x) c += has[x] ? 1 : 0;
-  int incl = c;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(FULL, incl, o);
-    if (lane >= o) incl += y;
+  for (int x = 0; x < NP; ++x) {
+    b[x] = __ballot_sync(FULL, has[x]);
+    total += __popc(b[x]);
   }
-  const int total = __shfl_sync(FULL, incl, 31);
   if (total == 0) return;
   int base = 0;
   if (lane == 0) base = atomicAdd(fill, total);
-  base = __shfl_sync(FULL, base, 0) + incl - c;
+  base = __shfl_sync(FULL, base, 0);
   const uint64_t region = (uint64_t)blockIdx.x * a.region_cap;
 #pragma unroll
   for (int x = 0; x < NP; ++x) {
     if (has[x]) {
-      const uint64_t pos = (uint64_t)base;
+      const uint64_t pos = (uint64_t)base + __popc(b[x] & lt);
       if (pos < a.region_cap) {
         a.prop_tgt[region + pos] = tgt[x];
         a.prop_key[region + pos] = key[x];
@@ -180,8 +180,8 @@ __device__ __forceinline__ void emit_many(const JoinArgs& a, int* fill, const bo
       } else {
         slots_insert(a.live_keys + (size_t)tgt[x] * a.K, a.K, key[x]);
       }
-      ++base;
     }
+    base += __popc(b[x]);
   }
 }
 
@@ -210,13 +210,16 @@ __device__ __forceinline__ Rec read_rec(const JoinArgs& a, const unsigned char* 
   return r;
 }
 
-// Lists the allowed pairs (i < nn, i < j < M, set test) into `pairs`.
-__device__ __forceinline__ int list_pairs(const JoinArgs& a, const Rec& rc, uint16_t* pairs) {
+// Lists the allowed pairs (i < nn, i < j < M, set test) into `pairs`, sorted by
+// first index: the whole warp expands one row's partner mask at a time.  *np0
+// receives the number of pairs whose first index is below 16.
+__device__ __forceinline__ int list_pairs(const JoinArgs& a, const Rec& rc, uint16_t* pairs,
+                                          int* np0) {
   const int lane = threadIdx.x & 31;
   const bool lo = lane < rc.M && rc.cid[lane] < a.n1;
   const bool hi = lane + 32 < rc.M && rc.cid[lane + 32] < a.n1;
   const uint64_t s1 = (uint64_t)__ballot_sync(FULL, lo) | ((uint64_t)__ballot_sync(FULL, hi) << 32);
-  uint64_t pm = lane < rc.nn ? partner_mask(a.mode, lane, rc.M, s1) : 0ull;
+  const uint64_t pm = lane < rc.nn ? partner_mask(a.mode, lane, rc.M, s1) : 0ull;
   const int cnt = __popcll(pm);
   int incl = cnt;
 #pragma unroll
@@ -225,11 +228,15 @@ __device__ __forceinline__ int list_pairs(const JoinArgs& a, const Rec& rc, uint
     if (lane >= o) incl += y;
   }
   const int np = __shfl_sync(FULL, incl, 31);
-  int pos = incl - cnt;
-  while (pm) {
-    const int j = __ffsll((long long)pm) - 1;
-    pm &= pm - 1ull;
-    pairs[pos++] = (uint16_t)((lane << 8) | j);
+  *np0 = __shfl_sync(FULL, incl, 15);
+  const int excl = incl - cnt;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int i = 0; i < rc.nn; ++i) {
+    const uint32_t m0 = (uint32_t)__shfl_sync(FULL, (unsigned)pm, i);
+    const uint32_t m1 = (uint32_t)__shfl_sync(FULL, (unsigned)(pm >> 32), i);
+    const int b = __shfl_sync(FULL, excl, i);
+    if ((m0 >> lane) & 1u) pairs[b + __popc(m0 & lt)] = (uint16_t)((i << 8) | lane);
+    if ((m1 >> lane) & 1u) pairs[b + __popc(m0) + __popc(m1 & lt)] = (uint16_t)((i << 8) | (lane + 32));
   }
   __syncwarp();
   return np;
@@ -377,7 +384,7 @@ __device__ __forceinline__ void node_tc(const JoinArgs& a, const Rec& rc, int np
         const float ri = *(const float*)(ti + 16), rj = *(const float*)(tj + 16);
         tgt[0] = rc.cid[i];
         tgt[1] = rc.cid[jj];
-        if (exact_rows(ri, rj, d)) {
+        if (exact_rows(ri, rj)) {
           const float dist = exact_value<METRIC>(g, ai, aj);
           key[0] = make_key(dist, tgt[1]);
           key[1] = make_key(dist, tgt[0]);
@@ -557,22 +564,10 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) k_join_ring(JoinArgs a, Pip
         if (slot >= R) slot -= R;
         return (const unsigned char*)(ring + (size_t)slot * stride);
       };
-      const int np = list_pairs(a, rc, pairs);
+      int np0 = 0;  // pairs with first index < 16 come first
+      const int np = list_pairs(a, rc, pairs, &np0);
       if (lane == 0) evals += (unsigned long long)np;
       if (TC) {
-        // pairs with first index < 16 come first: their count is lane 16's offset
-        int np0 = 0;
-        {
-          const bool lo = lane < rc.M && rc.cid[lane] < a.n1;
-          const bool hi = lane + 32 < rc.M && rc.cid[lane + 32] < a.n1;
-          const uint64_t s1 =
-              (uint64_t)__ballot_sync(FULL, lo) | ((uint64_t)__ballot_sync(FULL, hi) << 32);
-          const int cnt = lane < 16 && lane < rc.nn ? __popcll(partner_mask(a.mode, lane, rc.M, s1)) : 0;
-          int sum = cnt;
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
-          np0 = sum;
-        }
         node_tc<METRIC, HALF>(a, rc, np, pairs, np0, row_ptr, G, fill, reranked);
       } else {
         node_fp32<METRIC>(a, rc, np, pairs, row_ptr, fill);
@@ -649,7 +644,7 @@ __global__ void k_bf16_ext(Rows R, int64_t N, int dx, __nv_bfloat16* Xe,
   tail[1] = overflow ? __int_as_float(0x7f800000) : __fsqrt_ru(e2 * grow) * 1.000001f;
   tail[2] = __fsqrt_ru(nb2 * grow) * 1.000001f;
   tail[3] = __fsqrt_rn(nx2);
-  tail[4] = exact ? mx : -1.0f;
+  tail[4] = exact ? __double2float_ru((double)d * (double)mx * (double)mx) : -1.0f;
   if (!exact && inexact) atomicAdd(inexact, 1ull);
   tail[5] = tail[6] = tail[7] = 0.0f;
 }
