@@ -150,6 +150,7 @@ __device__ __forceinline__ float canon_dist_global4(const float* __restrict__ a,
   float acc = 0.0f;
   const float4* a4 = reinterpret_cast<const float4*>(a);
   const float4* b4 = reinterpret_cast<const float4*>(b);
+#pragma unroll 4
   for (int t = 0; t < (d >> 2); ++t) {
     const float4 x = __ldg(a4 + t), y = __ldg(b4 + t);
     acc = Canon<METRIC>::step(acc, x.x, y.x);

@@ -604,40 +604,73 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) k_join_ring(JoinArgs a, Pip
 // BF16 rows with their error data in a 32-byte tail:
 //   bf16 x[0..d), zeros up to dpad = round_up(d, 16), then floats
 //   {|b|^2, |b - x| (upper), |b| (upper), canonical |x|, rmax, 0, 0, 0}.
+// One warp per 32 rows.  Each 32-row x 32-dimension chunk is read coalesced
+// into shared memory; then every lane walks its own row through the chunk in
+// index order (the canonical norm needs the in-order sum) and writes its 16-bit
+// elements eight at a time.
+constexpr int EXT_WARPS = 8;
+
 template <bool HALF>
-__global__ void k_bf16_ext(Rows R, int64_t N, int dx, __nv_bfloat16* Xe,
-                           unsigned long long* inexact) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+__global__ void __launch_bounds__(EXT_WARPS * 32) k_bf16_ext(Rows R, int64_t N, int dx,
+                                                            __nv_bfloat16* Xe,
+                                                            unsigned long long* inexact) {
+  __shared__ float tile[EXT_WARPS][32][33];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t row0 = ((int64_t)blockIdx.x * EXT_WARPS + w) * 32;
+  if (row0 >= N) return;  // whole warp
   const int d = R.d, dpad = (d + 15) & ~15;
-  const float* x = R.row(i);
-  __nv_bfloat16* o = Xe + (size_t)i * dx;
+  const int64_t i = row0 + lane;
+  const bool live = i < N;
+  __nv_bfloat16* o = Xe + (size_t)(live ? i : row0) * dx;
   float nb2 = 0.f, e2 = 0.f, nx2 = 0.f, mx = 0.f;
   bool exact = true, overflow = false;
-  for (int t = 0; t < d; ++t) {
-    const float v = __ldg(x + t);
-    float bf;
-    if (HALF) {
-      // saturated: a row with a value beyond FP16 range gets an infinite
-      // error bound below, so every pair with it is re-ranked
-      const float vs = fminf(fmaxf(v, -65504.0f), 65504.0f);
-      overflow = overflow || vs != v;
-      const __half h = __float2half_rn(vs);
-      bf = __half2float(h);
-      reinterpret_cast<__half*>(o)[t] = h;
-    } else {
-      const __nv_bfloat16 b = __float2bfloat16_rn(v);
-      bf = __bfloat162float(b);
-      o[t] = b;
+  for (int t0 = 0; t0 < d; t0 += 32) {
+    for (int r = 0; r < 32; ++r) {
+      const int64_t rr = row0 + r;
+      tile[w][r][lane] = (rr < N && t0 + lane < d) ? __ldg(R.row(rr) + t0 + lane) : 0.0f;
     }
-    nb2 = __fmaf_rn(bf, bf, nb2);
-    const float e = __fsub_rn(bf, v);  // exact: bf and v are within a factor of two
-    e2 = __fmaf_rn(e, e, e2);
-    nx2 = __fmaf_rn(v, v, nx2);
-    exact = exact && v == rintf(v) && v >= 0.0f && v <= (HALF ? 2048.0f : 256.0f);
-    mx = fmaxf(mx, fabsf(v));
+    __syncwarp();
+    const int tn = min(32, d - t0);
+    for (int q0 = 0; q0 < tn; q0 += 8) {
+      uint32_t packed[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (q0 + q < tn) {
+          const float v = tile[w][lane][q0 + q];
+          float bf;
+          uint32_t bits;
+          if (HALF) {
+            // saturated: a row with a value beyond FP16 range gets an infinite
+            // error bound below, so every pair with it is re-ranked
+            const float vs = fminf(fmaxf(v, -65504.0f), 65504.0f);
+            overflow = overflow || vs != v;
+            const __half h = __float2half_rn(vs);
+            bf = __half2float(h);
+            bits = __half_as_ushort(h);
+          } else {
+            const __nv_bfloat16 b = __float2bfloat16_rn(v);
+            bf = __bfloat162float(b);
+            bits = __bfloat16_as_ushort(b);
+          }
+          packed[q >> 1] |= bits << ((q & 1) * 16);
+          nb2 = __fmaf_rn(bf, bf, nb2);
+          const float e = __fsub_rn(bf, v);  // exact: bf and v are within a factor of two
+          e2 = __fmaf_rn(e, e, e2);
+          nx2 = __fmaf_rn(v, v, nx2);
+          exact = exact && v == rintf(v) && v >= 0.0f && v <= (HALF ? 2048.0f : 256.0f);
+          mx = fmaxf(mx, fabsf(v));
+        }
+      }
+      // elements past d stay +0 (the same bits in both formats); d % 8 == 0 on
+      // the tensor-core paths, so q0 + 8 <= dpad
+      if (live)
+        *reinterpret_cast<uint4*>(o + t0 + q0) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+    }
+    __syncwarp();
   }
-  for (int t = d; t < dpad; ++t) o[t] = __float2bfloat16_rn(0.0f);  // +0 in both formats
+  if (!live) return;
+  for (int t = (d + 7) & ~7; t < dpad; t += 8)
+    *reinterpret_cast<uint4*>(o + t) = make_uint4(0u, 0u, 0u, 0u);
   const float grow = 1.0f + (float)(d + 2) * 1.2e-7f;
   float* tail = (float*)(o + dpad);
   tail[0] = nb2;
@@ -760,10 +793,11 @@ cudaError_t launch_pipe(int precision, const JoinArgs& a, const PipeArgs& P, siz
 cudaError_t launch_bf16_ext(Rows rows, int64_t N, int dx, __nv_bfloat16* Xe, int half,
                             unsigned long long* inexact, cudaStream_t st) {
   if (N == 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((N + EXT_WARPS * 32 - 1) / (EXT_WARPS * 32));
   if (half)
-    k_bf16_ext<true><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(rows, N, dx, Xe, inexact);
+    k_bf16_ext<true><<<blocks, EXT_WARPS * 32, 0, st>>>(rows, N, dx, Xe, inexact);
   else
-    k_bf16_ext<false><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(rows, N, dx, Xe, inexact);
+    k_bf16_ext<false><<<blocks, EXT_WARPS * 32, 0, st>>>(rows, N, dx, Xe, inexact);
   return cudaGetLastError();
 }
 

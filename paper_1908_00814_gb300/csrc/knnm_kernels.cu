@@ -85,7 +85,20 @@ __device__ int32_t draw_random(uint64_t seed, int64_t i, int64_t base, int64_t n
   int got = 0;
   const uint64_t pre = hash_prefix(seed, 0, STREAM_INIT, (uint64_t)i);
   const int limit = 32 * K;
-  for (int c0 = 0; c0 < limit && got < want; c0 += 32) {
+  {
+    // First 32 candidates at once: with nothing chosen yet, candidate c is taken
+    // iff it is not self and no earlier candidate drew the same id (an earlier
+    // equal one was either taken, or rejected for the same reason).
+    const int64_t j = base + (int64_t)(mix_step(pre ^ (uint64_t)lane) % (uint64_t)n_src);
+    const bool valid = j != i;
+    const unsigned same = __match_any_sync(FULL, valid ? j : -1 - (int64_t)lane);
+    const unsigned acc = __ballot_sync(FULL, valid && (same & lanemask_lt()) == 0);
+    got = min(want, __popc(acc));
+    const int src = lane < got ? (int)__fns(acc, 0, lane + 1) : 0;
+    const int64_t js = __shfl_sync(FULL, j, src);
+    if (lane < got) chosen = (int32_t)js;
+  }
+  for (int c0 = 32; c0 < limit && got < want; c0 += 32) {
     int c = c0 + lane;
     int64_t j = base + (int64_t)(mix_step(pre ^ (uint64_t)c) % (uint64_t)n_src);
     bool valid = c < limit && j != i;
@@ -117,8 +130,61 @@ __device__ int32_t draw_random(uint64_t seed, int64_t i, int64_t base, int64_t n
   return chosen;
 }
 
+// Canonical distances from row i to the rows g (one per lane, -1 for none) for
+// 16-byte aligned rows with d % 4 == 0.  The warp stages INIT_CH dimensions of
+// every listed row at a time in shared memory with coalesced 16-byte
+// asynchronous copies (two rows per warp instruction), then each lane
+// continues its own in-order accumulation from there: the same arithmetic as
+// canon_dist_global4, with all rows' loads in flight at once.
+constexpr int INIT_CH = 64;              // dimensions staged per pass
+constexpr int INIT_STRIDE = INIT_CH + 4;  // floats per staged row (conflict-free float4 reads)
+
+__device__ __forceinline__ void init_cp16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+
+template <int METRIC>
+__device__ __forceinline__ float staged_dist(const Rows& R, int64_t i, int32_t g, int rows,
+                                             const float* norms, float* buf) {
+  const int lane = threadIdx.x & 31, d = R.d;
+  const float4* xi = reinterpret_cast<const float4*>(R.row(i));
+  const float* yj = buf + lane * INIT_STRIDE;
+  float acc = 0.0f;
+  for (int c = 0; c < d; c += INIT_CH) {
+    const int q4 = min(INIT_CH, d - c) >> 2;  // float4 per row this pass
+    for (int s0 = 0; s0 < rows; s0 += 2) {
+      const int slot = s0 + (lane >> 4), o = lane & 15;
+      const int32_t gs = __shfl_sync(FULL, g, slot & 31);
+      if (slot < rows && gs >= 0 && o < q4)
+        init_cp16(buf + slot * INIT_STRIDE + o * 4, R.row(gs) + c + o * 4);
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncwarp();
+    if (g >= 0) {
+      for (int t = 0; t < q4; ++t) {
+        const float4 x = __ldg(xi + (c >> 2) + t);
+        const float4 y = *reinterpret_cast<const float4*>(yj + 4 * t);
+        acc = Canon<METRIC>::step(acc, x.x, y.x);
+        acc = Canon<METRIC>::step(acc, x.y, y.y);
+        acc = Canon<METRIC>::step(acc, x.z, y.z);
+        acc = Canon<METRIC>::step(acc, x.w, y.w);
+      }
+    }
+    __syncwarp();
+  }
+  float na = 0.f, nb = 0.f;
+  if (METRIC == COS) {
+    na = norms[i];
+    nb = g >= 0 ? norms[g] : 0.f;
+  }
+  return canon_finish<METRIC>(acc, na, nb);
+}
+
 template <int METRIC>
 __global__ void __launch_bounds__(BLOCK) k_init(InitArgs a) {
+  extern __shared__ __align__(16) float init_buf[];  // [warps][32][INIT_STRIDE] when staged
+  float* wbuf = init_buf + (threadIdx.x >> 5) * 32 * INIT_STRIDE;
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
   const int K = a.K, Kk = a.K_keep, Kr = a.K - a.K_keep;
@@ -149,7 +215,11 @@ __global__ void __launch_bounds__(BLOCK) k_init(InitArgs a) {
       if (__any_sync(FULL, bad) && lane == 0) raise_err(a.ctr, DERR_BAD_ID, i);
       if (__any_sync(FULL, dup) && lane == 0) raise_err(a.ctr, DERR_DUP_ID, i);
       uint64_t key = KEY_EMPTY;
-      if (lane < K && !bad) {
+      if (a.vec4) {
+        const int32_t g = (lane < K && !bad) ? (int32_t)(own_base + loc) : -1;
+        const float dist = staged_dist<METRIC>(a.rows, i, g, K, a.norms, wbuf);
+        if (g >= 0) key = make_key(dist, g);
+      } else if (lane < K && !bad) {
         int64_t g = own_base + loc;
         key = make_key(dist_rows<METRIC>(a.rows, i, g, a.norms, a.vec4), (int32_t)g);
       }
@@ -168,8 +238,13 @@ __global__ void __launch_bounds__(BLOCK) k_init(InitArgs a) {
     }
     int32_t drawn = draw_random(a.seed, i, base, n_src, want, K);
     uint64_t dkey = KEY_EMPTY;
-    if (lane < want)
+    if (a.vec4) {
+      const int32_t g = lane < want ? drawn : -1;
+      const float dist = staged_dist<METRIC>(a.rows, i, g, want, a.norms, wbuf);
+      if (g >= 0) dkey = make_key(dist, g);
+    } else if (lane < want) {
       dkey = make_key(dist_rows<METRIC>(a.rows, i, drawn, a.norms, a.vec4), drawn);
+    }
     int first = in ? Kk : 0;
     uint64_t shifted = __shfl_sync(FULL, dkey, (lane - first) & 31);
     uint64_t v = lane < first ? kept : (lane < K ? shifted : KEY_EMPTY);
@@ -270,20 +345,18 @@ __global__ void __launch_bounds__(BLOCK) k_sample_scatter(SampleArgs a) {
   for (int64_t u = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5); u < a.N;
        u += nwarps) {
     const int nf = a.new_cnt[u], of = a.old_cnt[u];
-    if (lane < nf) {
-      const int32_t v = a.new_ids[(size_t)u * a.cap_new + lane];
-      const uint64_t key =
-          sampling_key(hash_prefix(a.seed, t, STREAM_REV_NEW, (uint64_t)v), (int32_t)u);
-      const int pos = atomicSub(&a.rcnt[2 * (size_t)v], 1) - 1;
-      a.rbucket[a.roffs[2 * (size_t)v] + (uint64_t)pos] = key;
-    }
-    if (lane < of) {
-      const int32_t v = a.old_ids[(size_t)u * a.cap_old + lane];
-      const uint64_t key =
-          sampling_key(hash_prefix(a.seed, t, STREAM_REV_OLD, (uint64_t)v), (int32_t)u);
-      const int pos = atomicSub(&a.rcnt[2 * (size_t)v + 1], 1) - 1;
-      a.rbucket[a.roffs[2 * (size_t)v + 1] + (uint64_t)pos] = key;
-    }
+    const bool hn = lane < nf, ho = lane < of;
+    const int32_t vn = hn ? a.new_ids[(size_t)u * a.cap_new + lane] : 0;
+    const int32_t vo = ho ? a.old_ids[(size_t)u * a.cap_old + lane] : 0;
+    // both slot claims in flight before either store
+    const int pn = hn ? atomicSub(&a.rcnt[2 * (size_t)vn], 1) - 1 : 0;
+    const int po = ho ? atomicSub(&a.rcnt[2 * (size_t)vo + 1], 1) - 1 : 0;
+    if (hn)
+      a.rbucket[a.roffs[2 * (size_t)vn] + (uint64_t)pn] =
+          sampling_key(hash_prefix(a.seed, t, STREAM_REV_NEW, (uint64_t)vn), (int32_t)u);
+    if (ho)
+      a.rbucket[a.roffs[2 * (size_t)vo + 1] + (uint64_t)po] =
+          sampling_key(hash_prefix(a.seed, t, STREAM_REV_OLD, (uint64_t)vo), (int32_t)u);
   }
 }
 
@@ -543,14 +616,25 @@ __global__ void __launch_bounds__(256) k_scan_apply(const int32_t* cnt, int64_t 
 __global__ void k_scatter(const int32_t* prop_tgt, const uint64_t* prop_key,
                           const unsigned long long* region_cnt, uint64_t region_cap,
                           int32_t* cnt, const unsigned long long* offs, uint64_t* bucket) {
+  constexpr int U = 4;  // proposals per thread in flight: independent atomics overlap
   const uint64_t n = region_cnt[blockIdx.x];
   const uint64_t base = (uint64_t)blockIdx.x * region_cap;
-  const uint64_t stride = (uint64_t)blockDim.x * gridDim.y;
-  for (uint64_t o = (uint64_t)blockIdx.y * blockDim.x + threadIdx.x; o < n; o += stride) {
-    const int32_t tgt = prop_tgt[base + o];
-    const uint64_t key = prop_key[base + o];
-    const int pos = atomicSub(&cnt[tgt], 1) - 1;
-    bucket[offs[tgt] + (uint64_t)pos] = key;
+  const uint64_t step = (uint64_t)blockDim.x * gridDim.y * U;
+  for (uint64_t o0 = ((uint64_t)blockIdx.y * blockDim.x) * U + threadIdx.x; o0 < n; o0 += step) {
+    int32_t tgt[U];
+    uint64_t key[U];
+    int pos[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint64_t o = o0 + (uint64_t)u * blockDim.x;
+      tgt[u] = o < n ? prop_tgt[base + o] : -1;
+      key[u] = o < n ? prop_key[base + o] : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) pos[u] = tgt[u] >= 0 ? atomicSub(&cnt[tgt[u]], 1) - 1 : 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (tgt[u] >= 0) bucket[offs[tgt[u]] + (uint64_t)pos[u]] = key[u];
   }
 }
 
@@ -799,15 +883,26 @@ __global__ void k_bf16_prep(Rows R, int64_t N, __nv_bfloat16* Xb, float4* aux, f
 // Launchers
 // ---------------------------------------------------------------------------
 
+template <int METRIC>
+cudaError_t launch_init_m(const InitArgs& a, int grid, cudaStream_t st) {
+  const size_t smem = a.vec4 ? (size_t)WARPS_PER_BLOCK * 32 * INIT_STRIDE * 4 : 0;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_init<METRIC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_init<METRIC><<<grid, BLOCK, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_init(const InitArgs& a, cudaStream_t st) {
   int grid = grid_for_warps(a.N);
   switch (a.metric) {
-    case L2: k_init<L2><<<grid, BLOCK, 0, st>>>(a); break;
-    case IP: k_init<IP><<<grid, BLOCK, 0, st>>>(a); break;
-    case COS: k_init<COS><<<grid, BLOCK, 0, st>>>(a); break;
-    default: k_init<L1><<<grid, BLOCK, 0, st>>>(a); break;
+    case L2: return launch_init_m<L2>(a, grid, st);
+    case IP: return launch_init_m<IP>(a, grid, st);
+    case COS: return launch_init_m<COS>(a, grid, st);
+    default: return launch_init_m<L1>(a, grid, st);
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_norms(Rows rows, int64_t N, float* norms, cudaStream_t st) {
