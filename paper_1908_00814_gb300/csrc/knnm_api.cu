@@ -234,11 +234,19 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   const bool adaptive = tc && choose_join(ctx, KNNM_FP32, params->metric, D.cap_new, D.cap_old,
                                           d, rows_aligned, &jp32) == KNNM_OK;
   if (tc && !adaptive) ctx->err[0] = 0;
-  const int regions = adaptive ? std::max(jp.regions(), jp32.regions()) : jp.regions();
-  const int min_regions = adaptive ? std::min(jp.regions(), jp32.regions()) : regions;
+  // One proposal region per join block, sized for that join's grid; the two
+  // joins of the per-round choice share one allocation.
   const uint64_t per_node = 256;
-  uint64_t region_cap = ((uint64_t)N * per_node + min_regions - 1) / min_regions;
-  if (region_cap < 1024) region_cap = 1024;
+  auto cap_for = [&](int regions_of) {
+    uint64_t c = ((uint64_t)N * per_node + regions_of - 1) / regions_of;
+    return c < 1024 ? (uint64_t)1024 : c;
+  };
+  const int regions = adaptive ? std::max(jp.regions(), jp32.regions()) : jp.regions();
+  const uint64_t region_cap = cap_for(jp.regions());
+  const uint64_t region_cap32 = adaptive ? cap_for(jp32.regions()) : region_cap;
+  const uint64_t prop_slots =
+      std::max((uint64_t)jp.regions() * region_cap,
+               adaptive ? (uint64_t)jp32.regions() * region_cap32 : (uint64_t)0);
 
   // Carve the scratch (two passes: size, then pointers).
   struct Ptrs {
@@ -294,15 +302,15 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     P.rec = (jp.pipe || (adaptive && jp32.pipe))
                 ? c.take<unsigned char>((size_t)N * rec_bytes(jp.pipe ? jp.pa.cap : jp32.pa.cap))
                 : nullptr;
-    P.prop_tgt = c.take<int32_t>(region_cap * regions);
-    P.prop_key = c.take<uint64_t>(region_cap * regions);
+    P.prop_tgt = c.take<int32_t>(prop_slots);
+    P.prop_key = c.take<uint64_t>(prop_slots);
     P.region_cnt = c.take<unsigned long long>((size_t)regions);
     P.ctr = c.take<DevCounters>(1);
     P.pcnt = c.take<int32_t>((size_t)N);
     P.offs = c.take<unsigned long long>((size_t)N + 1);
     P.tile_sum = c.take<unsigned long long>((size_t)(N + 1023) / 1024 + 1);
     P.total = c.take<unsigned long long>(1);
-    P.bucket = c.take<uint64_t>(region_cap * regions);
+    P.bucket = c.take<uint64_t>(prop_slots);
   };
   Carver sizer;
   carve(sizer);
@@ -477,13 +485,15 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     const bool alt = adaptive && !use_tc;  // a tensor-core precision taking the FP32 join
     const JoinPath& j = alt ? jp32 : jp;
     const int jprec = alt ? KNNM_FP32 : precision;
+    const uint64_t rcap = alt ? region_cap32 : region_cap;
+    ja.region_cap = rcap;
     if (j.pipe)
       KNNM_CUDA(launch_pipe(jprec, ja, j.pa, j.smem, j.grid, rs));
     else
       KNNM_CUDA(launch_join(jprec, ja, j.plan, rs));
     if (timed) KNNM_CUDA(cudaEventRecord(ctx->rev[2], rs));
-    KNNM_CUDA(launch_bucket_update(ma, P.prop_tgt, P.prop_key, P.region_cnt, region_cap,
-                                   regions, P.tile_sum, P.total, rs));
+    KNNM_CUDA(launch_bucket_update(ma, P.prop_tgt, P.prop_key, P.region_cnt, rcap, j.regions(),
+                                   P.tile_sum, P.total, rs));
     if (timed) KNNM_CUDA(cudaEventRecord(ctx->rev[3], rs));
     if (sa.t_dev) KNNM_CUDA(launch_bump_int(P.tdev, rs));
     KNNM_CUDA(cudaMemcpyAsync(ctx->host_ctr, P.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost,
@@ -1183,8 +1193,9 @@ extern "C" int knnm_step_join(knnm_ctx* ctx, int mode, const float* X1, int64_t 
   rc = read_counters(ctx, ctr);
   if (rc) return rc;
   if (ctx->host_ctr->err)
-    return fail(ctx, KNNM_ERR_DEVICE, "device error bits 0x%llx",
-                (unsigned long long)ctx->host_ctr->err);
+    return fail(ctx, KNNM_ERR_DEVICE, "device error bits 0x%llx (row %llu)",
+                (unsigned long long)ctx->host_ctr->err,
+                (unsigned long long)ctx->host_ctr->err_row);
   if (updates) *updates = (int64_t)ctx->host_ctr->updates;
   if (dist_evals) *dist_evals = (int64_t)ctx->host_ctr->dist_evals;
   return KNNM_OK;
