@@ -366,41 +366,48 @@ __device__ __forceinline__ void node_tc(const JoinArgs& a, const Rec& rc, int np
     }
     __syncwarp();
     const int q_lo = mt == 0 ? 0 : np0, q_hi = mt == 0 ? np0 : np;
-    for (int q0 = q_lo; q0 < q_hi; q0 += 32) {
-      const int q = q0 + lane;
-      bool has[2] = {false, false};
-      int32_t tgt[2] = {0, 0};
-      uint64_t key[2] = {0ull, 0ull};
-      bool mark = false;
-      uint16_t pr = 0;
-      if (q < q_hi) {
-        pr = pairs[q];
-        const int i = pr >> 8, jj = pr & 0xFF;
-        const float g = G[(i & 15) * GSTR + jj];
-        const unsigned char* ti = row_ptr(i) + dpad * 2;
-        const unsigned char* tj = row_ptr(jj) + dpad * 2;
-        const float4 ai = *(const float4*)ti;
-        const float4 aj = *(const float4*)tj;
-        const float ri = *(const float*)(ti + 16), rj = *(const float*)(tj + 16);
-        tgt[0] = rc.cid[i];
-        tgt[1] = rc.cid[jj];
-        if (exact_rows(ri, rj)) {
-          const float dist = exact_value<METRIC>(g, ai, aj);
-          key[0] = make_key(dist, tgt[1]);
-          key[1] = make_key(dist, tgt[0]);
-          has[0] = key[0] < rc.kth[i];
-          has[1] = key[1] < rc.kth[jj];
-        } else {
-          float est;
-          const float E = bound_tc<METRIC>(g, ai, aj, d, &est);
-          mark = est - E <= fmaxf(key_dist(rc.kth[i]), key_dist(rc.kth[jj]));
+    // two pairs per lane per pass: independent chains for the schedulers
+    for (int q0 = q_lo; q0 < q_hi; q0 += 64) {
+      bool has[4] = {false, false, false, false};
+      int32_t tgt[4] = {0, 0, 0, 0};
+      uint64_t key[4] = {0ull, 0ull, 0ull, 0ull};
+      bool mark[2] = {false, false};
+      uint16_t pr[2] = {0, 0};
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int q = q0 + 32 * u + lane;
+        if (q < q_hi) {
+          pr[u] = pairs[q];
+          const int i = pr[u] >> 8, jj = pr[u] & 0xFF;
+          const float g = G[(i & 15) * GSTR + jj];
+          const unsigned char* ti = row_ptr(i) + dpad * 2;
+          const unsigned char* tj = row_ptr(jj) + dpad * 2;
+          const float4 ai = *(const float4*)ti;
+          const float4 aj = *(const float4*)tj;
+          const float ri = *(const float*)(ti + 16), rj = *(const float*)(tj + 16);
+          tgt[2 * u] = rc.cid[i];
+          tgt[2 * u + 1] = rc.cid[jj];
+          if (exact_rows(ri, rj)) {
+            const float dist = exact_value<METRIC>(g, ai, aj);
+            key[2 * u] = make_key(dist, tgt[2 * u + 1]);
+            key[2 * u + 1] = make_key(dist, tgt[2 * u]);
+            has[2 * u] = key[2 * u] < rc.kth[i];
+            has[2 * u + 1] = key[2 * u + 1] < rc.kth[jj];
+          } else {
+            float est;
+            const float E = bound_tc<METRIC>(g, ai, aj, d, &est);
+            mark[u] = est - E <= fmaxf(key_dist(rc.kth[i]), key_dist(rc.kth[jj]));
+          }
         }
       }
-      emit_many<2>(a, fill, has, tgt, key);
-      // entries up to q0 + 31 are consumed, so the front of the list is free
-      const unsigned b = __ballot_sync(FULL, mark);
-      if (mark) pairs[nr + __popc(b & ((1u << lane) - 1u))] = pr;
-      nr += __popc(b);
+      emit_many<4>(a, fill, has, tgt, key);
+      // entries up to q0 + 63 are consumed, so the front of the list is free
+      const unsigned lt = (1u << lane) - 1u;
+      const unsigned b0 = __ballot_sync(FULL, mark[0]), b1 = __ballot_sync(FULL, mark[1]);
+      __syncwarp();
+      if (mark[0]) pairs[nr + __popc(b0 & lt)] = pr[0];
+      if (mark[1]) pairs[nr + __popc(b0) + __popc(b1 & lt)] = pr[1];
+      nr += __popc(b0) + __popc(b1);
       __syncwarp();
     }
     __syncwarp();
