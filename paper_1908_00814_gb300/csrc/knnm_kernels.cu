@@ -674,11 +674,20 @@ __global__ void __launch_bounds__(BLOCK) k_merge_lists(MergeArgs a) {
         continue;
       }
       {
-        // many survivors: drop repeats inside the chunk, sort it, keep the 32
+        // many survivors: sort the chunk and drop its repeats, keep the 32
         // smallest of (list, chunk) and remove keys the list already holds;
         // that is the answer unless repeats pushed distinct keys past 32
-        const bool first = (__match_any_sync(FULL, x) & lanemask_lt()) == 0;
-        const uint64_t m = warp_merge_lo32(cur, warp_sort32(first ? x : KEY_EMPTY));
+        const uint64_t xs = warp_sort32(x);
+        const uint64_t xp = __shfl_up_sync(FULL, xs, 1);
+        const bool keep_x = xs != KEY_EMPTY && (lane == 0 || xs != xp);
+        const unsigned kx = __ballot_sync(FULL, keep_x);
+        stage[w][lane] = KEY_EMPTY;
+        __syncwarp();
+        if (keep_x) stage[w][__popc(kx & lanemask_lt())] = xs;
+        __syncwarp();
+        const uint64_t xd = stage[w][lane];  // sorted, repeats dropped, KEY_EMPTY after
+        __syncwarp();
+        const uint64_t m = warp_merge_lo32(cur, xd);
         const uint64_t mp = __shfl_up_sync(FULL, m, 1);
         const bool keep = m != KEY_EMPTY && (lane == 0 || m != mp);
         const unsigned km = __ballot_sync(FULL, keep);
@@ -711,19 +720,26 @@ __global__ void __launch_bounds__(BLOCK) k_merge_lists(MergeArgs a) {
       cur = lane < K ? stage[w][lane] : KEY_EMPTY;
       __syncwarp();
     }
-    // flags against the round-start snapshot; c_t counts entries absent from it
-    const uint64_t pk = lane < K ? a.prev_keys[(size_t)v * K + lane] : KEY_EMPTY - 1;
+    // flags against the round-start snapshot: an entry is old when the same key
+    // was in the list at round start.  The snapshot is sorted ascending (empty
+    // places last), so each entry finds its place by a five-step binary search.
+    const uint64_t pk = lane < K ? a.prev_keys[(size_t)v * K + lane] : KEY_EMPTY;
     const uint8_t pf = lane < K ? a.flags[(size_t)v * K + lane] : FLAG_NEW;
-    bool found = false;
-    uint8_t fl = FLAG_NEW;
-    for (int m = 0; m < K; ++m) {
-      const uint64_t o = __shfl_sync(FULL, pk, m);
-      const uint8_t of = (uint8_t)__shfl_sync(FULL, (int)pf, m);
-      if (o == cur) {
-        found = true;
-        fl = of;
-      }
+    int at = 0;  // number of snapshot keys <= cur among places 0..30
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const uint64_t probe = __shfl_sync(FULL, pk, at + step - 1);
+      if (probe <= cur) at += step;
     }
+    const uint64_t last = __shfl_sync(FULL, pk, 31);
+    if (at == 31 && last <= cur) at = 32;
+    const int idx = at > 0 ? at - 1 : 0;
+    const uint64_t o = __shfl_sync(FULL, pk, idx);
+    const uint8_t of = (uint8_t)__shfl_sync(FULL, (int)pf, idx);
+    const uint64_t kth_prev = __shfl_sync(FULL, pk, K - 1);
+    const bool found = cur == KEY_EMPTY ? kth_prev == KEY_EMPTY : (at > 0 && idx < K && o == cur);
+    const uint8_t fl = found ? (cur == KEY_EMPTY ? (uint8_t)__shfl_sync(FULL, (int)pf, K - 1) : of)
+                             : (uint8_t)FLAG_NEW;
     __syncwarp();
     if (lane < K) {
       a.keys[(size_t)v * K + lane] = cur;
