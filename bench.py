@@ -355,6 +355,23 @@ def run_serving(args, torch, knnm, ctx):
     }
 
 
+def join_traffic():
+    """DRAM bytes per launch of the join, from the committed ncu capture of the timed
+    merge's join launches; null when the kernel source has changed since."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_join_ring_traffic_smerge_sift_1m.json")
+    try:
+        with open(path) as f:
+            cap = json.load(f)
+        with open(os.path.join(ROOT, cap["source"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except (OSError, KeyError, ValueError):
+        return None, "no capture"
+    if sha != cap["source_sha256"]:
+        return None, "kernel changed since the capture"
+    return cap["mean_dram_bytes_per_launch"], os.path.relpath(path, ROOT)
+
+
 def timed_call(torch, fn, steps, warmup):
     """Device time of `fn` (ms, mean over steps) with CUDA events on the current stream."""
     for _ in range(warmup):
@@ -565,9 +582,11 @@ def run_ours(args, w):
     dominant = max(tot, key=tot.get)
     achieved = bytes_join / (tot["join"] / 1000.0) / 1e9 if tot["join"] > 0 else 0.0
     hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
-    roofline = {"kernel": "k_join_bf16 (distance block)", "bound": "hbm", "achieved": achieved,
-                "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "peak_source": f"hbm_gbs of {peaks_kind}", "traffic": None,
+    traffic, traffic_note = join_traffic()
+    roofline = {"kernel": "k_join_ring (BF16 tensor-core join)", "bound": "hbm",
+                "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "peak_source": f"hbm_gbs of {peaks_kind}", "traffic": traffic,
+                "traffic_source": traffic_note,
                 "time_share": {k: v / sum(tot.values()) for k, v in tot.items()},
                 "dominant_phase": dominant, "launches": launches_join,
                 "algorithmic_bytes_per_launch": bytes_join / max(launches_join, 1)}
