@@ -421,7 +421,47 @@ def run_other(args, name):
         print(f"# {label}: {ms:.1f} ms, recall {r['recall_at_10']:.4f}", file=sys.stderr,
               flush=True)
 
-    if w["kind"] == "joint":
+    if w["kind"] == "hmerge":
+        # H-Merge (Sec. 3.3) from 64 rows, layers of 64, 512, 4096 and 32768 kept
+        # (the hierarchy sizes of the paper's search experiments), beside an
+        # NN-Descent build of the whole set
+        first, keep = 64, [64, 512, 4096, 32768]
+        for prec in ("bf16", "fp32"):
+            p = knnm.params(k=K, precision=prec, max_iters=w["rounds"],
+                            sample_rate=w["sample_rate"], delta=0.001, seed=0)
+            Xh = Xd
+
+            def call():
+                perm, ids, dists, layers, st = ctx.hmerge(Xh, first, p, layers=keep)
+                return (torch.from_numpy(perm), ids, dists, layers, st)
+            for _ in range(warmup):
+                call()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                out = call()
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t0) * 1000.0 / steps
+            perm, ids, dists = out[0].long().cuda(), out[1], out[2]
+            # recall in the visiting order: rows and ids are positions
+            Xp = Xd[perm]
+            runs[f"hmerge_{prec}"] = {
+                "ms_per_step": ms, "points_per_s": n / (ms / 1000.0),
+                "recall_at_10": exact_recall(torch, Xp, torch.from_numpy(ids).cuda(), queries,
+                                             K=10),
+                "merges": out[4]["rounds"], "first_rows": first, "layers_kept": keep,
+                "timing": "host wall clock around the whole call (one library call per step)"}
+            print(f"# hmerge {prec}: {ms:.1f} ms", file=sys.stderr, flush=True)
+            bp = knnm.params(k=K, precision=prec, max_iters=w["rounds"],
+                             sample_rate=w["sample_rate"], delta=0.001, seed=0)
+            ms, out, stats = timed_call(torch, lambda: ctx.build(Xd, bp), steps, warmup)
+            runs[f"build_{prec}"] = {
+                "ms_per_step": ms, "points_per_s": n / (ms / 1000.0),
+                "recall_at_10": exact_recall(torch, Xd, out[0], queries, K=10),
+                "rounds": stats[-1]["rounds"]}
+        head = runs["hmerge_bf16"]
+        merge = "H-Merge (Sec. 3.3) beside an NN-Descent build"
+    elif w["kind"] == "joint":
         metric = w["metric"]
         G1, _, _ = ctx.build(S1, knnm.params(k=K, metric=metric, precision="fp32",
                                              max_iters=10, delta=0.001, seed=11))
@@ -474,7 +514,7 @@ def run_other(args, name):
     line = {"metric": METRIC, "value": head["points_per_s"], "unit": UNIT, "n_gpus": 1,
             "steps": steps, "warmup": warmup, "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
+            "dtype": "bf16+f32" if w["kind"] == "hmerge" else "f32", "data": "synthetic",
             "config": {"workload": name, "merge": merge, "n": n, "d": d, "k": K,
                        "metric": w["metric"], "max_rounds": w["rounds"],
                        "sample_rate": w["sample_rate"], "delta": 0.001,
@@ -670,7 +710,8 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=20000)
     ap.add_argument("--reference-rows", type=int, default=5000)
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "jmerge_gmm_2m_d96_k16_cos", "smerge_gist_1m_d960_k20"],
+                    choices=[WORKLOAD, "jmerge_gmm_2m_d96_k16_cos", "smerge_gist_1m_d960_k20",
+                             "hmerge_sift_1m_d128_k20"],
                     help="another merge workload (one JSON line of its own)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-batches", type=int, default=16)

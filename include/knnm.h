@@ -157,6 +157,30 @@ int knnm_merge_tree(knnm_ctx* ctx, const float* S, int64_t n, int d, int parts,
                     const int64_t* part_rows, const int32_t* G, const knnm_params* params,
                     int32_t* out_ids, float* out_dists, knnm_stats* stats);
 
+/* H-Merge (Sec. 3.3): a hierarchy of graphs on growing random samples of S,
+ * built by repeated J-Merge.  The rows are visited in a random order
+ * (perm_out[r] = the row of S at position r: a Feistel bijection keyed by
+ * params->seed); an NN-Descent graph is built on the first `first_rows`
+ * positions, then each step J-Merges the next raw block of as many positions
+ * as the graph already has (the whole rest when fewer than k + 1 positions
+ * would remain after it), so the graph doubles.  The
+ * growing graph keeps k entries per list (J-Merge never compares two rows of
+ * the existing graph, so shorter lists could not be refilled); each upper
+ * layer is kept as the first k/2 entries of its lists, the bottom one whole.
+ * Merge l of the sequence (the build is l = 0) runs with seed
+ * H(params->seed, l, 8, 0, 0).
+ *   S [n][d] (host or device); first_rows >= k + 1.
+ *   perm_out [n]; out_ids/out_dists [n][k]: the bottom graph, rows and ids as
+ *   positions (row r is S[perm_out[r]]).
+ *   layer_rows[0..n_layers): sizes of upper layers to return (each one of
+ *   first_rows * 2^i below n); layer_ids: their lists one after the other,
+ *   [layer_rows[i]][k/2] each, ids as positions.
+ * stats: rounds = merges run; per-round arrays hold per-merge sums. */
+int knnm_hmerge(knnm_ctx* ctx, const float* S, int64_t n, int d, int64_t first_rows,
+                const knnm_params* params, int32_t* perm_out, int32_t* out_ids,
+                float* out_dists, int n_layers, const int64_t* layer_rows, int32_t* layer_ids,
+                knnm_stats* stats);
+
 /* Device scratch, in bytes, that one whole-merge call of these sizes takes
  * from its context (all arrays on the device).  mode: 0 = S-Merge, 1 = J-Merge
  * (n1 = 0 is the build).  Needs a context because the join configuration

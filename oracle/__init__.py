@@ -64,10 +64,11 @@ def lib():
         L.orc_final.argtypes = [i64, i32, P, P, i32, P, P, P, P]
         L.orc_merge.argtypes = [i32, P, i64, i64, i32, i32, P, P, i32, f32, f32, i32, f32, u64,
                                 i32, P, P, P, P, ctypes.POINTER(ctypes.c_int)]
+        L.orc_permute.argtypes = [i64, u64, P]
         L.orc_bruteforce_knn.argtypes = [P, i64, i32, i32, i32, P, P]
         L.orc_bruteforce_merge.argtypes = [P, i64, i64, i32, i32, P, P, i32, P, P]
         for name in ("orc_init", "orc_sample", "orc_join", "orc_final", "orc_merge",
-                     "orc_bruteforce_knn", "orc_bruteforce_merge"):
+                     "orc_permute", "orc_bruteforce_knn", "orc_bruteforce_merge"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -227,6 +228,47 @@ def merge_joint(S1, G1, S_new, K, metric=L2, keep_ratio=0.5, sample_rate=0.5, ma
     X = np.concatenate([_f32(S1), _f32(S_new)], axis=0)
     return _merge(JOINT, X, len(S1), K, G1, None, metric, keep_ratio, sample_rate, max_iters,
                   delta, seed, literal)
+
+
+def permute(n, seed) -> np.ndarray:
+    """H-Merge sampling order: position r holds row perm[r] (Feistel bijection)."""
+    perm = np.empty(n, np.int32)
+    _check(lib().orc_permute(n, seed, _ptr(perm)), "permute")
+    return perm
+
+
+def hmerge(S, K, first_rows, metric=L2, sample_rate=0.5, max_iters=10, delta=0.0, seed=0):
+    """H-Merge (Sec. 3.3), step by step: rows visited in a random order; an
+    NN-Descent graph on the first `first_rows`; then each step J-Merges a raw block
+    as large as the current graph (the whole rest when less than k + 1 rows would
+    remain after it), so the graph doubles.  The
+    growing graph keeps k entries per list (J-Merge never compares two rows of the
+    existing graph, so lists cut to k/2 could not be refilled); each upper layer is
+    kept as the first k/2 entries of its lists.  Merge l runs with seed
+    H(seed, l, 8, 0, 0).  Returns (perm, layers, ids, dists): layers maps a layer's
+    row count to its lists (ids = positions in the order; k/2 wide above the
+    bottom); ids/dists are the bottom graph in positions."""
+    S = _f32(S)
+    n = len(S)
+    perm = permute(n, seed)
+    Xp = np.ascontiguousarray(S[perm])
+    half = max(1, K // 2)
+    m = min(first_rows, n)
+    ids, dists, _ = build_graph(Xp[:m], K, metric=metric, sample_rate=sample_rate,
+                                max_iters=max_iters, delta=delta, seed=hash64(seed, 0, 8, 0, 0))
+    layers = {m: ids if m == n else np.ascontiguousarray(ids[:, :half])}
+    level = 1
+    while m < n:
+        b = min(m, n - m)
+        if 0 < n - m - b < K + 1:   # too small a rest for a J-Merge of its own
+            b = n - m
+        ids, dists, _ = merge_joint(Xp[:m], ids, Xp[m:m + b], K, metric=metric,
+                                    sample_rate=sample_rate, max_iters=max_iters, delta=delta,
+                                    seed=hash64(seed, level, 8, 0, 0))
+        m += b
+        layers[m] = ids if m == n else np.ascontiguousarray(ids[:, :half])
+        level += 1
+    return perm, layers, ids, dists
 
 
 def build_graph(S, K, metric=L2, sample_rate=0.5, max_iters=10, delta=0.0, seed=0,

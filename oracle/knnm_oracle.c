@@ -529,6 +529,37 @@ done:
 }
 
 /* ------------------------------------------------------------------ */
+/* H-Merge sampling order (Sec. 3.3: each joined block is drawn at random   */
+/* from the whole set).  Reading: position r holds row perm[r], perm a      */
+/* bijection of [0, n) made by a 4-round Feistel network on b bits (b even, */
+/* 2^b >= n, b >= 2) whose round function is H(seed, round, 7, right half,  */
+/* 0) masked to b/2 bits, cycle-walked back into [0, n).                    */
+/* ------------------------------------------------------------------ */
+
+static uint64_t feistel(uint64_t x, int half, uint64_t seed) {
+  const uint64_t mask = (1ull << half) - 1ull;
+  uint64_t L = x >> half, R = x & mask;
+  for (int r = 0; r < 4; ++r) {
+    const uint64_t t = R;
+    R = L ^ (orc_hash(seed, (uint64_t)r, 7, R, 0) & mask);
+    L = t;
+  }
+  return (L << half) | R;
+}
+
+int orc_permute(int64_t n, uint64_t seed, int32_t* perm) {
+  if (n < 1) return ORC_ERR_INVALID;
+  int b = 2;
+  while ((1ll << b) < n) b += 2;
+  for (int64_t i = 0; i < n; ++i) {
+    uint64_t y = feistel((uint64_t)i, b / 2, seed);
+    while (y >= (uint64_t)n) y = feistel(y, b / 2, seed);
+    perm[i] = (int32_t)y;
+  }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
 /* Brute force: exact k-NN graph and the brute-force merge of Sec. 1       */
 /* ------------------------------------------------------------------ */
 

@@ -908,6 +908,169 @@ extern "C" int knnm_merge_tree(knnm_ctx* ctx, const float* S, int64_t n, int d, 
   return KNNM_OK;
 }
 
+extern "C" int knnm_hmerge(knnm_ctx* ctx, const float* S, int64_t n, int d, int64_t first_rows,
+                           const knnm_params* params, int32_t* perm_out, int32_t* out_ids,
+                           float* out_dists, int n_layers, const int64_t* layer_rows,
+                           int32_t* layer_ids, knnm_stats* stats) {
+  auto t_wall0 = std::chrono::steady_clock::now();
+  if (!ctx) return KNNM_ERR_INVALID;
+  ctx->err[0] = 0;
+  if (!S || !params || !perm_out || !out_ids || !out_dists || d < 1 || n > 0x7FFFFFFFLL ||
+      n_layers < 0 || (n_layers > 0 && (!layer_rows || !layer_ids)))
+    return fail(ctx, KNNM_ERR_INVALID, "bad H-Merge arguments");
+  const int K = params->k;
+  if (K < 2 || K > 32) return fail(ctx, KNNM_ERR_INVALID, "k=%d outside 2..32", K);
+  const int half = K / 2;
+  if (first_rows < K + 1 || first_rows > n)
+    return fail(ctx, KNNM_ERR_INVALID, "first_rows=%lld must be in k+1..n", (long long)first_rows);
+  // each step joins as many raw rows as the graph has, and the whole rest when
+  // what would be left after it is too small for a J-Merge of its own
+  auto block_after = [&](int64_t m) {
+    int64_t b = std::min(m, n - m);
+    if (n - m - b > 0 && n - m - b < K + 1) b = n - m;
+    return b;
+  };
+  for (int l = 0; l < n_layers; ++l) {
+    bool ok = false;
+    for (int64_t m = first_rows; m < n; m += block_after(m)) ok = ok || m == layer_rows[l];
+    if (!ok)
+      return fail(ctx, KNNM_ERR_INVALID, "layer of %lld rows is not produced",
+                  (long long)layer_rows[l]);
+  }
+  KNNM_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  float *Xs = nullptr, *Xp = nullptr, *dists = nullptr;
+  int32_t *perm = nullptr, *ids[2] = {nullptr, nullptr};
+  const bool s_dev = is_device_ptr(S);
+  auto release = [&]() {
+    cudaStreamSynchronize(st);
+    cudaFree(Xs);
+    cudaFree(Xp);
+    cudaFree(dists);
+    cudaFree(perm);
+    cudaFree(ids[0]);
+    cudaFree(ids[1]);
+  };
+  if ((!s_dev && cudaMalloc(&Xs, (size_t)n * d * 4) != cudaSuccess) ||
+      cudaMalloc(&Xp, (size_t)n * d * 4) != cudaSuccess ||
+      cudaMalloc(&dists, (size_t)n * K * 4) != cudaSuccess ||
+      cudaMalloc(&perm, (size_t)n * 4) != cudaSuccess ||
+      cudaMalloc(&ids[0], (size_t)n * K * 4) != cudaSuccess ||
+      cudaMalloc(&ids[1], (size_t)n * K * 4) != cudaSuccess) {
+    cudaGetLastError();
+    release();
+    return fail(ctx, KNNM_ERR_NOMEM, "cannot allocate the H-Merge buffers");
+  }
+  int rc = KNNM_OK;
+  auto cuda_ok = [&](cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return true;
+    rc = fail(ctx, KNNM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return false;
+  };
+  const float* X = S;
+  if (!s_dev) {
+    if (!cuda_ok(cudaMemcpyAsync(Xs, S, (size_t)n * d * 4, cudaMemcpyHostToDevice, st), "copy S")) {
+      release();
+      return rc;
+    }
+    X = Xs;
+  }
+  if (!cuda_ok(launch_permute(n, params->seed, perm, st), "permute") ||
+      !cuda_ok(launch_gather_rows(X, perm, n, d, Xp, st), "gather")) {
+    release();
+    return rc;
+  }
+  knnm_stats total;
+  memset(&total, 0, sizeof(total));
+  auto add_stats = [&](const knnm_stats& ms, int level) {
+    for (int t = 0; t < ms.rounds; ++t) {
+      total.updates[level] += ms.updates[t];
+      total.dist_evals[level] += ms.dist_evals[t];
+      total.proposals[level] += ms.proposals[t];
+      total.reranked[level] += ms.reranked[t];
+      total.gathered[level] += ms.gathered[t];
+      total.ms_sample[level] += ms.ms_sample[t];
+      total.ms_join[level] += ms.ms_join[t];
+      total.ms_update[level] += ms.ms_update[t];
+    }
+    total.kernel_launches += ms.kernel_launches;
+    total.ms_init += ms.ms_init;
+    total.ms_rounds += ms.ms_rounds;
+    total.ms_final += ms.ms_final;
+  };
+  // layer outputs: copy the k/2 lists of an m-row layer when it is asked for
+  int64_t layer_off = 0;
+  auto save_layer = [&](int64_t m, const int32_t* lists) {
+    int64_t off = 0;
+    for (int l = 0; l < n_layers; ++l) {
+      if (layer_rows[l] == m)  // the first k/2 entries of each list
+        return cuda_ok(cudaMemcpy2DAsync(layer_ids + off, (size_t)half * 4, lists, (size_t)K * 4,
+                                         (size_t)half * 4, (size_t)m, cudaMemcpyDefault, st),
+                       "copy layer");
+      off += layer_rows[l] * half;
+    }
+    return true;
+  };
+  (void)layer_off;
+  int64_t m = first_rows;
+  int cur = 0, level = 0;
+  {
+    knnm_params p = *params;
+    p.seed = mix_step(hash_prefix(params->seed, 0, 8, 0) ^ 0ull);
+    MergeIn in{JOINT, nullptr, 0, nullptr, Xp, m, nullptr, d};
+    knnm_stats ms;
+    rc = run_merge(ctx, in, &p, ids[cur], dists, &ms);
+    if (rc) {
+      release();
+      return rc;
+    }
+    add_stats(ms, 0);
+    if (m < n && !save_layer(m, ids[cur])) {
+      release();
+      return rc;
+    }
+  }
+  while (m < n) {
+    ++level;
+    if (level >= KNNM_MAX_ROUNDS) {
+      release();
+      return fail(ctx, KNNM_ERR_INVALID, "too many H-Merge steps");
+    }
+    const int64_t b = block_after(m);
+    const bool last = m + b == n;
+    knnm_params p = *params;
+    p.seed = mix_step(hash_prefix(params->seed, (uint64_t)level, 8, 0) ^ 0ull);
+    MergeIn in{JOINT, Xp, m, ids[cur], Xp + (size_t)m * d, b, nullptr, d};
+    knnm_stats ms;
+    rc = run_merge(ctx, in, &p, ids[cur ^ 1], dists, &ms);
+    if (rc) {
+      release();
+      return rc;
+    }
+    add_stats(ms, level);
+    cur ^= 1;
+    m += b;
+    if (!last && !save_layer(m, ids[cur])) {
+      release();
+      return rc;
+    }
+  }
+  total.rounds = level + 1;
+  bool ok = cuda_ok(cudaMemcpyAsync(out_ids, ids[cur], (size_t)n * K * 4, cudaMemcpyDefault, st),
+                    "copy ids") &&
+            cuda_ok(cudaMemcpyAsync(out_dists, dists, (size_t)n * K * 4, cudaMemcpyDefault, st),
+                    "copy dists") &&
+            cuda_ok(cudaMemcpyAsync(perm_out, perm, (size_t)n * 4, cudaMemcpyDefault, st),
+                    "copy perm") &&
+            cuda_ok(cudaStreamSynchronize(st), "sync");
+  release();
+  if (!ok) return rc;
+  total.ms_total = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() -
+                                                            t_wall0).count();
+  if (stats) *stats = total;
+  return KNNM_OK;
+}
+
 extern "C" int knnm_merge_scratch_bytes(knnm_ctx* ctx, int mode, int64_t n1, int64_t n2, int d,
                                         const knnm_params* params, uint64_t* bytes) {
   if (!ctx || !bytes || (mode != SYMMETRIC && mode != JOINT)) return KNNM_ERR_INVALID;

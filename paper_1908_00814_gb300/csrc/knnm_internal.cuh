@@ -401,6 +401,10 @@ cudaError_t launch_list_dists(Rows rows, int64_t n, const int32_t* G, int K, int
 cudaError_t launch_commit(int64_t n_snap, int64_t rows, int K, int32_t* res_ids,
                           float* res_dists, const int32_t* out_ids, const float* out_dists,
                           int64_t base, cudaStream_t st);
+// H-Merge: visiting order (a Feistel bijection of [0, n)) and the rows in it.
+cudaError_t launch_permute(int64_t n, uint64_t seed, int32_t* perm, cudaStream_t st);
+cudaError_t launch_gather_rows(const float* X, const int32_t* perm, int64_t n, int d, float* Xp,
+                               cudaStream_t st);
 // *p = v (one thread); *p += 1 (one thread).
 cudaError_t launch_set_int(int* p, int v, cudaStream_t st);
 cudaError_t launch_bump_int(int* p, cudaStream_t st);

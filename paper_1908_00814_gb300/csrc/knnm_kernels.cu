@@ -832,6 +832,44 @@ __global__ void __launch_bounds__(BLOCK) k_commit(int64_t n_snap, int64_t rows, 
   }
 }
 
+// H-Merge visiting order (Sec. 3.3: each block joined in is drawn at random
+// from the whole set): position r holds row perm[r], perm a 4-round Feistel
+// bijection on 2*half bits (round function H(seed, round, 7, right, 0) masked
+// to half bits), cycle-walked back into [0, n).
+__device__ __forceinline__ uint64_t feistel4(uint64_t x, int half, uint64_t seed) {
+  const uint64_t mask = (1ull << half) - 1ull;
+  uint64_t L = x >> half, R = x & mask;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const uint64_t t = R;
+    R = L ^ (mix_step(hash_prefix(seed, (uint64_t)r, 7, R) ^ 0ull) & mask);
+    L = t;
+  }
+  return (L << half) | R;
+}
+
+__global__ void k_permute(int64_t n, int half, uint64_t seed, int32_t* perm) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint64_t y = feistel4((uint64_t)i, half, seed);
+  // the cycle through i returns to [0, n) within 2^(2*half) steps
+  for (uint64_t guard = 0; y >= (uint64_t)n && guard < (1ull << (2 * half)); ++guard)
+    y = feistel4(y, half, seed);
+  perm[i] = (int32_t)y;
+}
+
+// Xp[r] = X[perm[r]], one warp per row.
+__global__ void k_gather_rows(const float* X, const int32_t* perm, int64_t n, int d, float* Xp) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
+  for (int64_t r = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5); r < n;
+       r += nwarps) {
+    const float* src = X + (size_t)perm[r] * d;
+    float* dst = Xp + (size_t)r * d;
+    for (int t = lane; t < d; t += 32) dst[t] = src[t];
+  }
+}
+
 __global__ void k_set_int(int* p, int v) { *p = v; }
 __global__ void k_bump_int(int* p) { *p += 1; }
 
@@ -998,6 +1036,19 @@ cudaError_t launch_commit(int64_t n_snap, int64_t rows, int K, int32_t* res_ids,
                           int64_t base, cudaStream_t st) {
   k_commit<<<grid_for_warps(n_snap + rows), BLOCK, 0, st>>>(n_snap, rows, K, res_ids, res_dists,
                                                            out_ids, out_dists, base);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_permute(int64_t n, uint64_t seed, int32_t* perm, cudaStream_t st) {
+  int b = 2;
+  while ((1ll << b) < n) b += 2;
+  k_permute<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, b / 2, seed, perm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows(const float* X, const int32_t* perm, int64_t n, int d, float* Xp,
+                               cudaStream_t st) {
+  k_gather_rows<<<grid_for_warps(n), BLOCK, 0, st>>>(X, perm, n, d, Xp);
   return cudaGetLastError();
 }
 

@@ -129,6 +129,9 @@ WORKLOADS = {
     "serve_sift_2m_d128_k16": dict(kind="serve", gen="sift_like", n=2_000_000, d=128, k=16,
                                    metric="l2", rounds=10, sample_rate=0.5, seed=1004,
                                    gen_args={}),
+    "hmerge_sift_1m_d128_k20": dict(kind="hmerge", gen="sift_like", n=1_000_000, d=128, k=20,
+                                    metric="l2", rounds=10, sample_rate=0.5, seed=1006,
+                                    gen_args={}),
     "smerge_gist_1m_d960_k20": dict(kind="symmetric", gen="gist_like", n=1_000_000, d=960,
                                     k=20, metric="l1", rounds=10, sample_rate=0.5, seed=1005,
                                     gen_args={}),

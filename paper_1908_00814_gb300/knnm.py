@@ -116,6 +116,8 @@ SIGNATURES = {
                                       _P, _P]),
     "knnm_merge_tree": (_I, [_P, _P, _I64, _I, _I, _P, _P, ctypes.POINTER(Params), _P, _P,
                              ctypes.POINTER(Stats)]),
+    "knnm_hmerge": (_I, [_P, _P, _I64, _I, _I64, ctypes.POINTER(Params), _P, _P, _P, _I, _P,
+                         _P, ctypes.POINTER(Stats)]),
     "knnm_merge_scratch_bytes": (_I, [_P, _I, _I64, _I64, _I, ctypes.POINTER(Params),
                                       ctypes.POINTER(ctypes.c_uint64)]),
     "knnm_server_create": (_I, [_I, _P, _I64, _P, _I, ctypes.POINTER(Params),
@@ -273,6 +275,29 @@ class Context:
                                           ctypes.byref(p), _ptr(ids), _ptr(dists),
                                           ctypes.byref(st)))
         return ids, dists, st.as_dict()
+
+    def hmerge(self, S, first_rows, p: Params, layers=()):
+        """H-Merge: returns (perm, ids, dists, layer_lists, stats); ids/dists are the
+        bottom graph and the upper layers' k/2 lists, rows and ids as positions in
+        the visiting order perm."""
+        n, d = S.shape
+        K, half = p.k, p.k // 2
+        perm = np.empty(n, np.int32)
+        ids = np.empty((n, K), np.int32)
+        dists = np.empty((n, K), np.float32)
+        rows = np.ascontiguousarray(np.asarray(list(layers), dtype=np.int64))
+        lay = np.empty(max(1, int(rows.sum())) * half, np.int32)
+        st = Stats()
+        self._sync_stream()
+        self._check(lib().knnm_hmerge(self.h, _ptr(S), n, d, first_rows, ctypes.byref(p),
+                                      _ptr(perm), _ptr(ids), _ptr(dists), len(rows),
+                                      _ptr(rows) if len(rows) else None,
+                                      _ptr(lay) if len(rows) else None, ctypes.byref(st)))
+        out, off = {}, 0
+        for m in rows.tolist():
+            out[m] = lay[off * half:(off + m) * half].reshape(m, half)
+            off += m
+        return perm, ids, dists, out, st.as_dict()
 
     def scratch_bytes(self, mode, n1, n2, d, p: Params) -> int:
         """Device scratch one whole-merge call of these sizes takes."""

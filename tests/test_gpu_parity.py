@@ -462,3 +462,22 @@ def test_tensor_core_rounds_follow_the_rerank_share(torch, km, ctx, orc):
                                    cuda(torch, G2), km.params(k=12, precision="fp16", max_iters=6,
                                                               delta=0.0))
     assert st["tc_rounds"][0] is False
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_hmerge_parity(torch, km, ctx, orc, precision):
+    """H-Merge (Sec. 3.3): visiting order, every upper layer (k/2 lists) and the
+    bottom graph equal the oracle's step-by-step composition."""
+    X = datagen.sift_like(2600, 32, seed=61)
+    K, first = 12, 100
+    perm_r, layers_r, ids_r, dists_r = orc.hmerge(X, K, first, max_iters=5, seed=9)
+    p = km.params(k=K, precision=precision, max_iters=5, delta=0.0, seed=9)
+    want = [m for m in layers_r if m < len(X)]
+    perm, ids, dists, layers, st = ctx.hmerge(cuda(torch, X), first, p, layers=want)
+    assert np.array_equal(perm, perm_r)
+    assert sorted(perm.tolist()) == list(range(len(X)))
+    assert st["rounds"] == len(layers_r)
+    for m in want:
+        assert_same(layers[m], layers_r[m], f"layer {m}")
+    assert_same(ids, ids_r, "bottom ids")
+    assert_same(dists, dists_r, "bottom dists")
