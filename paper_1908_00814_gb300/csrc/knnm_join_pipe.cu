@@ -725,15 +725,17 @@ cudaError_t plan_pipe(int precision, int metric, int cap_new, int cap_old, int d
   P->ring_rows = ring;
   const int cpr = P->row_bytes / 16;
   P->cpr_inv = (0x100000000ull + cpr - 1) / cpr;
-  P->pair_cap = cap_new * (cap_new + cap_old);
+  // pairs (i, j) with i < nn <= cap_new, i < j < M <= cap_new + cap_old
+  P->pair_cap = cap_new * (cap_new + cap_old) - cap_new * (cap_new + 1) / 2;
   size_t wb = (size_t)ring * P->row_stride + (size_t)NREC * RB + 2 * NREC * 8 +
               (((size_t)P->pair_cap * 2 + 15) & ~(size_t)15);
   if (tc) wb += (size_t)16 * GSTR * 4;
   wb = (wb + 127) & ~(size_t)127;
   P->warp_bytes = (int)wb;
-  // warps per block: as many as fit 220 KB (at most MAX_WARPS), one block per SM
+  // warps per block: as many as fit the 227 KB a block may hold (at most
+  // MAX_WARPS), one block per SM
   int w = MAX_WARPS;
-  while (w > 1 && (size_t)w * wb + 64 > 220 * 1024) --w;
+  while (w > 1 && (size_t)w * wb + 64 > 227 * 1024) --w;
   // long rows leave too few warps per SM to hide the gathers: the caller takes
   // the single-stage kernel instead
   if (w < MIN_WARPS || (size_t)w * wb + 64 > 227 * 1024) return cudaErrorInvalidValue;
