@@ -426,6 +426,11 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   sa.old_ids = P.old_ids;
   sa.old_cnt = P.old_cnt;
   sa.ctr = P.ctr;
+  // The merge only needs old(u) where new(u) is not empty; skipping the rest
+  // pays once few lists change (its extra counting pass costs more while most
+  // nodes are active), so direct launches turn it on after a round with fewer
+  // than N*K/8 updates; captured rounds always use it.
+  sa.active_only = ctx->use_graphs ? 1 : 0;
   if (P.rec) {
     sa.rec = P.rec;
     sa.rec_cap = jp.pipe ? jp.pa.cap : jp32.pa.cap;
@@ -538,6 +543,8 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     KNNM_CUDA(launch_set_int(P.tdev, 1, st));
   }
   for (int t = 1; t <= params->max_iters; ++t) {
+    if (!graphs && t > 1)
+      sa.active_only = (double)local.updates[t - 2] < (double)N * (double)K / 8.0 ? 1 : 0;
     if (graphs) {
       cudaGraphExec_t& g = round_exec[use_tc ? 1 : 0];
       if (!g) {

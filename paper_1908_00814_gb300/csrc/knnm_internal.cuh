@@ -385,6 +385,10 @@ struct SampleArgs {
   uint64_t* rbucket = nullptr;         // [N*K] reverse sampling keys grouped by (target, stream)
   unsigned long long* tile_sum = nullptr;  // [ceil(2N/1024)+1] scan scratch
   unsigned long long* total = nullptr;     // scan total
+  // Join-only sampling (bucketed path): old(u) is built only for nodes whose
+  // new(u) is not empty, the only ones the join pairs from; the others get
+  // empty candidate sets.  The step entry point keeps it off (full outputs).
+  int active_only = 0;
 };
 cudaError_t launch_sample(const SampleArgs& a, cudaStream_t st);
 // Context internals used by the serving loop (knnm_api.cu): grow the

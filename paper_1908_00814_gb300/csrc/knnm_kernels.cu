@@ -321,8 +321,9 @@ __global__ void __launch_bounds__(BLOCK) k_sample_fwd(SampleArgs a) {
     }
     if (a.rcnt) {
       // bucketed reverse lists: count the in-edges of (target, stream) here
+      // (old edges later, to active targets only, when active_only is set)
       if (sel) atomicAdd(&a.rcnt[2 * (size_t)v], 1);
-      if (isold) atomicAdd(&a.rcnt[2 * (size_t)v + 1], 1);
+      if (isold && !a.active_only) atomicAdd(&a.rcnt[2 * (size_t)v + 1], 1);
     } else {
       if (sel)
         slots_insert(a.rev_new + (size_t)v * s, s,
@@ -336,6 +337,32 @@ __global__ void __launch_bounds__(BLOCK) k_sample_fwd(SampleArgs a) {
   }
 }
 
+// A node is active when its new set will not be empty: it drew forward-new
+// entries, or some node drew it as one (a reverse-new in-edge).  Before the
+// scan the in-edge count says so; after it (while the scatter consumes the
+// counts) the bucket bounds do.
+__device__ __forceinline__ bool active_by_count(const SampleArgs& a, int32_t v) {
+  return a.new_cnt[v] > 0 || a.rcnt[2 * (size_t)v] > 0;
+}
+__device__ __forceinline__ bool active_by_bucket(const SampleArgs& a, int32_t v) {
+  return a.new_cnt[v] > 0 || a.roffs[2 * (size_t)v + 1] > a.roffs[2 * (size_t)v];
+}
+
+// Old-stream in-edges of active targets (active_only), counted after every
+// forward-new draw is known.
+__global__ void __launch_bounds__(BLOCK) k_sample_count_old(SampleArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
+  for (int64_t u = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5); u < a.N;
+       u += nwarps) {
+    const int of = a.old_cnt[u];
+    if (lane < of) {
+      const int32_t v = a.old_ids[(size_t)u * a.cap_old + lane];
+      if (active_by_count(a, v)) atomicAdd(&a.rcnt[2 * (size_t)v + 1], 1);
+    }
+  }
+}
+
 // Moves each reverse edge's sampling key into its (target, stream) bucket;
 // the counts are consumed back to zero.
 __global__ void __launch_bounds__(BLOCK) k_sample_scatter(SampleArgs a) {
@@ -345,9 +372,10 @@ __global__ void __launch_bounds__(BLOCK) k_sample_scatter(SampleArgs a) {
   for (int64_t u = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5); u < a.N;
        u += nwarps) {
     const int nf = a.new_cnt[u], of = a.old_cnt[u];
-    const bool hn = lane < nf, ho = lane < of;
+    const bool hn = lane < nf;
     const int32_t vn = hn ? a.new_ids[(size_t)u * a.cap_new + lane] : 0;
-    const int32_t vo = ho ? a.old_ids[(size_t)u * a.cap_old + lane] : 0;
+    const int32_t vo = lane < of ? a.old_ids[(size_t)u * a.cap_old + lane] : 0;
+    const bool ho = lane < of && (!a.active_only || active_by_bucket(a, vo));
     // both slot claims in flight before either store
     const int pn = hn ? atomicSub(&a.rcnt[2 * (size_t)vn], 1) - 1 : 0;
     const int po = ho ? atomicSub(&a.rcnt[2 * (size_t)vo + 1], 1) - 1 : 0;
@@ -416,6 +444,18 @@ __global__ void __launch_bounds__(BLOCK) k_sample_rev(SampleArgs a) {
   for (int64_t u = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5); u < a.N;
        u += nwarps) {
     const int nf = a.new_cnt[u], of = a.old_cnt[u];
+    if (a.active_only && nf == 0 && a.roffs[2 * u] == a.roffs[2 * u + 1]) {
+      // new(u) is empty: no pair of the join starts here
+      if (lane == 0) {
+        a.new_cnt[u] = 0;
+        a.old_cnt[u] = 0;
+        if (a.rec) {
+          int32_t* h = (int32_t*)(a.rec + (size_t)u * rec_bytes(a.rec_cap));
+          h[0] = h[1] = h[2] = h[3] = 0;
+        }
+      }
+      continue;
+    }
     const int32_t fn = lane < nf ? a.new_ids[(size_t)u * a.cap_new + lane] : -1;
     const int32_t fo = lane < of ? a.old_ids[(size_t)u * a.cap_old + lane] : -2;
     uint64_t rk, ok;
@@ -971,6 +1011,11 @@ cudaError_t launch_sample(const SampleArgs& a, cudaStream_t st) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (a.rcnt) {
+    if (a.active_only) {
+      k_sample_count_old<<<grid, BLOCK, 0, st>>>(a);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
     const int64_t n2 = 2 * a.N;
     const int64_t ntiles = (n2 + SCAN_TILE - 1) / SCAN_TILE;
     k_scan_tiles<<<(unsigned)ntiles, 256, 0, st>>>(a.rcnt, n2, a.tile_sum);
