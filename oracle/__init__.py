@@ -67,8 +67,11 @@ def lib():
         L.orc_permute.argtypes = [i64, u64, P]
         L.orc_bruteforce_knn.argtypes = [P, i64, i32, i32, i32, P, P]
         L.orc_bruteforce_merge.argtypes = [P, i64, i64, i32, i32, P, P, i32, P, P]
+        L.orc_diversify.argtypes = [P, i64, i32, i32, P, i32, i32, P, i64, P, P, P, P]
+        L.orc_search.argtypes = [P, i64, i32, i32, i32, P, P, P, P, i64, i32, i32, u64, P, P, P]
         for name in ("orc_init", "orc_sample", "orc_join", "orc_final", "orc_merge",
-                     "orc_permute", "orc_bruteforce_knn", "orc_bruteforce_merge"):
+                     "orc_permute", "orc_bruteforce_knn", "orc_bruteforce_merge",
+                     "orc_diversify", "orc_search"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -269,6 +272,47 @@ def hmerge(S, K, first_rows, metric=L2, sample_rate=0.5, max_iters=10, delta=0.0
         layers[m] = ids if m == n else np.ascontiguousarray(ids[:, :half])
         level += 1
     return perm, layers, ids, dists
+
+
+def diversify(S, G, max_degree, metric=L2, rows=None):
+    """Graph diversification (Alg. 3, Sec. 3.4) of the k-NN graph G: each row's
+    list and its reverse list, each in (distance, id) order, are diversified
+    (first entry kept; a later one dropped when a kept entry is closer to it
+    than the row is) and merged without repeats, cut to max_degree.  Returns
+    (ids, dists, degree, evals) for `rows` (all rows when None)."""
+    S, G = _f32(S), _i32(G)
+    n, d = S.shape
+    K = G.shape[1]
+    r = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    m = n if r is None else len(r)
+    ids = np.empty((m, max_degree), np.int32)
+    dists = np.empty((m, max_degree), np.float32)
+    deg = np.empty(m, np.int32)
+    ev = ctypes.c_uint64(0)
+    _check(lib().orc_diversify(_ptr(S), n, d, metric, _ptr(G), K, max_degree, _ptr(r), m,
+                               _ptr(ids), _ptr(dists), _ptr(deg), ctypes.byref(ev)), "diversify")
+    return ids, dists, deg, int(ev.value)
+
+
+def search(S, layers, Q, ef, k_out, metric=L2, seed=0):
+    """Top-down search (Sec. 3.4) of the queries Q on a hierarchy: `layers` is a
+    list of id arrays from the top layer down, layer l covering the first
+    len(layers[l]) rows of S (the bottom one all of them; ids < 0 are padding).
+    Greedy descent above the bottom, best-first over an ef-entry rank list at the
+    bottom.  Returns (ids, dists, evals) with k_out entries per query."""
+    S, Q = _f32(S), _f32(Q)
+    n, d = S.shape
+    rows = np.array([len(g) for g in layers], np.int64)
+    width = np.array([g.shape[1] for g in layers], np.int32)
+    flat = np.concatenate([_i32(g).ravel() for g in layers])
+    nq = len(Q)
+    ids = np.empty((nq, k_out), np.int32)
+    dists = np.empty((nq, k_out), np.float32)
+    ev = np.empty(nq, np.uint64)
+    _check(lib().orc_search(_ptr(S), n, d, metric, len(layers), _ptr(rows), _ptr(width),
+                            _ptr(flat), _ptr(Q), nq, ef, k_out, seed, _ptr(ids), _ptr(dists),
+                            _ptr(ev)), "search")
+    return ids, dists, ev
 
 
 def build_graph(S, K, metric=L2, sample_rate=0.5, max_iters=10, delta=0.0, seed=0,

@@ -2,7 +2,8 @@
  * knnm_oracle.c -- CPU oracle for the k-NN graph merge of Zhao, Wang, Lin and
  * Ngo, "On the Merge of k-NN Graph": Symmetric Merge (S-Merge, Alg. 1), Joint
  * Merge (J-Merge, Alg. 2) and the NN-Descent build that J-Merge reduces to when
- * the existing graph is empty.
+ * the existing graph is empty; the H-Merge visiting order (Sec. 3.3); graph
+ * diversification (Alg. 3) and the top-down search on the hierarchy (Sec. 3.4).
  *
  * TEST INFRASTRUCTURE ONLY.  This is a plain, slow, single-threaded
  * restatement of the method, written to check the CUDA library against.  It
@@ -600,5 +601,219 @@ int orc_bruteforce_merge(const float* X, int64_t n, int64_t n1, int d, int metri
       update_nn(out_ids + (size_t)i * K, out_dists + (size_t)i * K, NULL, K, (int32_t)j, l);
       update_nn(out_ids + (size_t)j * K, out_dists + (size_t)j * K, NULL, K, (int32_t)i, l);
     }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Graph diversification (Alg. 3, Sec. 3.4), run on a finished k-NN graph. */
+/* Readings:                                                               */
+/*   - A list is examined in (distance, id) order.  Its first entry is     */
+/*     kept; a later entry s is dropped as soon as one kept entry c has    */
+/*     m(s, c) < m(s, owner), else kept (Alg. 3: a strict "<" occludes).   */
+/*   - The reverse list of a is {b : a in G[b]} with distance m(a, b), in  */
+/*     (distance, id) order, taken from the input graph; it is            */
+/*     diversified by the same rule on its own.                           */
+/*   - "Merged": the union of both kept sets without repeats, in           */
+/*     (distance, id) order, cut to the first max_degree entries and       */
+/*     padded with id -1 / distance +inf.                                  */
+/* ------------------------------------------------------------------ */
+
+/* Alg. 3 on one list in entry order; the kept entries are moved to the front
+ * (in order) and their count is returned.  Stops once max_keep are kept: no
+ * later entry could reach the first max_keep of the union. */
+static int diversify_list(const float* X, int d, int metric, int32_t* ids, float* dists, int m,
+                          int max_keep, uint64_t* evals) {
+  int kept = 0;
+  for (int i = 0; i < m && kept < max_keep; ++i) {
+    int occluded = 0;
+    for (int c = 0; c < kept && !occluded; ++c) {
+      ++*evals;
+      occluded = orc_distance(metric, row(X, ids[i], d), row(X, ids[c], d), d) < dists[i];
+    }
+    if (!occluded) {
+      ids[kept] = ids[i];
+      dists[kept] = dists[i];
+      ++kept;
+    }
+  }
+  return kept;
+}
+
+/* Diversified lists of the rows listed in `rows` (all rows when rows is NULL,
+ * n_rows = n).  G [n][K] is a k-NN graph (ids in [0, n), no self, no repeats
+ * per row).  out_ids/out_dists [n_rows][max_degree], out_deg [n_rows];
+ * evals (may be NULL) receives the distance evaluations of Alg. 3's loops. */
+int orc_diversify(const float* X, int64_t n, int d, int metric, const int32_t* G, int K,
+                  int max_degree, const int64_t* rows, int64_t n_rows, int32_t* out_ids,
+                  float* out_dists, int32_t* out_deg, uint64_t* evals) {
+  if (n < 1 || K < 1 || max_degree < 1) return ORC_ERR_INVALID;
+  /* reverse lists of the whole graph (counting sort by target) */
+  int64_t* start = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  int32_t* src = (int32_t*)malloc((size_t)n * K * sizeof(int32_t));
+  int64_t* fill = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+  int64_t max_in = 0;
+  if (!start || !src || !fill) {
+    free(start); free(src); free(fill);
+    return ORC_ERR_NOMEM;
+  }
+  for (int64_t i = 0; i < (int64_t)n * K; ++i) {
+    if (G[i] < 0 || G[i] >= n) { free(start); free(src); free(fill); return ORC_ERR_INVALID; }
+    start[G[i] + 1]++;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    if (start[i + 1] > max_in) max_in = start[i + 1];
+    start[i + 1] += start[i];
+  }
+  for (int64_t i = 0; i < n; ++i) fill[i] = start[i];
+  for (int64_t b = 0; b < n; ++b)
+    for (int j = 0; j < K; ++j) src[fill[G[(size_t)b * K + j]]++] = (int32_t)b;
+  const int cap = (int)(max_in > K ? max_in : K);
+  int32_t* fi = (int32_t*)malloc(sizeof(int32_t) * (size_t)K);
+  float* fd = (float*)malloc(sizeof(float) * (size_t)K);
+  int32_t* ri = (int32_t*)malloc(sizeof(int32_t) * (size_t)cap);
+  float* rd = (float*)malloc(sizeof(float) * (size_t)cap);
+  uint64_t ev = 0;
+  int rc = ORC_OK;
+  if (!fi || !fd || !ri || !rd) rc = ORC_ERR_NOMEM;
+  const int64_t count = rows ? n_rows : n;
+  for (int64_t r = 0; r < count && rc == ORC_OK; ++r) {
+    const int64_t a = rows ? rows[r] : r;
+    if (a < 0 || a >= n) { rc = ORC_ERR_INVALID; break; }
+    for (int j = 0; j < K; ++j) {
+      fi[j] = G[(size_t)a * K + j];
+      fd[j] = orc_distance(metric, row(X, a, d), row(X, fi[j], d), d);
+      if (fi[j] == a) rc = ORC_ERR_INVALID;
+      for (int c = 0; c < j; ++c)
+        if (fi[c] == fi[j]) rc = ORC_ERR_INVALID;
+    }
+    if (rc != ORC_OK) break;
+    sort_entries(fi, fd, K);
+    const int nf = diversify_list(X, d, metric, fi, fd, K, K, &ev);
+    const int m = (int)(start[a + 1] - start[a]);
+    for (int j = 0; j < m; ++j) {
+      ri[j] = src[start[a] + j];
+      rd[j] = orc_distance(metric, row(X, a, d), row(X, ri[j], d), d);
+    }
+    sort_entries(ri, rd, m);
+    const int nr = diversify_list(X, d, metric, ri, rd, m, max_degree, &ev);
+    /* union of two entry-ordered lists; one id has one distance, so a repeat
+     * is an equal entry */
+    int32_t* oi = out_ids + (size_t)r * max_degree;
+    float* od = out_dists + (size_t)r * max_degree;
+    int x = 0, y = 0, k = 0;
+    while (k < max_degree && (x < nf || y < nr)) {
+      int take_f;
+      if (x < nf && y < nr) {
+        if (fi[x] == ri[y]) { ++y; continue; }
+        take_f = entry_less(fd[x], fi[x], rd[y], ri[y]);
+      } else {
+        take_f = x < nf;
+      }
+      if (take_f) { oi[k] = fi[x]; od[k] = fd[x]; ++x; }
+      else { oi[k] = ri[y]; od[k] = rd[y]; ++y; }
+      ++k;
+    }
+    out_deg[r] = k;
+    for (; k < max_degree; ++k) { oi[k] = -1; od[k] = INFINITY; }
+  }
+  if (evals) *evals = ev;
+  free(start); free(src); free(fill); free(fi); free(fd); free(ri); free(rd);
+  return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Top-down search on the hierarchy (Sec. 3.4).  Readings:                */
+/*   - Layers run from the top (fewest rows) to the bottom; layer l holds   */
+/*     the first layer_rows[l] rows of X and a graph of layer_width[l]      */
+/*     entries per row (ids < 0 are padding and skipped).                  */
+/*   - The search starts at row H(seed, 0, 9, q, 0) mod layer_rows[0].     */
+/*   - Above the bottom: greedy.  All neighbours of the current row are    */
+/*     compared with the query; the current row moves to the nearest of   */
+/*     them while that one ranks before it in (distance, id) order.        */
+/*   - Bottom: best-first over a rank list of at most ef entries in        */
+/*     (distance, id) order, seeded with the row the upper layers reached. */
+/*     The first unexpanded entry is expanded: each neighbour not seen     */
+/*     before is compared and enters the list when the list has room or    */
+/*     it ranks before the last entry (which then leaves).  The search     */
+/*     stops when every entry of the list is expanded; the first k_out     */
+/*     entries are the result (-1 / +inf padding when fewer).              */
+/* ------------------------------------------------------------------ */
+
+int orc_search(const float* X, int64_t n, int d, int metric, int n_layers,
+               const int64_t* layer_rows, const int32_t* layer_width, const int32_t* graphs,
+               const float* Q, int64_t nq, int ef, int k_out, uint64_t seed, int32_t* out_ids,
+               float* out_dists, uint64_t* out_evals) {
+  if (n < 1 || n_layers < 1 || ef < 1 || k_out < 1 || k_out > ef) return ORC_ERR_INVALID;
+  if (layer_rows[n_layers - 1] != n) return ORC_ERR_INVALID;
+  const int32_t** G = (const int32_t**)malloc(sizeof(int32_t*) * (size_t)n_layers);
+  uint8_t* seen = (uint8_t*)malloc((size_t)n);
+  int32_t* li = (int32_t*)malloc(sizeof(int32_t) * ((size_t)ef + 1));
+  float* ld = (float*)malloc(sizeof(float) * ((size_t)ef + 1));
+  uint8_t* done = (uint8_t*)malloc((size_t)ef + 1);
+  if (!G || !seen || !li || !ld || !done) {
+    free(G); free(seen); free(li); free(ld); free(done);
+    return ORC_ERR_NOMEM;
+  }
+  const int32_t* g = graphs;
+  for (int l = 0; l < n_layers; ++l) {
+    G[l] = g;
+    g += (size_t)layer_rows[l] * layer_width[l];
+  }
+  for (int64_t q = 0; q < nq; ++q) {
+    const float* x = row(Q, q, d);
+    uint64_t ev = 1;
+    int32_t cur = (int32_t)(orc_hash(seed, 0, 9, (uint64_t)q, 0) % (uint64_t)layer_rows[0]);
+    float dcur = orc_distance(metric, x, row(X, cur, d), d);
+    for (int l = 0; l + 1 < n_layers; ++l) {
+      const int w = layer_width[l];
+      for (;;) {
+        int32_t best = cur;
+        float db = dcur;
+        for (int j = 0; j < w; ++j) {
+          const int32_t v = G[l][(size_t)cur * w + j];
+          if (v < 0) continue;
+          const float dv = orc_distance(metric, x, row(X, v, d), d);
+          ++ev;
+          if (entry_less(dv, v, db, best)) { best = v; db = dv; }
+        }
+        if (best == cur) break;
+        cur = best;
+        dcur = db;
+      }
+    }
+    const int w = layer_width[n_layers - 1];
+    const int32_t* Gb = G[n_layers - 1];
+    memset(seen, 0, (size_t)n);
+    seen[cur] = 1;
+    int m = 1;
+    li[0] = cur; ld[0] = dcur; done[0] = 0;
+    for (;;) {
+      int e = 0;
+      while (e < m && done[e]) ++e;
+      if (e == m) break;
+      done[e] = 1;
+      const int32_t u = li[e];
+      for (int j = 0; j < w; ++j) {
+        const int32_t v = Gb[(size_t)u * w + j];
+        if (v < 0 || seen[v]) continue;
+        seen[v] = 1;
+        const float dv = orc_distance(metric, x, row(X, v, d), d);
+        ++ev;
+        if (m == ef && !entry_less(dv, v, ld[m - 1], li[m - 1])) continue;
+        int p = m < ef ? m++ : ef - 1;
+        while (p > 0 && entry_less(dv, v, ld[p - 1], li[p - 1])) {
+          li[p] = li[p - 1]; ld[p] = ld[p - 1]; done[p] = done[p - 1];
+          --p;
+        }
+        li[p] = v; ld[p] = dv; done[p] = 0;
+      }
+    }
+    for (int j = 0; j < k_out; ++j) {
+      out_ids[(size_t)q * k_out + j] = j < m ? li[j] : -1;
+      out_dists[(size_t)q * k_out + j] = j < m ? ld[j] : INFINITY;
+    }
+    if (out_evals) out_evals[q] = ev;
+  }
+  free(G); free(seen); free(li); free(ld); free(done);
   return ORC_OK;
 }
