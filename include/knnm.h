@@ -181,6 +181,68 @@ int knnm_hmerge(knnm_ctx* ctx, const float* S, int64_t n, int d, int64_t first_r
                 float* out_dists, int n_layers, const int64_t* layer_rows, int32_t* layer_ids,
                 knnm_stats* stats);
 
+/* Rows of S in a given order: out[r] = S[perm[r]] for r < n (device pointers;
+ * S [n_src][d] with every perm[r] in [0, n_src), out [n][d]).  Used to lay out
+ * the H-Merge hierarchy's rows, which the graphs above address by position. */
+int knnm_gather_rows(knnm_ctx* ctx, const float* S, int64_t n_src, int d, const int32_t* perm,
+                     int64_t n, float* out);
+
+/* ---------------------------------------------------------------------------
+ * Graph diversification and the top-down search on the hierarchy (Sec. 3.4).
+ * Device pointers only.
+ * ------------------------------------------------------------------------- */
+
+typedef struct {
+  uint64_t dist_evals;   /* distances computed by the diversification kernels */
+  uint64_t edges;        /* sum of the output degrees */
+  int64_t full_rows;     /* rows whose degree reached max_degree */
+  int64_t max_in_degree; /* largest in-degree of the input graph */
+  float ms;              /* device time of the call */
+} knnm_gd_stats;
+
+/* Graph diversification (Alg. 3) of the k-NN graph G [n][k] on S [n][d]
+ * (ids in [0, n), no self, no repeats in a row; k <= 32), as a post-process.
+ * For each row a: its list, in (distance, id) order of the canonical distance
+ * of `metric`, keeps its first entry; every later entry s is dropped when an
+ * entry already kept is strictly closer to s than a is (m(s, c) < m(s, a)),
+ * else kept.  The reverse list {b : a in G[b]}, in the same order, is
+ * diversified by the same rule on its own.  The row's output is the union of
+ * both kept sets without repeats, in (distance, id) order, cut to max_degree
+ * (1..256) entries: out_ids/out_dists [n][max_degree], padded with -1 / +inf
+ * after out_degree[a] entries.  A malformed G is KNNM_ERR_INVALID. */
+int knnm_diversify(knnm_ctx* ctx, const float* S, int64_t n, int d, const int32_t* G, int k,
+                   int metric, int max_degree, int32_t* out_ids, float* out_dists,
+                   int32_t* out_degree, knnm_gd_stats* stats);
+
+typedef struct {
+  uint64_t dist_evals;     /* query-row distances computed */
+  int64_t crowded_queries; /* queries whose visited table filled: some rows were
+                              compared again (the results do not change) */
+  float ms;                /* device time of the call */
+} knnm_search_stats;
+
+/* Top-down k-NN search of the queries Q [nq][d] on a hierarchy of graphs
+ * over S [n][d] (Sec. 3.4).  Layer l (0 = top, n_layers - 1 = bottom; at most
+ * 32 layers) covers the first layer_rows[l] rows of S (non-decreasing, the
+ * bottom one n) with the graph layer_ids[l] [layer_rows[l]][layer_width[l]]
+ * (layer_width <= 1024; ids < 0 are padding; other ids must be below
+ * layer_rows[l], else KNNM_ERR_INVALID after the call).  layer_ids is a host
+ * array of device pointers.  Each query starts at row
+ * H(seed, 0, 9, q, 0) mod layer_rows[0] (the library's counter-based hash).
+ * Above the bottom it moves greedily: to the nearest neighbour of the current
+ * row while that one ranks before it in (distance, id) order.  At the bottom
+ * it runs best-first over a rank list of ef entries (k_out <= ef <= 1024):
+ * the first unexpanded entry is expanded, each neighbour not compared before
+ * enters when the list has room or it ranks before the last entry; it stops
+ * when every listed entry is expanded.  out_ids/out_dists [nq][k_out] hold
+ * the first k_out entries (-1 / +inf when fewer); out_evals [nq] (may be
+ * NULL) the distances each query computed. */
+int knnm_search(knnm_ctx* ctx, const float* S, int64_t n, int d, int metric, int n_layers,
+                const int64_t* layer_rows, const int32_t* layer_width,
+                const int32_t* const* layer_ids, const float* Q, int64_t nq, int ef, int k_out,
+                uint64_t seed, int32_t* out_ids, float* out_dists, uint32_t* out_evals,
+                knnm_search_stats* stats);
+
 /* Device scratch, in bytes, that one whole-merge call of these sizes takes
  * from its context (all arrays on the device).  mode: 0 = S-Merge, 1 = J-Merge
  * (n1 = 0 is the build).  Needs a context because the join configuration

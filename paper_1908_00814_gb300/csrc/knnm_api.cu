@@ -1399,3 +1399,204 @@ extern "C" int knnm_step_final(knnm_ctx* ctx, int64_t N, int K, const int32_t* i
   KNNM_CUDA(cudaStreamSynchronize(st));
   return KNNM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Graph diversification (Alg. 3) and the top-down search (Sec. 3.4)
+// ---------------------------------------------------------------------------
+
+namespace {
+
+int read_gd_counters(knnm_ctx* ctx, GdCounters* dev, GdCounters* host) {
+  KNNM_CUDA(cudaMemcpyAsync(host, dev, sizeof(GdCounters), cudaMemcpyDeviceToHost, ctx->stream));
+  KNNM_CUDA(cudaStreamSynchronize(ctx->stream));
+  return KNNM_OK;
+}
+
+bool all_device(std::initializer_list<const void*> ps) {
+  for (const void* p : ps)
+    if (!p || !is_device_ptr(p)) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" int knnm_gather_rows(knnm_ctx* ctx, const float* S, int64_t n_src, int d,
+                                const int32_t* perm, int64_t n, float* out) {
+  if (!ctx) return KNNM_ERR_INVALID;
+  ctx->err[0] = 0;
+  if (n_src < 1 || n < 0 || d < 1 || n_src > 0x7FFFFFFFLL || !all_device({S, perm, out}))
+    return fail(ctx, KNNM_ERR_INVALID, "bad gather arguments (device pointers only)");
+  KNNM_CUDA(cudaSetDevice(ctx->device));
+  Carver c0;
+  c0.take<GdCounters>(1);
+  int rc = ensure_arena(ctx, c0.off);
+  if (rc) return rc;
+  GdCounters* ctr = reinterpret_cast<GdCounters*>(ctx->arena);
+  cudaStream_t st = ctx->stream;
+  KNNM_CUDA(cudaMemsetAsync(ctr, 0, sizeof(GdCounters), st));
+  KNNM_CUDA(cudaMemsetAsync(&ctr->err_row, 0xFF, 8, st));
+  KNNM_CUDA(launch_gather_checked(S, n_src, perm, n, d, out, ctr, st));
+  GdCounters h;
+  rc = read_gd_counters(ctx, ctr, &h);
+  if (rc) return rc;
+  if (h.err)
+    return fail(ctx, KNNM_ERR_INVALID, "perm[%llu] is outside the rows of S",
+                (unsigned long long)h.err_row);
+  return KNNM_OK;
+}
+
+extern "C" int knnm_diversify(knnm_ctx* ctx, const float* S, int64_t n, int d, const int32_t* G,
+                              int k, int metric, int max_degree, int32_t* out_ids,
+                              float* out_dists, int32_t* out_degree, knnm_gd_stats* stats) {
+  if (!ctx) return KNNM_ERR_INVALID;
+  ctx->err[0] = 0;
+  if (n < 2 || n > 0x7FFFFFFFLL || d < 1 || k < 1 || k > 32 || k >= n || metric < 0 ||
+      metric > 3 || max_degree < 1 || max_degree > 256)
+    return fail(ctx, KNNM_ERR_INVALID, "bad diversification arguments (n=%lld k=%d max_degree=%d)",
+                (long long)n, k, max_degree);
+  if (!all_device({S, G, out_ids, out_dists, out_degree}))
+    return fail(ctx, KNNM_ERR_INVALID, "diversification takes device pointers only");
+  KNNM_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  GdArgs a;
+  float* norms = nullptr;
+  GdCounters* ctr = nullptr;
+  auto carve = [&](Carver& c) {
+    a.indeg = c.take<int32_t>((size_t)n);
+    a.rev_fill = c.take<int32_t>((size_t)n);
+    a.rev_off = c.take<unsigned long long>((size_t)n + 1);
+    a.tile_sum = c.take<unsigned long long>((size_t)(n + 1023) / 1024 + 1);
+    a.total = c.take<unsigned long long>(1);
+    a.rev = c.take<uint64_t>((size_t)n * k);
+    a.fwd = c.take<uint64_t>((size_t)n * k);
+    a.fwd_cnt = c.take<int32_t>((size_t)n);
+    norms = c.take<float>((size_t)n);
+    ctr = c.take<GdCounters>(1);
+  };
+  Carver c0;
+  carve(c0);
+  int rc = ensure_arena(ctx, c0.off);
+  if (rc) return rc;
+  Carver c1;
+  c1.base = (char*)ctx->arena;
+  carve(c1);
+  a.X = S;
+  a.n = n;
+  a.d = d;
+  a.vec4 = (d % 4 == 0 && aligned16(S)) ? 1 : 0;
+  a.norms = metric == KNNM_COS ? norms : nullptr;
+  a.G = G;
+  a.K = k;
+  a.M = max_degree;
+  a.out_ids = out_ids;
+  a.out_dists = out_dists;
+  a.out_deg = out_degree;
+  a.ctr = ctr;
+  KNNM_CUDA(cudaMemsetAsync(ctr, 0, sizeof(GdCounters), st));
+  KNNM_CUDA(cudaMemsetAsync(&ctr->err_row, 0xFF, 8, st));
+  KNNM_CUDA(cudaEventRecord(ctx->ev[0], st));
+  if (metric == KNNM_COS) KNNM_CUDA(launch_norms(Rows{S, S, n, d}, n, norms, st));
+  KNNM_CUDA(launch_diversify(a, metric, st));
+  KNNM_CUDA(cudaEventRecord(ctx->ev[1], st));
+  GdCounters h;
+  rc = read_gd_counters(ctx, ctr, &h);
+  if (rc) return rc;
+  if (h.err)
+    return fail(ctx, KNNM_ERR_INVALID, "input graph row %llu is malformed (%s)",
+                (unsigned long long)h.err_row,
+                (h.err & DERR_DUP_ID) ? "repeated id" : "id out of range or self");
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->dist_evals = h.dist_evals;
+    stats->edges = h.edges;
+    stats->full_rows = (int64_t)h.full_rows;
+    stats->max_in_degree = (int64_t)h.max_in;
+    KNNM_CUDA(cudaEventElapsedTime(&stats->ms, ctx->ev[0], ctx->ev[1]));
+  }
+  return KNNM_OK;
+}
+
+extern "C" int knnm_search(knnm_ctx* ctx, const float* S, int64_t n, int d, int metric,
+                           int n_layers, const int64_t* layer_rows, const int32_t* layer_width,
+                           const int32_t* const* layer_ids, const float* Q, int64_t nq, int ef,
+                           int k_out, uint64_t seed, int32_t* out_ids, float* out_dists,
+                           uint32_t* out_evals, knnm_search_stats* stats) {
+  if (!ctx) return KNNM_ERR_INVALID;
+  ctx->err[0] = 0;
+  if (n < 1 || n > 0x7FFFFFFFLL || d < 1 || nq < 0 || metric < 0 || metric > 3 || k_out < 1 ||
+      ef < k_out || ef > 1024 || n_layers < 1 || n_layers > SEARCH_MAX_LAYERS || !layer_rows ||
+      !layer_width || !layer_ids)
+    return fail(ctx, KNNM_ERR_INVALID, "bad search arguments (ef=%d k_out=%d layers=%d)", ef,
+                k_out, n_layers);
+  SearchArgs a;
+  memset(&a, 0, sizeof(a));
+  for (int l = 0; l < n_layers; ++l) {
+    if (layer_rows[l] < 1 || layer_rows[l] > n || (l > 0 && layer_rows[l] < layer_rows[l - 1]) ||
+        layer_width[l] < 1 || layer_width[l] > 1024 || !layer_ids[l] ||
+        !is_device_ptr(layer_ids[l]))
+      return fail(ctx, KNNM_ERR_INVALID, "bad layer %d (rows, width or device pointer)", l);
+    a.rows[l] = layer_rows[l];
+    a.width[l] = layer_width[l];
+    a.g[l] = layer_ids[l];
+  }
+  if (layer_rows[n_layers - 1] != n)
+    return fail(ctx, KNNM_ERR_INVALID, "the bottom layer must cover all %lld rows", (long long)n);
+  if (!all_device({S}) || (nq > 0 && !all_device({Q, out_ids, out_dists})) ||
+      (nq > 0 && out_evals && !is_device_ptr(out_evals)))
+    return fail(ctx, KNNM_ERR_INVALID, "search takes device pointers only");
+  KNNM_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  float* norms = nullptr;
+  GdCounters* ctr = nullptr;
+  auto carve = [&](Carver& c) {
+    norms = c.take<float>((size_t)n);
+    ctr = c.take<GdCounters>(1);
+  };
+  Carver c0;
+  carve(c0);
+  int rc = ensure_arena(ctx, c0.off);
+  if (rc) return rc;
+  Carver c1;
+  c1.base = (char*)ctx->arena;
+  carve(c1);
+  a.X = S;
+  a.n = n;
+  a.d = d;
+  a.vec4 = (d % 4 == 0 && aligned16(S)) ? 1 : 0;
+  a.norms = metric == KNNM_COS ? norms : nullptr;
+  a.n_layers = n_layers;
+  a.Q = Q;
+  a.nq = nq;
+  a.ef = ef;
+  a.k_out = k_out;
+  a.seed = seed;
+  a.out_ids = out_ids;
+  a.out_dists = out_dists;
+  a.out_evals = out_evals;
+  a.ctr = ctr;
+  size_t smem = 0;
+  int grid = 0;
+  cudaError_t pe = plan_search(&a, &smem, &grid);
+  if (pe != cudaSuccess)
+    return fail(ctx, KNNM_ERR_INVALID, "no search layout for d=%d ef=%d: %s", d, ef,
+                cudaGetErrorString(pe));
+  KNNM_CUDA(cudaMemsetAsync(ctr, 0, sizeof(GdCounters), st));
+  KNNM_CUDA(cudaMemsetAsync(&ctr->err_row, 0xFF, 8, st));
+  KNNM_CUDA(cudaEventRecord(ctx->ev[0], st));
+  if (metric == KNNM_COS) KNNM_CUDA(launch_norms(Rows{S, S, n, d}, n, norms, st));
+  if (nq > 0) KNNM_CUDA(launch_search(a, metric, smem, grid, st));
+  KNNM_CUDA(cudaEventRecord(ctx->ev[1], st));
+  GdCounters h;
+  rc = read_gd_counters(ctx, ctr, &h);
+  if (rc) return rc;
+  if (h.err)
+    return fail(ctx, KNNM_ERR_INVALID, "a layer graph lists an id beyond its layer (row %llu)",
+                (unsigned long long)h.err_row);
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->dist_evals = h.dist_evals;
+    stats->crowded_queries = (int64_t)h.overflow;
+    KNNM_CUDA(cudaEventElapsedTime(&stats->ms, ctx->ev[0], ctx->ev[1]));
+  }
+  return KNNM_OK;
+}

@@ -523,4 +523,78 @@ cudaError_t launch_unpack(int64_t count, const uint64_t* keys, int32_t* ids, flo
 cudaError_t launch_bf16_prep(Rows rows, int64_t N, __nv_bfloat16* Xb, float4* aux, float* rmax,
                              int half, unsigned long long* inexact, cudaStream_t st);
 
+// Exclusive scan of cnt[0..n) into offs[0..n] (offs[n] = total); tile_sum
+// needs ceil(n / 1024) entries.
+cudaError_t launch_exclusive_scan(const int32_t* cnt, int64_t n, unsigned long long* tile_sum,
+                                  unsigned long long* offs, unsigned long long* total,
+                                  cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Graph diversification (Alg. 3) and the top-down search (Sec. 3.4):
+// knnm_gd.cu.
+// ---------------------------------------------------------------------------
+struct GdCounters {
+  unsigned long long dist_evals;  // distances computed
+  unsigned long long edges;       // sum of output degrees
+  unsigned long long full_rows;   // rows whose degree reached the cap
+  unsigned long long max_in;      // largest in-degree of the input graph
+  unsigned long long overflow;    // search: queries whose visited table ran out of room
+  unsigned long long err;         // DevErr bits
+  unsigned long long err_row;     // smallest offending row
+};
+
+struct GdArgs {
+  const float* X;      // [n][d]
+  int64_t n;
+  int d;
+  int vec4;            // rows 16-byte aligned and d % 4 == 0
+  const float* norms;  // canonical norms [n] (COS), else nullptr
+  const int32_t* G;    // [n][K] input graph
+  int K;
+  int M;               // output degree cap
+  int32_t* indeg;      // [n] in-degrees (zeroed by the launcher)
+  int32_t* rev_fill;   // [n] reverse-bucket cursors (zeroed by the launcher)
+  unsigned long long* rev_off;  // [n+1]
+  unsigned long long* tile_sum;
+  unsigned long long* total;
+  uint64_t* rev;       // [n*K] reverse entries (distance, source)
+  uint64_t* fwd;       // [n][K] forward kept entries
+  int32_t* fwd_cnt;    // [n]
+  int32_t* out_ids;    // [n][M]
+  float* out_dists;    // [n][M]
+  int32_t* out_deg;    // [n]
+  GdCounters* ctr;
+};
+cudaError_t launch_diversify(const GdArgs& a, int metric, cudaStream_t st);
+cudaError_t launch_gather_checked(const float* X, int64_t n_src, const int32_t* perm, int64_t n,
+                                  int d, float* out, GdCounters* ctr, cudaStream_t st);
+size_t gd_reverse_smem(int M);
+
+constexpr int SEARCH_MAX_LAYERS = 32;
+struct SearchArgs {
+  const float* X;  // [n][d], layer l covers rows [0, rows[l])
+  int64_t n;
+  int d;
+  int vec4;
+  const float* norms;  // canonical norms [n] (COS), else nullptr
+  int n_layers;
+  int64_t rows[SEARCH_MAX_LAYERS];
+  int width[SEARCH_MAX_LAYERS];
+  const int32_t* g[SEARCH_MAX_LAYERS];  // [rows[l]][width[l]], ids < 0 are padding
+  const float* Q;  // [nq][d]
+  int64_t nq;
+  int ef, k_out;
+  uint64_t seed;
+  int hbits;       // visited table of 2^hbits ids per query
+  int warps;       // warps per block
+  int warp_bytes;  // shared memory per warp
+  int32_t* out_ids;
+  float* out_dists;
+  uint32_t* out_evals;  // [nq] or nullptr
+  GdCounters* ctr;
+};
+// Fills hbits / warps / warp_bytes and the launch shape.
+cudaError_t plan_search(SearchArgs* a, size_t* smem, int* grid);
+cudaError_t launch_search(const SearchArgs& a, int metric, size_t smem, int grid, cudaStream_t st);
+
 }  // namespace knnm

@@ -999,6 +999,17 @@ cudaError_t launch_init(const InitArgs& a, cudaStream_t st) {
   }
 }
 
+cudaError_t launch_exclusive_scan(const int32_t* cnt, int64_t n, unsigned long long* tile_sum,
+                                  unsigned long long* offs, unsigned long long* total,
+                                  cudaStream_t st) {
+  const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (ntiles == 0) return cudaMemsetAsync(offs, 0, sizeof(unsigned long long), st);
+  k_scan_tiles<<<(unsigned)ntiles, 256, 0, st>>>(cnt, n, tile_sum);
+  k_scan_sums<<<1, 1024, 0, st>>>(tile_sum, ntiles, total);
+  k_scan_apply<<<(unsigned)ntiles, 256, 0, st>>>(cnt, n, tile_sum, offs, total);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_norms(Rows rows, int64_t N, float* norms, cudaStream_t st) {
   if (N == 0) return cudaSuccess;
   k_norms<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(rows, N, norms);

@@ -87,6 +87,23 @@ class ServerStats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class GdStats(ctypes.Structure):
+    _fields_ = [("dist_evals", ctypes.c_uint64), ("edges", ctypes.c_uint64),
+                ("full_rows", ctypes.c_int64), ("max_in_degree", ctypes.c_int64),
+                ("ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class SearchStats(ctypes.Structure):
+    _fields_ = [("dist_evals", ctypes.c_uint64), ("crowded_queries", ctypes.c_int64),
+                ("ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _lib = None
 
 # name -> (restype, argtypes) of every entry point in include/knnm.h
@@ -120,6 +137,11 @@ SIGNATURES = {
                          _P, ctypes.POINTER(Stats)]),
     "knnm_merge_scratch_bytes": (_I, [_P, _I, _I64, _I64, _I, ctypes.POINTER(Params),
                                       ctypes.POINTER(ctypes.c_uint64)]),
+    "knnm_gather_rows": (_I, [_P, _P, _I64, _I, _P, _I64, _P]),
+    "knnm_diversify": (_I, [_P, _P, _I64, _I, _P, _I, _I, _I, _P, _P, _P,
+                            ctypes.POINTER(GdStats)]),
+    "knnm_search": (_I, [_P, _P, _I64, _I, _I, _I, _P, _P, _P, _P, _I64, _I, _I, _U64, _P, _P,
+                         _P, ctypes.POINTER(SearchStats)]),
     "knnm_server_create": (_I, [_I, _P, _I64, _P, _I, ctypes.POINTER(Params),
                                 ctypes.POINTER(ServerConfig), ctypes.POINTER(ctypes.c_void_p)]),
     "knnm_server_submit": (_I, [_P, _P, _I64, _U64]),
@@ -298,6 +320,59 @@ class Context:
             out[m] = lay[off * half:(off + m) * half].reshape(m, half)
             off += m
         return perm, ids, dists, out, st.as_dict()
+
+    # ------------------------------------------- diversification and search
+    # Sec. 3.4.  All arrays: CUDA torch tensors.
+    def gather_rows(self, S, perm, n=None):
+        """out[r] = S[perm[r]] for the first n entries of perm."""
+        import torch
+        n_src, d = S.shape
+        n = perm.shape[0] if n is None else n
+        out = torch.empty((n, d), dtype=torch.float32, device=S.device)
+        self._sync_stream()
+        self._check(lib().knnm_gather_rows(self.h, _ptr(S), n_src, d, _ptr(perm), n, _ptr(out)))
+        return out
+
+    def diversify(self, S, G, max_degree, metric="l2"):
+        """Alg. 3 on G's lists and reverse lists; returns (ids, dists, degree, stats),
+        ids/dists [n][max_degree] padded with -1 / inf."""
+        import torch
+        n, d = S.shape
+        k = G.shape[1]
+        m = METRICS[metric] if isinstance(metric, str) else int(metric)
+        ids = torch.empty((n, max_degree), dtype=torch.int32, device=S.device)
+        dists = torch.empty((n, max_degree), dtype=torch.float32, device=S.device)
+        deg = torch.empty(n, dtype=torch.int32, device=S.device)
+        st = GdStats()
+        self._sync_stream()
+        self._check(lib().knnm_diversify(self.h, _ptr(S), n, d, _ptr(G), k, m, max_degree,
+                                         _ptr(ids), _ptr(dists), _ptr(deg), ctypes.byref(st)))
+        return ids, dists, deg, st.as_dict()
+
+    def search(self, S, layers, Q, ef, k_out, metric="l2", seed=0):
+        """Top-down search; `layers` lists the layer graphs from the top down (layer
+        l covers the first len(layers[l]) rows of S).  Returns (ids, dists, evals,
+        stats) with k_out entries per query."""
+        import torch
+        n, d = S.shape
+        nq = Q.shape[0]
+        m = METRICS[metric] if isinstance(metric, str) else int(metric)
+        L = len(layers)
+        rows = (ctypes.c_int64 * L)(*[int(g.shape[0]) for g in layers])
+        width = (ctypes.c_int32 * L)(*[int(g.shape[1]) for g in layers])
+        for g in layers:
+            assert g.is_contiguous() and g.dtype == torch.int32
+        ptrs = (ctypes.c_void_p * L)(*[g.data_ptr() for g in layers])
+        ids = torch.empty((nq, k_out), dtype=torch.int32, device=S.device)
+        dists = torch.empty((nq, k_out), dtype=torch.float32, device=S.device)
+        evals = torch.empty(nq, dtype=torch.int32, device=S.device)
+        st = SearchStats()
+        self._sync_stream()
+        self._check(lib().knnm_search(self.h, _ptr(S), n, d, m, L, ctypes.cast(rows, _P),
+                                      ctypes.cast(width, _P), ctypes.cast(ptrs, _P), _ptr(Q), nq,
+                                      ef, k_out, seed, _ptr(ids), _ptr(dists), _ptr(evals),
+                                      ctypes.byref(st)))
+        return ids, dists, evals, st.as_dict()
 
     def scratch_bytes(self, mode, n1, n2, d, p: Params) -> int:
         """Device scratch one whole-merge call of these sizes takes."""
