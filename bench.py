@@ -385,6 +385,120 @@ def timed_call(torch, fn, steps, warmup):
     return e0.elapsed_time(e1) / steps, outs[-1], [o[2] for o in outs]
 
 
+def query_recall(torch, X_dev, Q_dev, ids_dev, K=10, extra=48, qchunk=1024, chunk=262144):
+    """recall@K of search results for external queries: candidates from an FP32
+    scan (K + extra per query), exact float64 distances of the candidates and of
+    the returned ids, ties at the K-th distance counted as hits."""
+    hits = 0
+    n = X_dev.shape[0]
+    xn = (X_dev.double() ** 2).sum(1).float()
+    prev_tf32 = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    for a in range(0, Q_dev.shape[0], qchunk):
+        Q = Q_dev[a:a + qchunk]
+        qn = (Q ** 2).sum(1)
+        best_d = best_i = None
+        for b in range(0, n, chunk):
+            D = qn[:, None] + xn[None, b:b + chunk] - 2.0 * (Q @ X_dev[b:b + chunk].T)
+            d2, i2 = torch.topk(D, min(K + extra, D.shape[1]), dim=1, largest=False)
+            i2 = i2 + b
+            if best_d is None:
+                best_d, best_i = d2, i2
+            else:
+                cd, ci = torch.cat([best_d, d2], 1), torch.cat([best_i, i2], 1)
+                best_d, o = torch.topk(cd, K + extra, dim=1, largest=False)
+                best_i = torch.gather(ci, 1, o)
+        Q64 = Q.double()
+        cand = ((X_dev[best_i].double() - Q64[:, None, :]) ** 2).sum(-1)
+        kth = torch.sort(cand, dim=1).values[:, K - 1]
+        got = ids_dev[a:a + qchunk, :K].long()
+        gd = ((X_dev[got.clamp_min(0)].double() - Q64[:, None, :]) ** 2).sum(-1)
+        ok = (gd <= kth[:, None] * (1 + 1e-9) + 1e-12) & (got >= 0)
+        hits += int(ok.sum().item())
+    torch.backends.cuda.matmul.allow_tf32 = prev_tf32
+    return hits / (Q_dev.shape[0] * K)
+
+
+def run_search(args, name):
+    """Graph diversification (Alg. 3) of an H-Merge hierarchy and the top-down
+    search on it (Sec. 3.4): 10,000 held-out queries, recall@10 and queries/s
+    for a sweep of rank-list sizes, beside a flat search of the bottom layer."""
+    import torch
+    from paper_1908_00814_gb300 import build as kbuild, knnm
+    kbuild.build()
+    torch.cuda.set_device(0)
+    ctx = knnm.Context(0)
+    w = dict(datagen.WORKLOADS[name])
+    if args.rows:
+        w["n"] = args.rows
+    n, d, K, nq = w["n"], w["d"], w["k"], w["queries"]
+    X = datagen.generate(name, n=n + nq)
+    base = torch.from_numpy(X[:n]).cuda()
+    Q = torch.from_numpy(X[n:]).cuda()
+    del X
+    first = 64
+    keep = [m for m in (64, 512, 4096, 32768, 262144) if m < n]
+    p = knnm.params(k=K, precision="bf16", max_iters=w["rounds"], sample_rate=w["sample_rate"],
+                    delta=0.001, seed=0)
+    t0 = time.perf_counter()
+    perm, ids, _, layers, hst = ctx.hmerge(base, first, p, layers=keep)
+    torch.cuda.synchronize()
+    ms_hmerge = (time.perf_counter() - t0) * 1000.0
+    Xp = ctx.gather_rows(base, torch.from_numpy(perm).cuda())
+    del base
+    graphs = [torch.from_numpy(layers[m]).cuda() for m in keep] + [torch.from_numpy(ids).cuda()]
+    caps = [K] * len(keep) + [2 * K]
+
+    def diversify_all():
+        outs = [ctx.diversify(Xp[:g.shape[0]], g, cap) for g, cap in zip(graphs, caps)]
+        return outs, None, [o[3] for o in outs]
+    ms_div, res, _ = timed_call(torch, diversify_all, args.steps, args.warmup)
+    outs = res[0]
+    div = [o[0] for o in outs]
+    layer_info = [{"rows": int(g.shape[0]), "width_in": int(g.shape[1]), "max_degree": cap,
+                   "mean_degree": o[3]["edges"] / g.shape[0],
+                   "max_in_degree": o[3]["max_in_degree"], "ms": o[3]["ms"]}
+                  for g, cap, o in zip(graphs, caps, outs)]
+    sweep = []
+    for label, lay in (("hierarchy", div), ("flat", div[-1:])):
+        for ef in (16, 32, 64, 128, 256):
+            if label == "flat" and ef not in (32, 128):
+                continue
+            def call():
+                ids_, dists_, _, st_ = ctx.search(Xp, lay, Q, ef, 10, seed=0)
+                return ids_, dists_, st_
+            ms, out, sts = timed_call(torch, call, args.steps, args.warmup)
+            r = {"layers": label, "ef": ef, "ms": ms, "queries_per_s": nq / (ms / 1000.0),
+                 "recall_at_10": query_recall(torch, Xp, Q, out[0], K=10),
+                 "mean_dist_evals": sts[-1]["dist_evals"] / nq,
+                 "crowded_queries": sts[-1]["crowded_queries"]}
+            sweep.append(r)
+            print(f"# {label} ef={ef}: {ms:.2f} ms, {r['queries_per_s']:.0f} q/s, recall "
+                  f"{r['recall_at_10']:.4f}, {r['mean_dist_evals']:.0f} evals/query",
+                  file=sys.stderr, flush=True)
+    good = [r for r in sweep if r["layers"] == "hierarchy" and r["recall_at_10"] >= 0.95]
+    head = max(good, key=lambda r: r["queries_per_s"]) if good else sweep[-1]
+    line = {"metric": "queries/s of the top-down search at recall@10>=0.95 (Sec. 3.4)",
+            "value": head["queries_per_s"], "unit": "queries/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": name, "n": n, "d": d, "k": K, "queries": nq,
+                       "metric": "l2", "hierarchy": f"H-Merge from {first} rows, BF16, "
+                       f"upper layers {keep} (k/2 lists), bottom k",
+                       "diversify": "Alg. 3, lists + reverse lists, degree caps k above, "
+                                    "2k at the bottom",
+                       "head_ef": head["ef"], "parallelism": "replicas"},
+            "recall_at_10": head["recall_at_10"],
+            "ms_hmerge": ms_hmerge, "hmerge_merges": hst["rounds"],
+            "ms_diversify_all_layers": ms_div,
+            "diversify_points_per_s": sum(li["rows"] for li in layer_info) / (ms_div / 1000.0),
+            "layers": layer_info, "sweep": sweep}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def run_other(args, name):
     """The other merge workloads, one JSON line each: the joint merge of 1M raw
     cosine vectors into a 1M graph (96-d), and the 960-d GIST-like symmetric
@@ -711,7 +825,7 @@ def main():
     ap.add_argument("--reference-rows", type=int, default=5000)
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "jmerge_gmm_2m_d96_k16_cos", "smerge_gist_1m_d960_k20",
-                             "hmerge_sift_1m_d128_k20"],
+                             "hmerge_sift_1m_d128_k20", "hsearch_sift_1m_d128_k20"],
                     help="another merge workload (one JSON line of its own)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-batches", type=int, default=16)
@@ -728,6 +842,8 @@ def main():
         w["n"] = args.rows
     if args.impl == "reference":
         return run_reference(args, w)
+    if args.workload == "hsearch_sift_1m_d128_k20":
+        return run_search(args, args.workload)
     if args.workload != WORKLOAD:
         return run_other(args, args.workload)
     return run_ours(args, w)

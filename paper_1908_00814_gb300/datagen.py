@@ -89,6 +89,26 @@ def sift_like(n: int, d: int = 128, n_centres: int = 256, seed: int = 0, rank: i
     return X
 
 
+def sift_manifold(n: int, d: int = 128, latent: int = 16, n_comp: int = 64, sep: float = 1.5,
+                  seed: int = 0, chunk: int = 1 << 16) -> np.ndarray:
+    """Search stand-in for SIFT: a 16-d latent mixture of 64 overlapping unit
+    Gaussians (means N(0, sep^2)), mapped to d dims by a random N(0, 1/latent)
+    matrix, scaled and rounded to integers in [0, 255].  Unlike sift_like's
+    well-separated clusters (whose k-NN graph splits into one component per
+    cluster, which no graph search can cross), its k-NN graph is one weakly
+    connected component."""
+    rng = _rng(seed)
+    means = rng.normal(0.0, sep, size=(n_comp, latent))
+    M = rng.normal(0.0, 1.0 / np.sqrt(latent), size=(d, latent))
+    which = rng.integers(0, n_comp, size=n)
+    X = np.empty((n, d), np.float32)
+    for b in range(0, n, chunk):
+        e = min(n, b + chunk)
+        z = means[which[b:e]] + rng.standard_normal((e - b, latent))
+        X[b:e] = np.clip(np.rint(64.0 + 16.0 * (z @ M.T)), 0, 255)
+    return X
+
+
 def gist_like(n: int, d: int = 960, latent: int = 64, seed: int = 0, n_comp: int = 256,
               rank: int = 16, chunk: int = 1 << 16) -> np.ndarray:
     """|M u|: a random d x d mixing M (entries N(0, 1/d)) of u = [z; 0.02 e],
@@ -132,6 +152,9 @@ WORKLOADS = {
     "hmerge_sift_1m_d128_k20": dict(kind="hmerge", gen="sift_like", n=1_000_000, d=128, k=20,
                                     metric="l2", rounds=10, sample_rate=0.5, seed=1006,
                                     gen_args={}),
+    "hsearch_sift_1m_d128_k20": dict(kind="hsearch", gen="sift_manifold", n=1_000_000, d=128, k=20,
+                                     metric="l2", rounds=10, sample_rate=0.5, seed=1007,
+                                     queries=10_000, gen_args={}),
     "smerge_gist_1m_d960_k20": dict(kind="symmetric", gen="gist_like", n=1_000_000, d=960,
                                     k=20, metric="l1", rounds=10, sample_rate=0.5, seed=1005,
                                     gen_args={}),
@@ -156,5 +179,6 @@ def poisson_arrivals(count: int, rate_per_s: float, seed: int) -> np.ndarray:
 def generate(name: str, n: int | None = None) -> np.ndarray:
     w = WORKLOADS[name]
     gen = {"gaussian_mixture": gaussian_mixture, "sift_like": sift_like,
+           "sift_manifold": sift_manifold,
            "gist_like": gist_like, "clustered_mixture": clustered_mixture}[w["gen"]]
     return gen(n if n is not None else w["n"], w["d"], seed=w["seed"], **w["gen_args"])
