@@ -68,7 +68,8 @@ def lib():
         L.orc_bruteforce_knn.argtypes = [P, i64, i32, i32, i32, P, P]
         L.orc_bruteforce_merge.argtypes = [P, i64, i64, i32, i32, P, P, i32, P, P]
         L.orc_diversify.argtypes = [P, i64, i32, i32, P, i32, i32, P, i64, P, P, P, P]
-        L.orc_search.argtypes = [P, i64, i32, i32, i32, P, P, P, P, i64, i32, i32, u64, P, P, P]
+        L.orc_search.argtypes = [P, i64, i32, i32, i32, P, P, P, P, i64, P, i32, i32, u64, P, P,
+                                 P]
         for name in ("orc_init", "orc_sample", "orc_join", "orc_final", "orc_merge",
                      "orc_permute", "orc_bruteforce_knn", "orc_bruteforce_merge",
                      "orc_diversify", "orc_search"):
@@ -294,12 +295,14 @@ def diversify(S, G, max_degree, metric=L2, rows=None):
     return ids, dists, deg, int(ev.value)
 
 
-def search(S, layers, Q, ef, k_out, metric=L2, seed=0):
+def search(S, layers, Q, ef, k_out, metric=L2, seed=0, query_index=None):
     """Top-down search (Sec. 3.4) of the queries Q on a hierarchy: `layers` is a
     list of id arrays from the top layer down, layer l covering the first
     len(layers[l]) rows of S (the bottom one all of them; ids < 0 are padding).
     Greedy descent above the bottom, best-first over an ef-entry rank list at the
-    bottom.  Returns (ids, dists, evals) with k_out entries per query."""
+    bottom.  Query q starts from the hash of its batch index, or of
+    query_index[q] when given.  Returns (ids, dists, evals) with k_out entries
+    per query."""
     S, Q = _f32(S), _f32(Q)
     n, d = S.shape
     rows = np.array([len(g) for g in layers], np.int64)
@@ -309,9 +312,10 @@ def search(S, layers, Q, ef, k_out, metric=L2, seed=0):
     ids = np.empty((nq, k_out), np.int32)
     dists = np.empty((nq, k_out), np.float32)
     ev = np.empty(nq, np.uint64)
+    qi = None if query_index is None else np.ascontiguousarray(query_index, dtype=np.int64)
     _check(lib().orc_search(_ptr(S), n, d, metric, len(layers), _ptr(rows), _ptr(width),
-                            _ptr(flat), _ptr(Q), nq, ef, k_out, seed, _ptr(ids), _ptr(dists),
-                            _ptr(ev)), "search")
+                            _ptr(flat), _ptr(Q), nq, _ptr(qi), ef, k_out, seed, _ptr(ids),
+                            _ptr(dists), _ptr(ev)), "search")
     return ids, dists, ev
 
 

@@ -726,7 +726,8 @@ int orc_diversify(const float* X, int64_t n, int d, int metric, const int32_t* G
 /*   - Layers run from the top (fewest rows) to the bottom; layer l holds   */
 /*     the first layer_rows[l] rows of X and a graph of layer_width[l]      */
 /*     entries per row (ids < 0 are padding and skipped).                  */
-/*   - The search starts at row H(seed, 0, 9, q, 0) mod layer_rows[0].     */
+/*   - Query q starts at row H(seed, 0, 9, q, 0) mod layer_rows[0] (q its  */
+/*     index in the batch; qidx, when given, supplies it per query).       */
 /*   - Above the bottom: greedy.  All neighbours of the current row are    */
 /*     compared with the query; the current row moves to the nearest of   */
 /*     them while that one ranks before it in (distance, id) order.        */
@@ -741,8 +742,8 @@ int orc_diversify(const float* X, int64_t n, int d, int metric, const int32_t* G
 
 int orc_search(const float* X, int64_t n, int d, int metric, int n_layers,
                const int64_t* layer_rows, const int32_t* layer_width, const int32_t* graphs,
-               const float* Q, int64_t nq, int ef, int k_out, uint64_t seed, int32_t* out_ids,
-               float* out_dists, uint64_t* out_evals) {
+               const float* Q, int64_t nq, const int64_t* qidx, int ef, int k_out,
+               uint64_t seed, int32_t* out_ids, float* out_dists, uint64_t* out_evals) {
   if (n < 1 || n_layers < 1 || ef < 1 || k_out < 1 || k_out > ef) return ORC_ERR_INVALID;
   if (layer_rows[n_layers - 1] != n) return ORC_ERR_INVALID;
   const int32_t** G = (const int32_t**)malloc(sizeof(int32_t*) * (size_t)n_layers);
@@ -762,7 +763,8 @@ int orc_search(const float* X, int64_t n, int d, int metric, int n_layers,
   for (int64_t q = 0; q < nq; ++q) {
     const float* x = row(Q, q, d);
     uint64_t ev = 1;
-    int32_t cur = (int32_t)(orc_hash(seed, 0, 9, (uint64_t)q, 0) % (uint64_t)layer_rows[0]);
+    const uint64_t qi = (uint64_t)(qidx ? qidx[q] : q);
+    int32_t cur = (int32_t)(orc_hash(seed, 0, 9, qi, 0) % (uint64_t)layer_rows[0]);
     float dcur = orc_distance(metric, x, row(X, cur, d), d);
     for (int l = 0; l + 1 < n_layers; ++l) {
       const int w = layer_width[l];
