@@ -459,13 +459,14 @@ def run_search(args, name):
                    "mean_degree": o[3]["edges"] / g.shape[0],
                    "max_in_degree": o[3]["max_in_degree"], "ms": o[3]["ms"]}
                   for g, cap, o in zip(graphs, caps, outs)]
+    aux = ctx.search_prepare(Xp)
     sweep = []
     for label, lay in (("hierarchy", div), ("flat", div[-1:])):
         for ef in (16, 32, 64, 128, 256):
             if label == "flat" and ef not in (32, 128):
                 continue
             def call():
-                ids_, dists_, _, st_ = ctx.search(Xp, lay, Q, ef, 10, seed=0)
+                ids_, dists_, _, st_ = ctx.search(Xp, lay, Q, ef, 10, seed=0, row_aux=aux)
                 return ids_, dists_, st_
             ms, out, sts = timed_call(torch, call, args.steps, args.warmup)
             r = {"layers": label, "ef": ef, "ms": ms, "queries_per_s": nq / (ms / 1000.0),

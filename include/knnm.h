@@ -221,8 +221,15 @@ typedef struct {
   float ms;                /* device time of the call */
 } knnm_search_stats;
 
+/* Per-row data the search reads, row_aux [n][2] floats: {max |x| when every
+ * coordinate of the row is an integer of magnitude <= 2^24, else -1; the
+ * row's canonical norm}.  Compute it once per row set and pass it to every
+ * knnm_search over that set (device pointers). */
+int knnm_search_prepare(knnm_ctx* ctx, const float* S, int64_t n, int d, float* row_aux);
+
 /* Top-down k-NN search of the queries Q [nq][d] on a hierarchy of graphs
- * over S [n][d] (Sec. 3.4).  Layer l (0 = top, n_layers - 1 = bottom; at most
+ * over S [n][d] (Sec. 3.4).  row_aux: knnm_search_prepare's output for S, or
+ * NULL to compute it inside the call.  Layer l (0 = top, n_layers - 1 = bottom; at most
  * 32 layers) covers the first layer_rows[l] rows of S (non-decreasing, the
  * bottom one n) with the graph layer_ids[l] [layer_rows[l]][layer_width[l]]
  * (layer_width <= 1024; ids < 0 are padding; other ids must be below
@@ -236,8 +243,12 @@ typedef struct {
  * enters when the list has room or it ranks before the last entry; it stops
  * when every listed entry is expanded.  out_ids/out_dists [nq][k_out] hold
  * the first k_out entries (-1 / +inf when fewer); out_evals [nq] (may be
- * NULL) the distances each query computed. */
-int knnm_search(knnm_ctx* ctx, const float* S, int64_t n, int d, int metric, int n_layers,
+ * NULL) the distances each query computed.  Every distance is the canonical
+ * one: a row is first compared by a reordered sum, which is used as is only
+ * when both rows are small integers (every partial sum exact) and otherwise
+ * only to skip rows that provably cannot enter the rank list. */
+int knnm_search(knnm_ctx* ctx, const float* S, int64_t n, int d, const float* row_aux,
+                int metric, int n_layers,
                 const int64_t* layer_rows, const int32_t* layer_width,
                 const int32_t* const* layer_ids, const float* Q, int64_t nq, int ef, int k_out,
                 uint64_t seed, int32_t* out_ids, float* out_dists, uint32_t* out_evals,

@@ -1516,8 +1516,21 @@ extern "C" int knnm_diversify(knnm_ctx* ctx, const float* S, int64_t n, int d, c
   return KNNM_OK;
 }
 
-extern "C" int knnm_search(knnm_ctx* ctx, const float* S, int64_t n, int d, int metric,
-                           int n_layers, const int64_t* layer_rows, const int32_t* layer_width,
+extern "C" int knnm_search_prepare(knnm_ctx* ctx, const float* S, int64_t n, int d,
+                                   float* row_aux) {
+  if (!ctx) return KNNM_ERR_INVALID;
+  ctx->err[0] = 0;
+  if (n < 1 || n > 0x7FFFFFFFLL || d < 1 || !all_device({S, row_aux}))
+    return fail(ctx, KNNM_ERR_INVALID, "bad search_prepare arguments (device pointers only)");
+  KNNM_CUDA(cudaSetDevice(ctx->device));
+  KNNM_CUDA(launch_row_aux(S, n, d, row_aux, ctx->stream));
+  KNNM_CUDA(cudaStreamSynchronize(ctx->stream));
+  return KNNM_OK;
+}
+
+extern "C" int knnm_search(knnm_ctx* ctx, const float* S, int64_t n, int d, const float* row_aux,
+                           int metric, int n_layers, const int64_t* layer_rows,
+                           const int32_t* layer_width,
                            const int32_t* const* layer_ids, const float* Q, int64_t nq, int ef,
                            int k_out, uint64_t seed, int32_t* out_ids, float* out_dists,
                            uint32_t* out_evals, knnm_search_stats* stats) {
@@ -1542,14 +1555,14 @@ extern "C" int knnm_search(knnm_ctx* ctx, const float* S, int64_t n, int d, int 
   if (layer_rows[n_layers - 1] != n)
     return fail(ctx, KNNM_ERR_INVALID, "the bottom layer must cover all %lld rows", (long long)n);
   if (!all_device({S}) || (nq > 0 && !all_device({Q, out_ids, out_dists})) ||
-      (nq > 0 && out_evals && !is_device_ptr(out_evals)))
+      (nq > 0 && out_evals && !is_device_ptr(out_evals)) || (row_aux && !is_device_ptr(row_aux)))
     return fail(ctx, KNNM_ERR_INVALID, "search takes device pointers only");
   KNNM_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
-  float* norms = nullptr;
+  float* aux = nullptr;
   GdCounters* ctr = nullptr;
   auto carve = [&](Carver& c) {
-    norms = c.take<float>((size_t)n);
+    aux = c.take<float>(row_aux ? 1 : (size_t)n * 2);
     ctr = c.take<GdCounters>(1);
   };
   Carver c0;
@@ -1563,7 +1576,7 @@ extern "C" int knnm_search(knnm_ctx* ctx, const float* S, int64_t n, int d, int 
   a.n = n;
   a.d = d;
   a.vec4 = (d % 4 == 0 && aligned16(S)) ? 1 : 0;
-  a.norms = metric == KNNM_COS ? norms : nullptr;
+  a.aux = row_aux ? row_aux : aux;
   a.n_layers = n_layers;
   a.Q = Q;
   a.nq = nq;
@@ -1583,7 +1596,7 @@ extern "C" int knnm_search(knnm_ctx* ctx, const float* S, int64_t n, int d, int 
   KNNM_CUDA(cudaMemsetAsync(ctr, 0, sizeof(GdCounters), st));
   KNNM_CUDA(cudaMemsetAsync(&ctr->err_row, 0xFF, 8, st));
   KNNM_CUDA(cudaEventRecord(ctx->ev[0], st));
-  if (metric == KNNM_COS) KNNM_CUDA(launch_norms(Rows{S, S, n, d}, n, norms, st));
+  if (!row_aux) KNNM_CUDA(launch_row_aux(S, n, d, aux, st));
   if (nq > 0) KNNM_CUDA(launch_search(a, metric, smem, grid, st));
   KNNM_CUDA(cudaEventRecord(ctx->ev[1], st));
   GdCounters h;

@@ -12,7 +12,10 @@
 // Search: one warp per query, the query staged in shared memory.  Greedy moves
 // on the layers above the bottom; best-first at the bottom over a rank list of
 // ef entries in shared memory, with a per-query visited table (open
-// addressing).  When the table is crowded a row may be compared again; a row
+// addressing).  Rows are compared four at a time, eight lanes each, by a
+// reordered sum; that estimate is the canonical distance when both rows are
+// small integers (every partial sum exact), settles a row that provably
+// cannot enter the list otherwise, and leaves the rest to the in-order sum.  When the table is crowded a row may be compared again; a row
 // that was dropped from the full rank list can never re-enter it (its key is
 // above the list's last entry, which only decreases), and repeats of listed
 // rows are dropped, so the result is that of the exact visited set.
@@ -305,8 +308,10 @@ __global__ void __launch_bounds__(GD_WARPS * 32) k_gd_reverse(const GdArgs a) {
 
 __host__ __device__ __forceinline__ int round16(int x) { return (x + 15) & ~15; }
 __host__ __device__ __forceinline__ int search_qbytes(int d) { return round16(4 * d); }
+// Per-warp shared memory: query, the rank list with its expanded flags, 32
+// candidate keys (also the ids of the rows being compared), the visited table.
 __host__ __device__ __forceinline__ int search_warp_bytes(int d, int ef, int hbits) {
-  return search_qbytes(d) + 16 * ef + 2 * round16(ef) + 8 * 32 + (4 << hbits);
+  return search_qbytes(d) + round16(8 * ef) + round16(ef) + 8 * 32 + (4 << hbits);
 }
 
 // Marks id v as seen: 1 when newly recorded, 0 when recorded before, 2 when
@@ -323,29 +328,101 @@ __device__ __forceinline__ int visit(int32_t* H, int hbits, int32_t v) {
   return 2;
 }
 
+// Per-row search data: {max |x| when every coordinate is an integer of
+// magnitude <= 2^24, else -1; canonical norm}.  One warp per row: the row is
+// read coalesced into shared memory, checked by all lanes, and its norm summed
+// in index order by lane 0.
+constexpr int AUX_WARPS = 8;
+constexpr int AUX_CHUNK = 1024;  // floats staged per pass
+__global__ void __launch_bounds__(AUX_WARPS * 32) k_row_aux(const float* X, int64_t n, int d,
+                                                            float2* aux) {
+  __shared__ float stage[AUX_WARPS][AUX_CHUNK];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float* sx = stage[w];
+  for (int64_t i = (int64_t)blockIdx.x * AUX_WARPS + w; i < n;
+       i += (int64_t)gridDim.x * AUX_WARPS) {
+    const float* r = X + (size_t)i * d;
+    float acc = 0.0f, mx = 0.0f;
+    bool integral = true;
+    for (int t0 = 0; t0 < d; t0 += AUX_CHUNK) {
+      const int len = min(AUX_CHUNK, d - t0);
+      for (int t = lane; t < len; t += 32) {
+        const float x = __ldg(r + t0 + t);
+        sx[t] = x;
+        mx = fmaxf(mx, fabsf(x));
+        integral = integral && x == rintf(x);
+      }
+      __syncwarp();
+      if (lane == 0)
+        for (int t = 0; t < len; ++t) acc = __fmaf_rn(sx[t], sx[t], acc);
+      __syncwarp();
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, o));
+    integral = __all_sync(FULL, integral);
+    if (lane == 0) aux[i] = make_float2(integral && mx <= 16777216.0f ? mx : -1.0f, __fsqrt_rn(acc));
+  }
+}
+
+// True when every partial sum of the pair's canonical accumulation is an
+// integer below 2^24 in magnitude: then any summation order gives the
+// canonical bits.  qm, rm: max |coordinate| of two integer rows.
 template <int METRIC>
-__global__ void __launch_bounds__(256) k_search(const SearchArgs a) {
+__device__ __forceinline__ bool exact_pair(float qm, float rm, int d) {
+  if (qm < 0.0f || rm < 0.0f) return false;
+  const unsigned long long q = (unsigned long long)qm, r = (unsigned long long)rm;
+  const unsigned long long lim = 1ull << 24;
+  if (METRIC == L2) return (unsigned long long)d * (q + r) * (q + r) < lim;
+  if (METRIC == L1) return (unsigned long long)d * (q + r) < lim;
+  return (unsigned long long)d * q * r < lim;  // IP, COS: the dot product
+}
+
+// Upper bound on |estimate - canonical| for one pair, where both are sums of
+// the same exactly known terms in different orders (each within
+// gamma_d * sum|terms| of the exact sum, gamma_m = m u / (1 - m u)).
+template <int METRIC>
+__device__ __forceinline__ float pair_bound(float est, float g, float nq, float nr, float den) {
+  if (METRIC == L2 || METRIC == L1) return 2.0f * g * est / (1.0f - g) * 1.0001f;
+  const float dot = 2.2f * g * nq * nr;  // sum |a_i b_i| <= |a||b| (norms within gamma)
+  if (METRIC == IP) return dot * 1.0001f + 1e-37f;
+  if (den == 0.0f) return 0.0f;  // both read 1
+  return (dot / den) * 1.0001f + 8.0f * 5.9604645e-8f;  // COS: division and 1 - x
+}
+
+template <int METRIC>
+__global__ void __launch_bounds__(128) k_search(const SearchArgs a) {
   extern __shared__ __align__(16) unsigned char s_sm[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   unsigned char* base = s_sm + (size_t)w * a.warp_bytes;
   float* qs = reinterpret_cast<float*>(base);
-  uint64_t* LA = reinterpret_cast<uint64_t*>(base + search_qbytes(a.d));
-  uint64_t* LB = LA + a.ef;
-  uint8_t* FA = reinterpret_cast<uint8_t*>(LB + a.ef);
-  uint8_t* FB = FA + round16(a.ef);
-  uint64_t* cand = reinterpret_cast<uint64_t*>(FB + round16(a.ef));
+  unsigned char* lists = base + search_qbytes(a.d);
+  uint64_t* LA = reinterpret_cast<uint64_t*>(lists);
+  uint8_t* FA = lists + round16(8 * a.ef);
+  uint64_t* cand = reinterpret_cast<uint64_t*>(FA + round16(a.ef));
+  int32_t* vid = reinterpret_cast<int32_t*>(cand);  // row ids under comparison (before a merge)
   int32_t* H = reinterpret_cast<int32_t*>(cand + 32);
   const int hsize = 1 << a.hbits;
   const int L = a.n_layers;
   const unsigned lt = (1u << lane) - 1u;
+  const int grp = lane >> 3, part = lane & 7;  // 4 rows per pass, 8 lanes per row
+  // gamma_{d+2} for the estimate bounds
+  const float g = (float)(a.d + 2) * 5.9604645e-8f / (1.0f - (float)(a.d + 2) * 5.9604645e-8f);
   unsigned long long evals_all = 0, overflow = 0;
   for (int64_t q = (int64_t)blockIdx.x * a.warps + w; q < a.nq;
        q += (int64_t)gridDim.x * a.warps) {
     const float* qg = a.Q + (size_t)q * a.d;
-    for (int t = lane; t < a.d; t += 32) qs[t] = qg[t];
+    bool qint = true;
+    float qmax = 0.0f;
+    for (int t = lane; t < a.d; t += 32) {
+      const float x = qg[t];
+      qs[t] = x;
+      qmax = fmaxf(qmax, fabsf(x));
+      qint = qint && x == rintf(x);
+    }
+    for (int o = 16; o > 0; o >>= 1) qmax = fmaxf(qmax, __shfl_xor_sync(FULL, qmax, o));
+    qmax = (__all_sync(FULL, qint) && qmax <= 16777216.0f) ? qmax : -1.0f;
     __syncwarp();
     float qn = 0.0f;
-    if (METRIC == COS) {
+    if (METRIC == COS || METRIC == IP) {
       if (lane == 0) {
         float acc = 0.0f;
         for (int t = 0; t < a.d; ++t) acc = __fmaf_rn(qs[t], qs[t], acc);
@@ -353,16 +430,100 @@ __global__ void __launch_bounds__(256) k_search(const SearchArgs a) {
       }
       qn = __shfl_sync(FULL, qn, 0);
     }
-    auto dist_q = [&](int32_t v) {
-      const float nr = METRIC == COS ? __ldg(a.norms + v) : 0.0f;
-      return dist_query<METRIC>(qs, a.X + (size_t)v * a.d, a.d, a.vec4, qn, nr);
+    // Keys of the rows v of the lanes with `want`.  A row is first estimated
+    // by 8 lanes (a reordered sum of the canonical terms); the estimate is the
+    // canonical value when exact_pair holds; otherwise, when `filter` is set
+    // and the estimate proves the row's distance above thr, the row cannot
+    // enter and comes back as KEY_EMPTY; every other row gets its canonical
+    // distance from its own lane (in-order sum).
+    auto eval = [&](int32_t v, bool want, bool filter, float thr) {
+      const unsigned m = __ballot_sync(FULL, want);
+      const int cnt_f = __popc(m), rank = __popc(m & lt);
+      float2 ax = make_float2(-1.0f, 0.0f);
+      if (want) {
+        vid[rank] = v;
+        ax = __ldg(reinterpret_cast<const float2*>(a.aux) + v);  // consumed after the rows
+      }
+      __syncwarp();
+      float est_acc = 0.0f;
+      const int n4 = a.d >> 2;
+      // 8 rows per batch, two per 8-lane group; every load of a batch is issued
+      // before any of its sums starts
+      for (int p0 = 0; p0 < cnt_f; p0 += 8) {
+        const int ra = p0 + grp, rb = p0 + 4 + grp;
+        const bool va = ra < cnt_f, vb = rb < cnt_f;
+        const float* rowa = a.X + (size_t)(va ? vid[ra] : 0) * a.d;
+        const float* rowb = a.X + (size_t)(vb ? vid[rb] : 0) * a.d;
+        float acca = 0.0f, accb = 0.0f;
+        if (a.vec4) {
+          const float4* q4 = reinterpret_cast<const float4*>(qs);
+          const float4* a4 = reinterpret_cast<const float4*>(rowa);
+          const float4* b4 = reinterpret_cast<const float4*>(rowb);
+          for (int c0 = part; c0 < n4; c0 += 32) {
+            float4 ya[4], yb[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int c = c0 + 8 * u;
+              const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+              ya[u] = (va && c < n4) ? __ldg(a4 + c) : z;
+              yb[u] = (vb && c < n4) ? __ldg(b4 + c) : z;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int c = c0 + 8 * u;
+              if (c < n4) {
+                const float4 x = q4[c];
+                acca = Canon<METRIC>::step(acca, x.x, ya[u].x);
+                acca = Canon<METRIC>::step(acca, x.y, ya[u].y);
+                acca = Canon<METRIC>::step(acca, x.z, ya[u].z);
+                acca = Canon<METRIC>::step(acca, x.w, ya[u].w);
+                accb = Canon<METRIC>::step(accb, x.x, yb[u].x);
+                accb = Canon<METRIC>::step(accb, x.y, yb[u].y);
+                accb = Canon<METRIC>::step(accb, x.z, yb[u].z);
+                accb = Canon<METRIC>::step(accb, x.w, yb[u].w);
+              }
+            }
+          }
+        } else {
+          for (int t = part; t < a.d; t += 8) {
+            const float ya = va ? __ldg(rowa + t) : 0.0f, yb = vb ? __ldg(rowb + t) : 0.0f;
+            acca = Canon<METRIC>::step(acca, qs[t], ya);
+            accb = Canon<METRIC>::step(accb, qs[t], yb);
+          }
+        }
+        acca = __fadd_rn(acca, __shfl_xor_sync(FULL, acca, 1));
+        acca = __fadd_rn(acca, __shfl_xor_sync(FULL, acca, 2));
+        acca = __fadd_rn(acca, __shfl_xor_sync(FULL, acca, 4));
+        accb = __fadd_rn(accb, __shfl_xor_sync(FULL, accb, 1));
+        accb = __fadd_rn(accb, __shfl_xor_sync(FULL, accb, 2));
+        accb = __fadd_rn(accb, __shfl_xor_sync(FULL, accb, 4));
+        const int src = ((rank - p0) & 3) << 3;
+        const float ea = __shfl_sync(FULL, acca, src), eb = __shfl_sync(FULL, accb, src);
+        if (want && rank >= p0 && rank < p0 + 4) est_acc = ea;
+        if (want && rank >= p0 + 4 && rank < p0 + 8) est_acc = eb;
+      }
+      __syncwarp();
+      uint64_t k = KEY_EMPTY;
+      bool need = false;
+      if (want) {
+        const float nr = ax.y;
+        const float est = canon_finish<METRIC>(est_acc, qn, nr);
+        if (exact_pair<METRIC>(qmax, ax.x, a.d)) {
+          k = make_key(est, v);
+        } else {
+          const float den = __fmul_rn(qn, nr);
+          need = !(filter && est - pair_bound<METRIC>(est, g, qn, nr, den) > thr);
+        }
+      }
+      if (__any_sync(FULL, need) && need)
+        k = make_key(dist_query<METRIC>(qs, a.X + (size_t)v * a.d, a.d, a.vec4, qn, ax.y), v);
+      return k;
     };
     uint32_t ev = 1;
     const int32_t start =
         (int32_t)(mix_step(hash_prefix(a.seed, 0, 9, (uint64_t)q) ^ 0ull) % (uint64_t)a.rows[0]);
-    float d0 = 0.0f;
-    if (lane == 0) d0 = dist_q(start);
-    uint64_t ck = make_key(__shfl_sync(FULL, d0, 0), start);
+    uint64_t ck = eval(start, lane == 0, false, 0.0f);
+    ck = __shfl_sync(FULL, ck, 0);
     // greedy descent through the layers above the bottom
     for (int l = 0; l + 1 < L; ++l) {
       const int wl = a.width[l];
@@ -375,8 +536,7 @@ __global__ void __launch_bounds__(256) k_search(const SearchArgs a) {
             record_error(a.ctr, DERR_BAD_ID, key_id(ck));
             v = -1;
           }
-          uint64_t k = KEY_EMPTY;
-          if (v >= 0) k = make_key(dist_q(v), v);
+          const uint64_t k = eval(v, v >= 0, true, key_dist(best));
           ev += __popc(__ballot_sync(FULL, v >= 0));
           const uint64_t m = warp_min64(k);
           best = m < best ? m : best;
@@ -394,20 +554,22 @@ __global__ void __launch_bounds__(256) k_search(const SearchArgs a) {
       FA[0] = 0;
     }
     __syncwarp();
-    int cnt = 1;
+    int cnt = 1, hint = 0;  // entries before `hint` are expanded
     bool crowded = false;
     const int wb = a.width[L - 1];
     const int32_t* gb = a.g[L - 1];
     for (;;) {
       int e = -1;
-      for (int c0 = 0; c0 < cnt; c0 += 32) {
-        const unsigned b = __ballot_sync(FULL, c0 + lane < cnt && FA[c0 + lane] == 0);
+      for (int c0 = hint & ~31; c0 < cnt; c0 += 32) {
+        const int i = c0 + lane;
+        const unsigned b = __ballot_sync(FULL, i >= hint && i < cnt && FA[i] == 0);
         if (b) {
           e = c0 + __ffs(b) - 1;
           break;
         }
       }
       if (e < 0) break;
+      hint = e + 1;
       const int32_t ue = key_id(LA[e]);
       __syncwarp();
       if (lane == 0) FA[e] = 1;
@@ -425,46 +587,59 @@ __global__ void __launch_bounds__(256) k_search(const SearchArgs a) {
           fresh = r != 0;
           crowded = crowded || r == 2;
         }
-        uint64_t k = KEY_EMPTY;
-        if (fresh) k = make_key(dist_q(v), v);
+        const bool full = cnt == a.ef;
+        const uint64_t thr = full ? LA[cnt - 1] : KEY_EMPTY;
+        uint64_t k = eval(v, fresh, full, full ? key_dist(thr) : 0.0f);
         ev += __popc(__ballot_sync(FULL, fresh));
-        const uint64_t thr = cnt == a.ef ? LA[cnt - 1] : KEY_EMPTY;
         if (k >= thr) k = KEY_EMPTY;
-        if (!__any_sync(FULL, k != KEY_EMPTY)) continue;
-        k = warp_sort32(k);
+        const unsigned cm = __ballot_sync(FULL, k != KEY_EMPTY);
+        if (cm == 0u) continue;
+        if (cm & (cm - 1u)) {
+          k = warp_sort32(k);  // two or more: ascending in lanes 0..
+        } else {
+          const uint64_t one = __shfl_sync(FULL, k, __ffs(cm) - 1);
+          k = lane == 0 ? one : KEY_EMPTY;
+        }
         const uint64_t pk = __shfl_up_sync(FULL, k, 1);
         bool keep = k != KEY_EMPTY && !(lane > 0 && pk == k);
+        int below = 0;  // entries of the current list below this candidate
         if (keep) {
-          const int pos = count_below(LA, cnt, k);
-          keep = !(pos < cnt && LA[pos] == k);
+          below = count_below(LA, cnt, k);
+          keep = !(below < cnt && LA[below] == k);
         }
         const unsigned kb = __ballot_sync(FULL, keep);
-        if (keep) cand[__popc(kb & lt)] = k;
-        const int nc = __popc(kb);
+        if (kb == 0u) continue;
+        const int nc = __popc(kb), rank = __popc(kb & lt);
+        if (keep) cand[rank] = k;
+        const int pmin = __shfl_sync(FULL, below, __ffs(kb) - 1);
         __syncwarp();
-        for (int i = lane; i < cnt; i += 32) {
-          const uint64_t x = LA[i];
-          const int pos = i + count_below(cand, nc, x);
-          if (pos < a.ef) {
-            LB[pos] = x;
-            FB[pos] = FA[i];
+        // In place: entries from pmin on move right past the candidates below
+        // them (chunks from the end; targets strictly increase, so no write
+        // lands on an entry not yet read); those pushed beyond ef drop out.
+        for (int c0 = (cnt - 1) & ~31; c0 >= (pmin & ~31); c0 -= 32) {
+          const int i = c0 + lane;
+          const bool mv = i >= pmin && i < cnt;
+          uint64_t x = 0;
+          uint8_t f = 0;
+          int np = 0;
+          if (mv) {
+            x = LA[i];
+            f = FA[i];
+            np = i + count_below(cand, nc, x);
           }
+          __syncwarp();
+          if (mv && np < a.ef) {
+            LA[np] = x;
+            FA[np] = f;
+          }
+          __syncwarp();
         }
-        if (lane < nc) {
-          const uint64_t x = cand[lane];
-          const int pos = lane + count_below(LA, cnt, x);
-          if (pos < a.ef) {
-            LB[pos] = x;
-            FB[pos] = 0;
-          }
+        if (keep && rank + below < a.ef) {
+          LA[rank + below] = k;
+          FA[rank + below] = 0;
         }
         cnt = min(a.ef, cnt + nc);
-        uint64_t* tl = LA;
-        LA = LB;
-        LB = tl;
-        uint8_t* tf = FA;
-        FA = FB;
-        FB = tf;
+        hint = min(hint, pmin);
         __syncwarp();
       }
     }
@@ -482,12 +657,6 @@ __global__ void __launch_bounds__(256) k_search(const SearchArgs a) {
     if (lane == 0 && a.out_evals) a.out_evals[q] = ev;
     evals_all += ev;
     overflow += __any_sync(FULL, crowded) ? 1ull : 0ull;
-    // the two rank buffers swap an odd or even number of times per query:
-    // start the next query from the region layout again
-    LA = reinterpret_cast<uint64_t*>(base + search_qbytes(a.d));
-    LB = LA + a.ef;
-    FA = reinterpret_cast<uint8_t*>(LB + a.ef);
-    FB = FA + round16(a.ef);
     __syncwarp();
   }
   if (lane == 0) {
@@ -572,6 +741,7 @@ cudaError_t plan_search(SearchArgs* a, size_t* smem, int* grid) {
   while (hbits < 14 && (1 << hbits) < 32 * a->ef) ++hbits;
   a->hbits = hbits;
   a->warp_bytes = search_warp_bytes(a->d, a->ef, hbits);
+  if (a->warp_bytes % 16 != 0) return cudaErrorInvalidValue;  // every region 16-byte aligned
   const int cap = 227 * 1024;
   if (a->warp_bytes > cap) return cudaErrorInvalidValue;
   int warps = 4;
@@ -586,6 +756,13 @@ cudaError_t plan_search(SearchArgs* a, size_t* smem, int* grid) {
   const int64_t want = (a->nq + warps - 1) / warps;
   *grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * per_sm));
   return cudaSuccess;
+}
+
+cudaError_t launch_row_aux(const float* X, int64_t n, int d, float* aux, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const int grid = (int)std::min<int64_t>((n + AUX_WARPS - 1) / AUX_WARPS, 152 * 8);
+  k_row_aux<<<grid, AUX_WARPS * 32, 0, st>>>(X, n, d, reinterpret_cast<float2*>(aux));
+  return cudaGetLastError();
 }
 
 cudaError_t launch_search(const SearchArgs& a, int metric, size_t smem, int grid,

@@ -576,7 +576,7 @@ struct SearchArgs {
   int64_t n;
   int d;
   int vec4;
-  const float* norms;  // canonical norms [n] (COS), else nullptr
+  const float* aux;  // [n][2] per row: max |x| of an integer row (else -1), canonical norm
   int n_layers;
   int64_t rows[SEARCH_MAX_LAYERS];
   int width[SEARCH_MAX_LAYERS];
@@ -596,5 +596,8 @@ struct SearchArgs {
 // Fills hbits / warps / warp_bytes and the launch shape.
 cudaError_t plan_search(SearchArgs* a, size_t* smem, int* grid);
 cudaError_t launch_search(const SearchArgs& a, int metric, size_t smem, int grid, cudaStream_t st);
+// Per-row search data aux [n][2]: {max |x| when the row is all integers of
+// magnitude <= 2^24, else -1; canonical norm}.
+cudaError_t launch_row_aux(const float* X, int64_t n, int d, float* aux, cudaStream_t st);
 
 }  // namespace knnm

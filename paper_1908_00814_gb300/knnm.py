@@ -140,8 +140,9 @@ SIGNATURES = {
     "knnm_gather_rows": (_I, [_P, _P, _I64, _I, _P, _I64, _P]),
     "knnm_diversify": (_I, [_P, _P, _I64, _I, _P, _I, _I, _I, _P, _P, _P,
                             ctypes.POINTER(GdStats)]),
-    "knnm_search": (_I, [_P, _P, _I64, _I, _I, _I, _P, _P, _P, _P, _I64, _I, _I, _U64, _P, _P,
-                         _P, ctypes.POINTER(SearchStats)]),
+    "knnm_search_prepare": (_I, [_P, _P, _I64, _I, _P]),
+    "knnm_search": (_I, [_P, _P, _I64, _I, _P, _I, _I, _P, _P, _P, _P, _I64, _I, _I, _U64, _P,
+                         _P, _P, ctypes.POINTER(SearchStats)]),
     "knnm_server_create": (_I, [_I, _P, _I64, _P, _I, ctypes.POINTER(Params),
                                 ctypes.POINTER(ServerConfig), ctypes.POINTER(ctypes.c_void_p)]),
     "knnm_server_submit": (_I, [_P, _P, _I64, _U64]),
@@ -349,10 +350,20 @@ class Context:
                                          _ptr(ids), _ptr(dists), _ptr(deg), ctypes.byref(st)))
         return ids, dists, deg, st.as_dict()
 
-    def search(self, S, layers, Q, ef, k_out, metric="l2", seed=0):
+    def search_prepare(self, S):
+        """Per-row data for knnm_search over S ([n][2] floats)."""
+        import torch
+        n, d = S.shape
+        aux = torch.empty((n, 2), dtype=torch.float32, device=S.device)
+        self._sync_stream()
+        self._check(lib().knnm_search_prepare(self.h, _ptr(S), n, d, _ptr(aux)))
+        return aux
+
+    def search(self, S, layers, Q, ef, k_out, metric="l2", seed=0, row_aux=None):
         """Top-down search; `layers` lists the layer graphs from the top down (layer
-        l covers the first len(layers[l]) rows of S).  Returns (ids, dists, evals,
-        stats) with k_out entries per query."""
+        l covers the first len(layers[l]) rows of S); row_aux from search_prepare
+        (None: computed inside the call).  Returns (ids, dists, evals, stats) with
+        k_out entries per query."""
         import torch
         n, d = S.shape
         nq = Q.shape[0]
@@ -368,7 +379,8 @@ class Context:
         evals = torch.empty(nq, dtype=torch.int32, device=S.device)
         st = SearchStats()
         self._sync_stream()
-        self._check(lib().knnm_search(self.h, _ptr(S), n, d, m, L, ctypes.cast(rows, _P),
+        self._check(lib().knnm_search(self.h, _ptr(S), n, d, _ptr(row_aux), m, L,
+                                      ctypes.cast(rows, _P),
                                       ctypes.cast(width, _P), ctypes.cast(ptrs, _P), _ptr(Q), nq,
                                       ef, k_out, seed, _ptr(ids), _ptr(dists), _ptr(evals),
                                       ctypes.byref(st)))

@@ -156,18 +156,40 @@ def test_hierarchical_search_matches_oracle(torch, km, ctx, orc, hierarchy, ef, 
 
 
 @pytest.mark.parametrize("metric", ["l2", "l1", "ip", "cos"])
-def test_flat_search_matches_oracle(torch, km, ctx, orc, metric):
+@pytest.mark.parametrize("kind", ["float", "int"])
+def test_flat_search_matches_oracle(torch, km, ctx, orc, metric, kind):
+    """Float rows take the estimate-then-canonical route, small-integer rows the
+    exact estimate; both must give the oracle's bits."""
     mcode = km.METRICS[metric]
-    X = datagen.gaussian_mixture(5000, 20, n_comp=10, seed=8, normalize=metric == "cos")
+    if kind == "int":
+        X = datagen.sift_like(4000, 32, n_centres=4, seed=8)
+        Q = np.concatenate([X[:40], datagen.sift_like(160, 32, n_centres=4, seed=9)])
+        Q[-1, 0] += 0.5   # a non-integer query: its pairs take the bounded route
+    else:
+        X = datagen.gaussian_mixture(5000, 20, n_comp=10, seed=8, normalize=metric == "cos")
+        Q = np.concatenate([X[:50], datagen.gaussian_mixture(150, 20, n_comp=10, seed=9,
+                                                            normalize=metric == "cos")])
     G, _ = orc.bruteforce_knn(X, 10, metric=mcode)
-    Q = np.concatenate([X[:50], datagen.gaussian_mixture(150, 20, n_comp=10, seed=9,
-                                                        normalize=metric == "cos")])
     want = orc.search(X, [G], Q, 64, 12, metric=mcode, seed=2)
-    got = ctx.search(cuda(torch, X), [cuda(torch, G)], cuda(torch, Q), 64, 12, metric=metric,
-                     seed=2)
-    assert same_bits(got[0].cpu().numpy(), want[0])
-    assert same_bits(got[1].cpu().numpy(), want[1])
-    assert np.array_equal(got[2].cpu().numpy().astype(np.uint64), want[2])
+    Xd = cuda(torch, X)
+    for aux in (None, ctx.search_prepare(Xd)):
+        got = ctx.search(Xd, [cuda(torch, G)], cuda(torch, Q), 64, 12, metric=metric, seed=2,
+                         row_aux=aux)
+        assert same_bits(got[0].cpu().numpy(), want[0])
+        assert same_bits(got[1].cpu().numpy(), want[1])
+        assert np.array_equal(got[2].cpu().numpy().astype(np.uint64), want[2])
+
+
+def test_search_prepare(torch, km, ctx):
+    X = datagen.gaussian_mixture(300, 12, seed=3)
+    X[:100] = np.round(X[:100] * 10)
+    X[100:110] = np.round(X[100:110]) * 1e7    # integers beyond 2^24 count as inexact
+    aux = ctx.search_prepare(cuda(torch, X)).cpu().numpy()
+    for i in range(300):
+        integral = bool((X[i] == np.round(X[i])).all()) and np.abs(X[i]).max() <= 2 ** 24
+        assert aux[i, 0] == (np.abs(X[i]).max() if integral else -1.0)
+    ref = np.sqrt((X.astype(np.float64) ** 2).sum(1))
+    assert np.allclose(aux[:, 1], ref, rtol=1e-5)
 
 
 def test_crowded_visited_table_keeps_the_result(torch, km, ctx, orc):
