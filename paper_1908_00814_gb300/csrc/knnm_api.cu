@@ -1492,6 +1492,9 @@ extern "C" int knnm_diversify(knnm_ctx* ctx, const float* S, int64_t n, int d, c
   a.out_dists = out_dists;
   a.out_deg = out_degree;
   a.ctr = ctr;
+  if (!plan_diversify(&a))
+    return fail(ctx, KNNM_ERR_INVALID, "no diversification layout for d=%d max_degree=%d", d,
+                max_degree);
   KNNM_CUDA(cudaMemsetAsync(ctr, 0, sizeof(GdCounters), st));
   KNNM_CUDA(cudaMemsetAsync(&ctr->err_row, 0xFF, 8, st));
   KNNM_CUDA(cudaEventRecord(ctx->ev[0], st));

@@ -64,6 +64,62 @@ __device__ __forceinline__ float dist_query(const float* qs, const float* __rest
   return canon_finish<METRIC>(acc, nq, nr);
 }
 
+// Canonical distance of two rows staged in shared memory (16-byte aligned,
+// d % 4 == 0), a first.
+template <int METRIC>
+__device__ __forceinline__ float dist_staged(const float* ra, const float* rb, int d, float na,
+                                             float nb) {
+  float acc = 0.0f;
+  const float4* a4 = reinterpret_cast<const float4*>(ra);
+  const float4* b4 = reinterpret_cast<const float4*>(rb);
+#pragma unroll 4
+  for (int t = 0; t < (d >> 2); ++t) {
+    const float4 x = a4[t], y = b4[t];
+    acc = Canon<METRIC>::step(acc, x.x, y.x);
+    acc = Canon<METRIC>::step(acc, x.y, y.y);
+    acc = Canon<METRIC>::step(acc, x.z, y.z);
+    acc = Canon<METRIC>::step(acc, x.w, y.w);
+  }
+  return canon_finish<METRIC>(acc, na, nb);
+}
+
+// Same with the second row in global memory (16-byte aligned).
+template <int METRIC>
+__device__ __forceinline__ float dist_staged_global(const float* ra, const float* __restrict__ rb,
+                                                    int d, float na, float nb) {
+  float acc = 0.0f;
+  const float4* a4 = reinterpret_cast<const float4*>(ra);
+  const float4* b4 = reinterpret_cast<const float4*>(rb);
+#pragma unroll 4
+  for (int t = 0; t < (d >> 2); ++t) {
+    const float4 x = a4[t], y = __ldg(b4 + t);
+    acc = Canon<METRIC>::step(acc, x.x, y.x);
+    acc = Canon<METRIC>::step(acc, x.y, y.y);
+    acc = Canon<METRIC>::step(acc, x.z, y.z);
+    acc = Canon<METRIC>::step(acc, x.w, y.w);
+  }
+  return canon_finish<METRIC>(acc, na, nb);
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// The warp copies rows ids[0..count) of X into dst (stride floats apart);
+// every lane takes 16-byte pieces; completion is awaited by the caller.
+__device__ __forceinline__ void stage_rows(float* dst, int stride, const float* X, int d,
+                                           const int32_t* ids, int count, int lane) {
+  const int n4 = d >> 2;
+  for (int c = lane; c < count * n4; c += 32) {
+    const int r = c / n4, t = c - r * n4;
+    cp_async16(dst + (size_t)r * stride + 4 * t, X + (size_t)ids[r] * d + 4 * t);
+  }
+}
+
 // Pair p of the strict lower triangle, row-major: p = i (i - 1) / 2 + c, c < i.
 __device__ __forceinline__ void tri_decode(int p, int& i, int& c) {
   int r = (int)((1.0f + sqrtf(8.0f * (float)p + 1.0f)) * 0.5f);
@@ -104,7 +160,15 @@ __device__ __forceinline__ void record_error(GdCounters* c, unsigned bit, int64_
   atomicMin(&c->err_row, (unsigned long long)row);
 }
 
-__host__ __device__ __forceinline__ int gd_warp_bytes(int M) { return 8 * M + 8 * 32 + 4 * 32; }
+// Reverse pass, per warp: the batch's rows (32 x stride floats when staging),
+// kept keys [M], forward keys [32], occlusion masks [32], batch ids [32].
+__host__ __device__ __forceinline__ int gd_rows_bytes(int stage, int stride) {
+  return stage ? 32 * stride * 4 : 0;
+}
+__host__ __device__ __forceinline__ int gd_kept_bytes(int M) { return (8 * M + 15) & ~15; }
+__host__ __device__ __forceinline__ int gd_warp_bytes(int M, int stage, int stride) {
+  return gd_rows_bytes(stage, stride) + gd_kept_bytes(M) + 8 * 32 + 4 * 32 + 4 * 32;
+}
 
 // ---------------------------------------------------------------------------
 // Diversification
@@ -131,8 +195,12 @@ __global__ void __launch_bounds__(256) k_gd_count(const GdArgs a) {
 template <int METRIC>
 __global__ void __launch_bounds__(GD_WARPS * 32) k_gd_forward(const GdArgs a) {
   __shared__ uint32_t occl_s[GD_WARPS][32];
+  __shared__ int32_t ids_s[GD_WARPS][32];
+  extern __shared__ __align__(16) unsigned char fwd_sm[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint32_t* occl = occl_s[w];
+  int32_t* sid = ids_s[w];
+  float* rows = reinterpret_cast<float*>(fwd_sm) + (size_t)w * a.K * a.stride;
   const unsigned lt = (1u << lane) - 1u;
   unsigned long long evals = 0;
   for (int64_t u = (int64_t)blockIdx.x * GD_WARPS + w; u < a.n;
@@ -154,7 +222,13 @@ __global__ void __launch_bounds__(GD_WARPS * 32) k_gd_forward(const GdArgs a) {
       a.rev[a.rev_off[id] + (unsigned long long)slot] = make_key(dl, (int32_t)u);
     }
     occl[lane] = 0u;
+    sid[lane] = id;
     __syncwarp();
+    if (a.stage) {  // the listed rows, in list order, into shared memory
+      stage_rows(rows, a.stride, a.X, a.d, sid, nv, lane);
+      cp_async_wait_all();
+      __syncwarp();
+    }
     const int P = nv * (nv - 1) / 2;
     for (int base = 0; base < P; base += 32) {
       const int p = base + lane;
@@ -162,8 +236,18 @@ __global__ void __launch_bounds__(GD_WARPS * 32) k_gd_forward(const GdArgs a) {
       if (p < P) tri_decode(p, i, c);
       const int32_t si = __shfl_sync(FULL, id, i), sc = __shfl_sync(FULL, id, c);
       const float di = __shfl_sync(FULL, dl, i);
-      if (p < P && dist_rows<METRIC>(a.X, a.d, a.vec4, a.norms, si, sc) < di)
-        atomicOr(&occl[i], 1u << c);
+      if (p < P) {
+        float dic;
+        if (a.stage) {
+          const float ni = METRIC == COS ? __ldg(a.norms + si) : 0.0f;
+          const float nc = METRIC == COS ? __ldg(a.norms + sc) : 0.0f;
+          dic = dist_staged<METRIC>(rows + (size_t)i * a.stride, rows + (size_t)c * a.stride, a.d,
+                                    ni, nc);
+        } else {
+          dic = dist_rows<METRIC>(a.X, a.d, a.vec4, a.norms, si, sc);
+        }
+        if (dic < di) atomicOr(&occl[i], 1u << c);
+      }
     }
     evals += (unsigned long long)P;
     __syncwarp();
@@ -185,9 +269,13 @@ __global__ void __launch_bounds__(GD_WARPS * 32) k_gd_reverse(const GdArgs a) {
   extern __shared__ __align__(16) unsigned char gd_sm[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int M = a.M;
-  uint64_t* kept = reinterpret_cast<uint64_t*>(gd_sm + (size_t)w * gd_warp_bytes(M));
-  uint64_t* fk = kept + M;
+  unsigned char* wbase = gd_sm + (size_t)w * gd_warp_bytes(M, a.stage, a.stride);
+  float* rows = reinterpret_cast<float*>(wbase);  // the batch's rows when staging
+  uint64_t* kept = reinterpret_cast<uint64_t*>(wbase + gd_rows_bytes(a.stage, a.stride));
+  uint64_t* fk = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(kept) +
+                                             gd_kept_bytes(M));
   uint32_t* occl = reinterpret_cast<uint32_t*>(fk + 32);
+  int32_t* sid = reinterpret_cast<int32_t*>(occl + 32);
   const unsigned lt = (1u << lane) - 1u;
   unsigned long long evals = 0, edges = 0, full = 0, max_in = 0;
   for (int64_t u = (int64_t)blockIdx.x * GD_WARPS + w; u < a.n;
@@ -212,10 +300,27 @@ __global__ void __launch_bounds__(GD_WARPS * 32) k_gd_reverse(const GdArgs a) {
       if (nb == 0) break;
       const int32_t s = key_id(best);
       const float ds = key_dist(best);
+      if (a.stage) {
+        sid[lane] = s;
+        __syncwarp();
+        stage_rows(rows, a.stride, a.X, a.d, sid, nb, lane);
+        cp_async_wait_all();
+        __syncwarp();
+      }
       bool surv = lane < nb;
       for (int j = 0; surv && j < nk; ++j) {
         ++evals;
-        if (dist_rows<METRIC>(a.X, a.d, a.vec4, a.norms, s, key_id(kept[j])) < ds) surv = false;
+        const int32_t kj = key_id(kept[j]);
+        float dk;
+        if (a.stage) {
+          const float ns = METRIC == COS ? __ldg(a.norms + s) : 0.0f;
+          const float nk2 = METRIC == COS ? __ldg(a.norms + kj) : 0.0f;
+          dk = dist_staged_global<METRIC>(rows + (size_t)lane * a.stride, a.X + (size_t)kj * a.d,
+                                          a.d, ns, nk2);
+        } else {
+          dk = dist_rows<METRIC>(a.X, a.d, a.vec4, a.norms, s, kj);
+        }
+        if (dk < ds) surv = false;
       }
       const unsigned sm = __ballot_sync(FULL, surv);
       occl[lane] = 0u;
@@ -229,8 +334,16 @@ __global__ void __launch_bounds__(GD_WARPS * 32) k_gd_reverse(const GdArgs a) {
         const float di = __shfl_sync(FULL, ds, i);
         if (p < P && ((sm >> i) & 1u) && ((sm >> c) & 1u)) {
           ++evals;
-          if (dist_rows<METRIC>(a.X, a.d, a.vec4, a.norms, si, sc) < di)
-            atomicOr(&occl[i], 1u << c);
+          float dic;
+          if (a.stage) {
+            const float ni = METRIC == COS ? __ldg(a.norms + si) : 0.0f;
+            const float nc = METRIC == COS ? __ldg(a.norms + sc) : 0.0f;
+            dic = dist_staged<METRIC>(rows + (size_t)i * a.stride, rows + (size_t)c * a.stride,
+                                      a.d, ni, nc);
+          } else {
+            dic = dist_rows<METRIC>(a.X, a.d, a.vec4, a.norms, si, sc);
+          }
+          if (dic < di) atomicOr(&occl[i], 1u << c);
         }
       }
       __syncwarp();
@@ -702,7 +815,21 @@ cudaError_t launch_gather_checked(const float* X, int64_t n_src, const int32_t* 
   return cudaGetLastError();
 }
 
-size_t gd_reverse_smem(int M) { return (size_t)GD_WARPS * gd_warp_bytes(M); }
+size_t gd_reverse_smem(int M, int stage, int stride) {
+  return (size_t)GD_WARPS * gd_warp_bytes(M, stage, stride);
+}
+
+bool plan_diversify(GdArgs* a) {
+  // stage rows in shared memory when 32 rows per warp fit a 227 KB block
+  a->stride = a->d + 4;
+  a->stage = (a->vec4 && (size_t)GD_WARPS * 32 * a->stride * 4 + gd_reverse_smem(a->M, 0, 0) <=
+                             227 * 1024)
+                 ? 1
+                 : 0;
+  // every warp's region must start 16-byte aligned (staged rows, 64-bit keys)
+  return gd_warp_bytes(a->M, a->stage, a->stride) % 16 == 0 &&
+         (!a->stage || ((size_t)a->K * a->stride * 4) % 16 == 0);
+}
 
 cudaError_t launch_diversify(const GdArgs& a, int metric, cudaStream_t st) {
   cudaError_t e;
@@ -716,14 +843,16 @@ cudaError_t launch_diversify(const GdArgs& a, int metric, cudaStream_t st) {
       cudaSuccess)
     return e;
   const int grid = gd_grid(a.n);
-  const size_t smem = gd_reverse_smem(a.M);
+  const size_t smem = gd_reverse_smem(a.M, a.stage, a.stride);
+  const size_t fsmem = a.stage ? (size_t)GD_WARPS * a.K * a.stride * 4 : 0;
   switch (metric) {
-#define KNNM_GD_CASE(M_)                                                     \
-  case M_:                                                                   \
-    k_gd_forward<M_><<<grid, GD_WARPS * 32, 0, st>>>(a);                     \
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;                   \
-    if (smem > 48 * 1024 && (e = set_smem(k_gd_reverse<M_>, smem)) != cudaSuccess) return e; \
-    k_gd_reverse<M_><<<grid, GD_WARPS * 32, smem, st>>>(a);                  \
+#define KNNM_GD_CASE(M_)                                                             \
+  case M_:                                                                           \
+    if ((e = set_smem(k_gd_forward<M_>, fsmem)) != cudaSuccess) return e;            \
+    k_gd_forward<M_><<<grid, GD_WARPS * 32, fsmem, st>>>(a);                         \
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;                           \
+    if ((e = set_smem(k_gd_reverse<M_>, smem)) != cudaSuccess) return e;             \
+    k_gd_reverse<M_><<<grid, GD_WARPS * 32, smem, st>>>(a);                          \
     break;
     KNNM_GD_CASE(L2)
     KNNM_GD_CASE(IP)

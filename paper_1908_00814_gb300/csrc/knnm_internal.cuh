@@ -552,6 +552,8 @@ struct GdArgs {
   const int32_t* G;    // [n][K] input graph
   int K;
   int M;               // output degree cap
+  int stage;           // rows staged in shared memory (set by plan_diversify)
+  int stride;          // floats between staged rows
   int32_t* indeg;      // [n] in-degrees (zeroed by the launcher)
   int32_t* rev_fill;   // [n] reverse-bucket cursors (zeroed by the launcher)
   unsigned long long* rev_off;  // [n+1]
@@ -565,10 +567,12 @@ struct GdArgs {
   int32_t* out_deg;    // [n]
   GdCounters* ctr;
 };
+// Fills the staging fields of a (vec4, d, K, M set); false when the layout
+// would leave a shared-memory region misaligned.
+bool plan_diversify(GdArgs* a);
 cudaError_t launch_diversify(const GdArgs& a, int metric, cudaStream_t st);
 cudaError_t launch_gather_checked(const float* X, int64_t n_src, const int32_t* perm, int64_t n,
                                   int d, float* out, GdCounters* ctr, cudaStream_t st);
-size_t gd_reverse_smem(int M);
 
 constexpr int SEARCH_MAX_LAYERS = 32;
 struct SearchArgs {
