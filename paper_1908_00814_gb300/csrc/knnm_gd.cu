@@ -24,7 +24,8 @@
 namespace knnm {
 namespace {
 
-constexpr int GD_WARPS = 8;
+constexpr int GD_WARPS = 8;   // forward pass and helpers
+constexpr int REV_WARPS = 4;  // reverse pass (its staged batch takes ~17 KB per warp at d = 128)
 constexpr int VISIT_PROBES = 32;
 
 __device__ __forceinline__ float f_inf() { return __int_as_float(0x7f800000); }
@@ -114,9 +115,10 @@ __device__ __forceinline__ void cp_async_wait_all() {
 __device__ __forceinline__ void stage_rows(float* dst, int stride, const float* X, int d,
                                            const int32_t* ids, int count, int lane) {
   const int n4 = d >> 2;
-  for (int c = lane; c < count * n4; c += 32) {
-    const int r = c / n4, t = c - r * n4;
-    cp_async16(dst + (size_t)r * stride + 4 * t, X + (size_t)ids[r] * d + 4 * t);
+  for (int r = 0; r < count; ++r) {
+    const float* src = X + (size_t)ids[r] * d;
+    float* to = dst + (size_t)r * stride;
+    for (int t = lane; t < n4; t += 32) cp_async16(to + 4 * t, src + 4 * t);
   }
 }
 
@@ -127,6 +129,23 @@ __device__ __forceinline__ void tri_decode(int p, int& i, int& c) {
   while ((r + 1) * r / 2 <= p) ++r;
   i = r;
   c = p - r * (r - 1) / 2;
+}
+
+// occl[i] |= bit for every lane, where the lanes' rows i are non-decreasing
+// (consecutive pairs of the triangle): the bits of a run of equal i are OR-ed
+// by shuffles and its first lane alone writes, instead of one shared-memory
+// atomic per lane on the same word.
+__device__ __forceinline__ void or_by_row(uint32_t* occl, uint32_t bit, int i, bool valid,
+                                          int lane) {
+  if (!valid) i = -1 - lane;  // a run of its own
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t b2 = __shfl_down_sync(FULL, bit, o);
+    const int i2 = __shfl_down_sync(FULL, i, o);
+    if (lane + o < 32 && i2 == i) bit |= b2;
+  }
+  const int up = __shfl_up_sync(FULL, i, 1);
+  if (valid && bit != 0u && (lane == 0 || up != i)) atomicOr(&occl[i], bit);
 }
 
 // Number of entries of the ascending array a[0..n) below x.
@@ -195,21 +214,37 @@ __global__ void __launch_bounds__(256) k_gd_count(const GdArgs a) {
 template <int METRIC>
 __global__ void __launch_bounds__(GD_WARPS * 32) k_gd_forward(const GdArgs a) {
   __shared__ uint32_t occl_s[GD_WARPS][32];
-  __shared__ int32_t ids_s[GD_WARPS][32];
+  __shared__ int32_t ids_s[GD_WARPS][33];
   extern __shared__ __align__(16) unsigned char fwd_sm[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint32_t* occl = occl_s[w];
-  int32_t* sid = ids_s[w];
-  float* rows = reinterpret_cast<float*>(fwd_sm) + (size_t)w * a.K * a.stride;
+  int32_t* sid = ids_s[w];  // staged rows: slot 0 = the row itself, slot 1 + j = its entry j
+  float* rows = reinterpret_cast<float*>(fwd_sm) + (size_t)w * (a.K + 1) * a.stride;
   const unsigned lt = (1u << lane) - 1u;
   unsigned long long evals = 0;
   for (int64_t u = (int64_t)blockIdx.x * GD_WARPS + w; u < a.n;
        u += (int64_t)gridDim.x * GD_WARPS) {
-    uint64_t key = KEY_EMPTY;
+    int32_t v = -1;
     if (lane < a.K) {
-      const int32_t v = a.G[u * a.K + lane];
-      if (v >= 0 && v < a.n && v != u)
-        key = make_key(dist_rows<METRIC>(a.X, a.d, a.vec4, a.norms, (int32_t)u, v), v);
+      v = a.G[u * a.K + lane];
+      if (v < 0 || v >= a.n || v == u) v = -1;  // reported by the count pass
+    }
+    uint64_t key = KEY_EMPTY;
+    if (a.stage) {  // the row and its entries, in list order, into shared memory
+      if (lane == 0) sid[0] = (int32_t)u;
+      if (lane < a.K) sid[1 + lane] = v >= 0 ? v : (int32_t)u;
+      __syncwarp();
+      stage_rows(rows, a.stride, a.X, a.d, sid, a.K + 1, lane);
+      cp_async_wait_all();
+      __syncwarp();
+      if (v >= 0) {
+        const float nu = METRIC == COS ? __ldg(a.norms + u) : 0.0f;
+        const float nv_ = METRIC == COS ? __ldg(a.norms + v) : 0.0f;
+        key = make_key(dist_staged<METRIC>(rows, rows + (size_t)(1 + lane) * a.stride, a.d, nu,
+                                           nv_), v);
+      }
+    } else if (v >= 0) {
+      key = make_key(dist_rows<METRIC>(a.X, a.d, a.vec4, a.norms, (int32_t)u, v), v);
     }
     key = warp_sort32(key);
     const int nv = __popc(__ballot_sync(FULL, key != KEY_EMPTY));
@@ -221,33 +256,37 @@ __global__ void __launch_bounds__(GD_WARPS * 32) k_gd_forward(const GdArgs a) {
       const int slot = atomicAdd(&a.rev_fill[id], 1);
       a.rev[a.rev_off[id] + (unsigned long long)slot] = make_key(dl, (int32_t)u);
     }
+    int my_slot = 0;  // staged slot of this lane's (sorted) entry
+    if (a.stage && key != KEY_EMPTY)
+      for (int j = 0; j < a.K; ++j)
+        if (sid[1 + j] == id) {
+          my_slot = 1 + j;
+          break;
+        }
     occl[lane] = 0u;
-    sid[lane] = id;
     __syncwarp();
-    if (a.stage) {  // the listed rows, in list order, into shared memory
-      stage_rows(rows, a.stride, a.X, a.d, sid, nv, lane);
-      cp_async_wait_all();
-      __syncwarp();
-    }
     const int P = nv * (nv - 1) / 2;
     for (int base = 0; base < P; base += 32) {
       const int p = base + lane;
       int i = 1, c = 0;
       if (p < P) tri_decode(p, i, c);
       const int32_t si = __shfl_sync(FULL, id, i), sc = __shfl_sync(FULL, id, c);
+      const int ti = __shfl_sync(FULL, my_slot, i), tc = __shfl_sync(FULL, my_slot, c);
       const float di = __shfl_sync(FULL, dl, i);
+      uint32_t bit = 0u;
       if (p < P) {
         float dic;
         if (a.stage) {
           const float ni = METRIC == COS ? __ldg(a.norms + si) : 0.0f;
           const float nc = METRIC == COS ? __ldg(a.norms + sc) : 0.0f;
-          dic = dist_staged<METRIC>(rows + (size_t)i * a.stride, rows + (size_t)c * a.stride, a.d,
-                                    ni, nc);
+          dic = dist_staged<METRIC>(rows + (size_t)ti * a.stride, rows + (size_t)tc * a.stride,
+                                    a.d, ni, nc);
         } else {
           dic = dist_rows<METRIC>(a.X, a.d, a.vec4, a.norms, si, sc);
         }
-        if (dic < di) atomicOr(&occl[i], 1u << c);
+        bit = dic < di ? 1u << c : 0u;
       }
+      or_by_row(occl, bit, i, p < P, lane);
     }
     evals += (unsigned long long)P;
     __syncwarp();
@@ -265,7 +304,7 @@ __global__ void __launch_bounds__(GD_WARPS * 32) k_gd_forward(const GdArgs a) {
 // then the union with the forward result, cut to M entries.  Once M reverse
 // entries are kept no later one can reach the first M of the union.
 template <int METRIC>
-__global__ void __launch_bounds__(GD_WARPS * 32) k_gd_reverse(const GdArgs a) {
+__global__ void __launch_bounds__(REV_WARPS * 32) k_gd_reverse(const GdArgs a) {
   extern __shared__ __align__(16) unsigned char gd_sm[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int M = a.M;
@@ -278,8 +317,8 @@ __global__ void __launch_bounds__(GD_WARPS * 32) k_gd_reverse(const GdArgs a) {
   int32_t* sid = reinterpret_cast<int32_t*>(occl + 32);
   const unsigned lt = (1u << lane) - 1u;
   unsigned long long evals = 0, edges = 0, full = 0, max_in = 0;
-  for (int64_t u = (int64_t)blockIdx.x * GD_WARPS + w; u < a.n;
-       u += (int64_t)gridDim.x * GD_WARPS) {
+  for (int64_t u = (int64_t)blockIdx.x * REV_WARPS + w; u < a.n;
+       u += (int64_t)gridDim.x * REV_WARPS) {
     const unsigned long long r0 = a.rev_off[u];
     const int m = (int)(a.rev_off[u + 1] - r0);
     max_in = max(max_in, (unsigned long long)m);
@@ -332,6 +371,7 @@ __global__ void __launch_bounds__(GD_WARPS * 32) k_gd_reverse(const GdArgs a) {
         if (p < P) tri_decode(p, i, c);
         const int32_t si = __shfl_sync(FULL, s, i), sc = __shfl_sync(FULL, s, c);
         const float di = __shfl_sync(FULL, ds, i);
+        uint32_t bit = 0u;
         if (p < P && ((sm >> i) & 1u) && ((sm >> c) & 1u)) {
           ++evals;
           float dic;
@@ -343,8 +383,9 @@ __global__ void __launch_bounds__(GD_WARPS * 32) k_gd_reverse(const GdArgs a) {
           } else {
             dic = dist_rows<METRIC>(a.X, a.d, a.vec4, a.norms, si, sc);
           }
-          if (dic < di) atomicOr(&occl[i], 1u << c);
+          bit = dic < di ? 1u << c : 0u;
         }
+        or_by_row(occl, bit, i, p < P, lane);
       }
       __syncwarp();
       uint32_t kb = 0u;
@@ -370,7 +411,10 @@ __global__ void __launch_bounds__(GD_WARPS * 32) k_gd_reverse(const GdArgs a) {
     for (int c0 = 0; c0 < nk; c0 += 32) {
       const uint64_t r = c0 + lane < nk ? kept[c0 + lane] : KEY_EMPTY;
       bool keep = r != KEY_EMPTY;
-      for (int j = 0; keep && j < fc; ++j) keep = fk[j] != r;
+      if (keep) {
+        const int pos = count_below(fk, fc, r);
+        keep = !(pos < fc && fk[pos] == r);
+      }
       const unsigned b = __ballot_sync(FULL, keep);
       if (keep) kept[nr + __popc(b & lt)] = r;
       nr += __popc(b);
@@ -816,19 +860,19 @@ cudaError_t launch_gather_checked(const float* X, int64_t n_src, const int32_t* 
 }
 
 size_t gd_reverse_smem(int M, int stage, int stride) {
-  return (size_t)GD_WARPS * gd_warp_bytes(M, stage, stride);
+  return (size_t)REV_WARPS * gd_warp_bytes(M, stage, stride);
 }
 
 bool plan_diversify(GdArgs* a) {
   // stage rows in shared memory when 32 rows per warp fit a 227 KB block
   a->stride = a->d + 4;
-  a->stage = (a->vec4 && (size_t)GD_WARPS * 32 * a->stride * 4 + gd_reverse_smem(a->M, 0, 0) <=
-                             227 * 1024)
+  a->stage = (a->vec4 && (size_t)GD_WARPS * 33 * a->stride * 4 <= 227 * 1024 &&
+               gd_reverse_smem(a->M, 1, a->stride) <= 227 * 1024)
                  ? 1
                  : 0;
   // every warp's region must start 16-byte aligned (staged rows, 64-bit keys)
   return gd_warp_bytes(a->M, a->stage, a->stride) % 16 == 0 &&
-         (!a->stage || ((size_t)a->K * a->stride * 4) % 16 == 0);
+         (!a->stage || ((size_t)(a->K + 1) * a->stride * 4) % 16 == 0);
 }
 
 cudaError_t launch_diversify(const GdArgs& a, int metric, cudaStream_t st) {
@@ -844,7 +888,8 @@ cudaError_t launch_diversify(const GdArgs& a, int metric, cudaStream_t st) {
     return e;
   const int grid = gd_grid(a.n);
   const size_t smem = gd_reverse_smem(a.M, a.stage, a.stride);
-  const size_t fsmem = a.stage ? (size_t)GD_WARPS * a.K * a.stride * 4 : 0;
+  const size_t fsmem = a.stage ? (size_t)GD_WARPS * (a.K + 1) * a.stride * 4 : 0;
+  const int rgrid = (int)std::min<int64_t>((a.n + REV_WARPS - 1) / REV_WARPS, 152 * 64);
   switch (metric) {
 #define KNNM_GD_CASE(M_)                                                             \
   case M_:                                                                           \
@@ -852,7 +897,7 @@ cudaError_t launch_diversify(const GdArgs& a, int metric, cudaStream_t st) {
     k_gd_forward<M_><<<grid, GD_WARPS * 32, fsmem, st>>>(a);                         \
     if ((e = cudaGetLastError()) != cudaSuccess) return e;                           \
     if ((e = set_smem(k_gd_reverse<M_>, smem)) != cudaSuccess) return e;             \
-    k_gd_reverse<M_><<<grid, GD_WARPS * 32, smem, st>>>(a);                          \
+    k_gd_reverse<M_><<<rgrid, REV_WARPS * 32, smem, st>>>(a);                        \
     break;
     KNNM_GD_CASE(L2)
     KNNM_GD_CASE(IP)
