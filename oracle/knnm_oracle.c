@@ -15,7 +15,8 @@
  *   - Distance (Alg. 1, l <- m(s_i, s_j)): one FP32 accumulator, dimensions in
  *     index order, fmaf per term.  L2 is the squared Euclidean distance (same
  *     ranking as l2), IP is 0 - dot, COS is 1 - dot/(|a||b|) (1 when a norm is
- *     zero), L1 adds |a_t - b_t| in order.
+ *     zero), L1 adds |a_t - b_t| in order, CHI2 adds (a_t - b_t)^2 / (a_t + b_t)
+ *     in order (a term with a_t + b_t = 0 adds 0; meant for non-negative rows).
  *   - List order: ascending (distance, id); ids unique per list, no self.
  *   - Random numbers: H(seed, t, stream, owner, member) = five chained
  *     SplitMix64 steps (Steele, Lea and Flood, OOPSLA 2014), each absorbing one
@@ -48,7 +49,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { ORC_L2 = 0, ORC_IP = 1, ORC_COS = 2, ORC_L1 = 3 };
+enum { ORC_L2 = 0, ORC_IP = 1, ORC_COS = 2, ORC_L1 = 3, ORC_CHI2 = 4 };
 enum { ORC_SYMMETRIC = 0, ORC_JOINT = 1 };
 enum { STREAM_FWD_NEW = 0, STREAM_REV_NEW = 1, STREAM_REV_OLD = 2, STREAM_INIT = 3 };
 enum { FLAG_OLD = 0, FLAG_NEW = 1 };
@@ -85,6 +86,15 @@ float orc_distance(int metric, const float* a, const float* b, int d) {
   }
   if (metric == ORC_L1) {
     for (int t = 0; t < d; ++t) acc = acc + fabsf(a[t] - b[t]);
+    return acc;
+  }
+  if (metric == ORC_CHI2) {  /* the chi-square distance of the NUSWide experiments (Sec. 5) */
+    for (int t = 0; t < d; ++t) {
+      const float x = a[t] - b[t];
+      const float s = a[t] + b[t];
+      const float q = x * x;
+      acc = acc + (s == 0.0f ? 0.0f : q / s);
+    }
     return acc;
   }
   return NAN;

@@ -148,3 +148,53 @@ def test_exact_knn_f64_helper_matches_direct(orc):
         ref = np.argsort(full, axis=1, kind="stable")[:, :5]
         assert np.array_equal(ids, ref)
         assert np.allclose(dd, np.take_along_axis(full, ref, 1))
+
+
+def test_chi_square_hand_values(orc):
+    """Chi-square distance (the NUSWide metric of Sec. 5): the sum over t of
+    (a_t - b_t)^2 / (a_t + b_t), a term with a_t + b_t = 0 counting 0."""
+    f = lambda a, b: float(orc.distance(orc.CHI2, np.array(a, np.float32), np.array(b, np.float32)))
+    assert f([1, 0, 3, 2], [3, 0, 1, 2]) == 2.0        # 4/4 + 0 + 4/4 + 0/4
+    assert f([1, 2], [0, 0]) == 3.0                    # 1/1 + 4/2
+    assert f([0, 0, 0], [0, 0, 0]) == 0.0
+    assert f([4, 0, 9], [4, 0, 9]) == 0.0
+    # pairs whose terms are exact: the sum is exact
+    rng = np.random.default_rng(1)
+    pairs = [(1, 3, 1.0), (2, 2, 0.0), (0, 0, 0.0), (1, 0, 1.0), (4, 0, 4.0), (3, 1, 1.0),
+             (0, 8, 8.0), (5, 3, 0.5)]
+    for _ in range(20):
+        pick = [pairs[i] for i in rng.integers(0, len(pairs), size=40)]
+        a = [p[0] for p in pick]
+        b = [p[1] for p in pick]
+        assert f(a, b) == sum(p[2] for p in pick)
+
+
+def test_chi_square_close_to_float64_and_symmetric(orc):
+    rng = np.random.default_rng(7)
+    u = 2.0 ** -24
+    for d in (5, 64, 500):
+        for _ in range(20):
+            a = rng.gamma(0.5, 3.0, size=d).astype(np.float32)   # sparse-ish histograms
+            b = rng.gamma(0.5, 3.0, size=d).astype(np.float32)
+            a[rng.random(d) < 0.3] = 0.0
+            b[rng.random(d) < 0.3] = 0.0
+            A, B = a.astype(np.float64), b.astype(np.float64)
+            S = A + B
+            terms = np.where(S == 0, 0.0, (A - B) ** 2 / np.where(S == 0, 1.0, S))
+            got = orc.distance(orc.CHI2, a, b)
+            assert abs(float(got) - terms.sum()) <= (d + 8) * u * terms.sum() * 1.01
+            assert got.tobytes() == orc.distance(orc.CHI2, b, a).tobytes()
+
+
+def test_chi_square_bruteforce_knn_matches_float64(orc):
+    rng = np.random.default_rng(9)
+    X = rng.poisson(1.5, size=(300, 24)).astype(np.float32)
+    ids, dists = orc.bruteforce_knn(X, 8, metric=orc.CHI2)
+    X64 = X.astype(np.float64)
+    for i in range(0, 300, 7):
+        S = X64[i] + X64
+        T = np.where(S == 0, 0.0, (X64[i] - X64) ** 2 / np.where(S == 0, 1.0, S)).sum(1)
+        T[i] = np.inf
+        want = np.sort(T)[:8]
+        assert np.allclose(dists[i], want, rtol=1e-5, atol=1e-6)
+        assert np.allclose(T[ids[i]], want, rtol=1e-5, atol=1e-6)
