@@ -24,7 +24,10 @@
  *     dimensions in index order, fused multiply-add per term.  KNNM_L2 is the
  *     squared Euclidean distance (same ranking as l2), KNNM_IP is 0 - a.b,
  *     KNNM_COS is 1 - a.b/(|a||b|) (1 when a norm is zero), KNNM_L1 is the sum of
- *     |a_t - b_t| in index order.  Inputs must be finite.
+ *     |a_t - b_t| in index order, KNNM_CHI2 the sum of (a_t - b_t)^2 / (a_t + b_t)
+ *     in index order (0 for a term with a_t + b_t = 0; the chi-square distance of
+ *     the paper's NUSWide experiments, meant for non-negative rows).  Inputs
+ *     must be finite.
  *   - knnm_merge_* and knnm_build accept host or device pointers for every
  *     array argument (the library asks the CUDA runtime which one each is).
  *     Host inputs are copied to the device and host outputs copied back inside
@@ -53,7 +56,7 @@ enum {
   KNNM_ERR_DEVICE = -6     /* a kernel reported an internal error */
 };
 
-typedef enum { KNNM_L2 = 0, KNNM_IP = 1, KNNM_COS = 2, KNNM_L1 = 3 } knnm_metric;
+typedef enum { KNNM_L2 = 0, KNNM_IP = 1, KNNM_COS = 2, KNNM_L1 = 3, KNNM_CHI2 = 4 } knnm_metric;
 
 /* KNNM_FP32: every distance is the canonical FP32 distance, one thread per pair
  * on the CUDA cores.  KNNM_BF16_RERANK: distances are first estimated from
@@ -64,8 +67,8 @@ typedef enum { KNNM_L2 = 0, KNNM_IP = 1, KNNM_COS = 2, KNNM_L1 = 3 } knnm_metric
  * bound is about 8x tighter and far fewer pairs need the re-rank on data of
  * moderate range (a row with a value beyond +-65504 re-ranks every pair).  Rows
  * of small non-negative integers (<= 256 in BF16, <= 2048 in FP16) are exact
- * on the tensor cores and never re-ranked.  L1 has no tensor-core form and
- * always runs as KNNM_FP32. */
+ * on the tensor cores and never re-ranked.  L1 and CHI2 have no tensor-core
+ * form and always run as KNNM_FP32. */
 typedef enum { KNNM_FP32 = 0, KNNM_BF16_RERANK = 1, KNNM_FP16_RERANK = 2 } knnm_precision;
 
 typedef struct {

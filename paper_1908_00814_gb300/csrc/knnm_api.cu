@@ -98,7 +98,7 @@ struct Derived {
 int derive(knnm_ctx* ctx, const knnm_params* p, int mode, int64_t n1, Derived* out) {
   if (!p) return fail(ctx, KNNM_ERR_INVALID, "params is NULL");
   if (p->k < 1 || p->k > 32) return fail(ctx, KNNM_ERR_INVALID, "k=%d outside 1..32", p->k);
-  if (p->metric < 0 || p->metric > 3) return fail(ctx, KNNM_ERR_INVALID, "bad metric %d", p->metric);
+  if (p->metric < 0 || p->metric > 4) return fail(ctx, KNNM_ERR_INVALID, "bad metric %d", p->metric);
   if (p->precision < KNNM_FP32 || p->precision > KNNM_FP16_RERANK)
     return fail(ctx, KNNM_ERR_INVALID, "bad precision %d", p->precision);
   if (p->max_iters < 0 || p->max_iters > KNNM_MAX_ROUNDS)
@@ -133,7 +133,7 @@ struct JoinPath {
 
 int choose_join(knnm_ctx* ctx, int precision, int metric, int cap_new, int cap_old, int d,
                 bool rows_aligned, JoinPath* jp) {
-  const bool tc = precision != KNNM_FP32 && metric != KNNM_L1;
+  const bool tc = precision != KNNM_FP32 && metric != KNNM_L1 && metric != KNNM_CHI2;
   if (tc || rows_aligned) {
     if (plan_pipe(precision, metric, cap_new, cap_old, d, &jp->pa, &jp->smem, &jp->grid) ==
         cudaSuccess) {
@@ -201,7 +201,8 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     if (in.n2 > 0 && !in.S2 && !size_only) return fail(ctx, KNNM_ERR_INVALID, "S_new is NULL");
   }
   // L1 has no tensor-core form
-  const int precision = params->metric != KNNM_L1 ? params->precision : KNNM_FP32;
+  const int precision =
+      params->metric != KNNM_L1 && params->metric != KNNM_CHI2 ? params->precision : KNNM_FP32;
   if (precision != KNNM_FP32 && d % 8 != 0)
     return fail(ctx, KNNM_ERR_INVALID, "the tensor-core paths need d %% 8 == 0 (d=%d)", d);
 
@@ -1253,13 +1254,14 @@ extern "C" int knnm_step_join(knnm_ctx* ctx, int mode, const float* X1, int64_t 
   ctx->err[0] = 0;
   int rc = check_rows(ctx, X1, nx1, X2, N, d);
   if (rc) return rc;
-  if (!params || params->k < 1 || params->k > 32 || params->metric < 0 || params->metric > 3)
+  if (!params || params->k < 1 || params->k > 32 || params->metric < 0 || params->metric > 4)
     return fail(ctx, KNNM_ERR_INVALID, "bad params");
   if (cap_new < 1 || cap_old < 1 || cap_new + cap_old > 96 || set_split < 0 || set_split > N ||
       (mode != SYMMETRIC && mode != JOINT))
     return fail(ctx, KNNM_ERR_INVALID, "bad capacities, split or mode");
   const int K = params->k;
-  const int precision = params->metric != KNNM_L1 ? params->precision : KNNM_FP32;
+  const int precision =
+      params->metric != KNNM_L1 && params->metric != KNNM_CHI2 ? params->precision : KNNM_FP32;
   if (precision != KNNM_FP32 && d % 8 != 0)
     return fail(ctx, KNNM_ERR_INVALID, "the tensor-core paths need d %% 8 == 0");
   cudaStream_t st = ctx->stream;
@@ -1451,7 +1453,7 @@ extern "C" int knnm_diversify(knnm_ctx* ctx, const float* S, int64_t n, int d, c
   if (!ctx) return KNNM_ERR_INVALID;
   ctx->err[0] = 0;
   if (n < 2 || n > 0x7FFFFFFFLL || d < 1 || k < 1 || k > 32 || k >= n || metric < 0 ||
-      metric > 3 || max_degree < 1 || max_degree > 256)
+      metric > 4 || max_degree < 1 || max_degree > 256)
     return fail(ctx, KNNM_ERR_INVALID, "bad diversification arguments (n=%lld k=%d max_degree=%d)",
                 (long long)n, k, max_degree);
   if (!all_device({S, G, out_ids, out_dists, out_degree}))
@@ -1539,7 +1541,7 @@ extern "C" int knnm_search(knnm_ctx* ctx, const float* S, int64_t n, int d, cons
                            uint32_t* out_evals, knnm_search_stats* stats) {
   if (!ctx) return KNNM_ERR_INVALID;
   ctx->err[0] = 0;
-  if (n < 1 || n > 0x7FFFFFFFLL || d < 1 || nq < 0 || metric < 0 || metric > 3 || k_out < 1 ||
+  if (n < 1 || n > 0x7FFFFFFFLL || d < 1 || nq < 0 || metric < 0 || metric > 4 || k_out < 1 ||
       ef < k_out || ef > 1024 || n_layers < 1 || n_layers > SEARCH_MAX_LAYERS || !layer_rows ||
       !layer_width || !layer_ids)
     return fail(ctx, KNNM_ERR_INVALID, "bad search arguments (ef=%d k_out=%d layers=%d)", ef,

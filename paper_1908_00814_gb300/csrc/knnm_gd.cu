@@ -530,6 +530,7 @@ __device__ __forceinline__ bool exact_pair(float qm, float rm, int d) {
   const unsigned long long lim = 1ull << 24;
   if (METRIC == L2) return (unsigned long long)d * (q + r) * (q + r) < lim;
   if (METRIC == L1) return (unsigned long long)d * (q + r) < lim;
+  if (METRIC == CHI2) return false;  // a quotient per term: not exact in general
   return (unsigned long long)d * q * r < lim;  // IP, COS: the dot product
 }
 
@@ -538,7 +539,9 @@ __device__ __forceinline__ bool exact_pair(float qm, float rm, int d) {
 // gamma_d * sum|terms| of the exact sum, gamma_m = m u / (1 - m u)).
 template <int METRIC>
 __device__ __forceinline__ float pair_bound(float est, float g, float nq, float nr, float den) {
-  if (METRIC == L2 || METRIC == L1) return 2.0f * g * est / (1.0f - g) * 1.0001f;
+  if (METRIC == L2 || METRIC == L1)  // non-negative terms
+    return 2.0f * g * est / (1.0f - g) * 1.0001f;
+  if (METRIC == CHI2) return __int_as_float(0x7f800000);  // terms of either sign: no skip
   const float dot = 2.2f * g * nq * nr;  // sum |a_i b_i| <= |a||b| (norms within gamma)
   if (METRIC == IP) return dot * 1.0001f + 1e-37f;
   if (den == 0.0f) return 0.0f;  // both read 1
@@ -903,6 +906,7 @@ cudaError_t launch_diversify(const GdArgs& a, int metric, cudaStream_t st) {
     KNNM_GD_CASE(IP)
     KNNM_GD_CASE(COS)
     KNNM_GD_CASE(L1)
+    KNNM_GD_CASE(CHI2)
 #undef KNNM_GD_CASE
     default:
       return cudaErrorInvalidValue;
@@ -952,6 +956,7 @@ cudaError_t launch_search(const SearchArgs& a, int metric, size_t smem, int grid
     KNNM_SEARCH_CASE(IP)
     KNNM_SEARCH_CASE(COS)
     KNNM_SEARCH_CASE(L1)
+    KNNM_SEARCH_CASE(CHI2)
 #undef KNNM_SEARCH_CASE
     default:
       return cudaErrorInvalidValue;

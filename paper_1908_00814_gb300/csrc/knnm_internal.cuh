@@ -21,7 +21,7 @@ constexpr uint64_t KEY_EMPTY = ~0ull;
 constexpr uint8_t FLAG_OLD = 0;
 constexpr uint8_t FLAG_NEW = 1;
 
-enum Metric { L2 = 0, IP = 1, COS = 2, L1 = 3 };
+enum Metric { L2 = 0, IP = 1, COS = 2, L1 = 3, CHI2 = 4 };
 enum Mode { SYMMETRIC = 0, JOINT = 1 };
 enum Stream { STREAM_FWD_NEW = 0, STREAM_REV_NEW = 1, STREAM_REV_OLD = 2, STREAM_INIT = 3 };
 
@@ -116,6 +116,14 @@ template <>
 struct Canon<L1> {
   __device__ __forceinline__ static float step(float acc, float a, float b) {
     return __fadd_rn(acc, fabsf(__fsub_rn(a, b)));
+  }
+};
+// Chi-square: (a - b)^2 / (a + b) per term, 0 when a + b = 0.
+template <>
+struct Canon<CHI2> {
+  __device__ __forceinline__ static float step(float acc, float a, float b) {
+    const float x = __fsub_rn(a, b), s = __fadd_rn(a, b);
+    return __fadd_rn(acc, s == 0.0f ? 0.0f : __fdiv_rn(__fmul_rn(x, x), s));
   }
 };
 

@@ -588,7 +588,7 @@ template <int METRIC>
 cudaError_t plan_metric(int precision, int cap_new, int cap_old, int d, JoinPlan* out) {
   const int cap_rows = cap_new + cap_old;
   const int pair_cap = cap_new * cap_rows;
-  if (precision != 0 && METRIC != L1) {
+  if (precision != 0 && METRIC != L1 && METRIC != CHI2) {
     out->chunk = d;
     out->smem = bf16_smem_bytes(d, pair_cap);
     return precision == 2 ? occupancy_grid(k_join_bf16<METRIC, true>, out->smem, &out->grid)
@@ -615,25 +615,27 @@ cudaError_t plan_metric(int precision, int cap_new, int cap_old, int d, JoinPlan
 
 cudaError_t plan_join(int precision, int metric, int cap_new, int cap_old, int d, JoinPlan* out) {
   if (cap_new + cap_old > 255) return cudaErrorInvalidValue;
-  if (precision != 0 && metric != L1 && (cap_new > TC_NEW || cap_new + cap_old > TC_ROWS))
+  if (precision != 0 && metric != L1 && metric != CHI2 &&
+      (cap_new > TC_NEW || cap_new + cap_old > TC_ROWS))
     return cudaErrorInvalidValue;
   switch (metric) {
     case L2: return plan_metric<L2>(precision, cap_new, cap_old, d, out);
     case IP: return plan_metric<IP>(precision, cap_new, cap_old, d, out);
     case COS: return plan_metric<COS>(precision, cap_new, cap_old, d, out);
-    default: return plan_metric<L1>(precision, cap_new, cap_old, d, out);
+    case L1: return plan_metric<L1>(precision, cap_new, cap_old, d, out);
+    default: return plan_metric<CHI2>(precision, cap_new, cap_old, d, out);
   }
 }
 
 cudaError_t launch_join(int precision, const JoinArgs& a, const JoinPlan& plan, cudaStream_t st) {
   const int pair_cap = a.cap_new * (a.cap_new + a.cap_old);
-  if (precision == 2 && a.metric != L1) {
+  if (precision == 2 && a.metric != L1 && a.metric != CHI2) {
     switch (a.metric) {
       case L2: k_join_bf16<L2, true><<<plan.grid, JT, plan.smem, st>>>(a, pair_cap); break;
       case IP: k_join_bf16<IP, true><<<plan.grid, JT, plan.smem, st>>>(a, pair_cap); break;
       default: k_join_bf16<COS, true><<<plan.grid, JT, plan.smem, st>>>(a, pair_cap); break;
     }
-  } else if (precision == 1 && a.metric != L1) {
+  } else if (precision == 1 && a.metric != L1 && a.metric != CHI2) {
     switch (a.metric) {
       case L2: k_join_bf16<L2, false><<<plan.grid, JT, plan.smem, st>>>(a, pair_cap); break;
       case IP: k_join_bf16<IP, false><<<plan.grid, JT, plan.smem, st>>>(a, pair_cap); break;
@@ -644,7 +646,8 @@ cudaError_t launch_join(int precision, const JoinArgs& a, const JoinPlan& plan, 
       case L2: k_join_fp32<L2><<<plan.grid, JT, plan.smem, st>>>(a, plan.chunk, pair_cap); break;
       case IP: k_join_fp32<IP><<<plan.grid, JT, plan.smem, st>>>(a, plan.chunk, pair_cap); break;
       case COS: k_join_fp32<COS><<<plan.grid, JT, plan.smem, st>>>(a, plan.chunk, pair_cap); break;
-      default: k_join_fp32<L1><<<plan.grid, JT, plan.smem, st>>>(a, plan.chunk, pair_cap); break;
+      case L1: k_join_fp32<L1><<<plan.grid, JT, plan.smem, st>>>(a, plan.chunk, pair_cap); break;
+      default: k_join_fp32<CHI2><<<plan.grid, JT, plan.smem, st>>>(a, plan.chunk, pair_cap); break;
     }
   }
   return cudaGetLastError();

@@ -702,7 +702,7 @@ cudaError_t setup_ring(size_t smem, int threads, int* per_sm) {
 
 cudaError_t plan_pipe(int precision, int metric, int cap_new, int cap_old, int d, PipeArgs* P,
                       size_t* smem, int* grid) {
-  const bool tc = precision != 0 && metric != L1;
+  const bool tc = precision != 0 && metric != L1 && metric != CHI2;
   const bool hf = precision == 2;
   const int cap = round_up4(cap_new + cap_old);
   if (cap_new + cap_old > 255 || cap > 64) return cudaErrorInvalidValue;
@@ -761,7 +761,8 @@ cudaError_t plan_pipe(int precision, int metric, int cap_new, int cap_old, int d
               : hf ? setup_ring<COS, true, true>(*smem, 32 * w, &per)
                    : setup_ring<COS, true, false>(*smem, 32 * w, &per);
       break;
-    default: e = setup_ring<L1, false, false>(*smem, 32 * w, &per); break;
+    case L1: e = setup_ring<L1, false, false>(*smem, 32 * w, &per); break;
+    default: e = setup_ring<CHI2, false, false>(*smem, 32 * w, &per); break;
   }
   if (e != cudaSuccess) return e;
   if (per < 1) return cudaErrorInvalidConfiguration;
@@ -774,7 +775,7 @@ cudaError_t plan_pipe(int precision, int metric, int cap_new, int cap_old, int d
 
 cudaError_t launch_pipe(int precision, const JoinArgs& a, const PipeArgs& P, size_t smem,
                         int grid, cudaStream_t st) {
-  const bool tc = precision != 0 && a.metric != L1;
+  const bool tc = precision != 0 && a.metric != L1 && a.metric != CHI2;
   const int threads = 32 * P.cw;
   if (tc && precision == 2) {
     switch (a.metric) {
@@ -793,7 +794,8 @@ cudaError_t launch_pipe(int precision, const JoinArgs& a, const PipeArgs& P, siz
       case L2: k_join_ring<L2, false, false><<<grid, threads, smem, st>>>(a, P); break;
       case IP: k_join_ring<IP, false, false><<<grid, threads, smem, st>>>(a, P); break;
       case COS: k_join_ring<COS, false, false><<<grid, threads, smem, st>>>(a, P); break;
-      default: k_join_ring<L1, false, false><<<grid, threads, smem, st>>>(a, P); break;
+      case L1: k_join_ring<L1, false, false><<<grid, threads, smem, st>>>(a, P); break;
+      default: k_join_ring<CHI2, false, false><<<grid, threads, smem, st>>>(a, P); break;
     }
   }
   return cudaGetLastError();

@@ -995,7 +995,8 @@ cudaError_t launch_init(const InitArgs& a, cudaStream_t st) {
     case L2: return launch_init_m<L2>(a, grid, st);
     case IP: return launch_init_m<IP>(a, grid, st);
     case COS: return launch_init_m<COS>(a, grid, st);
-    default: return launch_init_m<L1>(a, grid, st);
+    case L1: return launch_init_m<L1>(a, grid, st);
+    default: return launch_init_m<CHI2>(a, grid, st);
   }
 }
 
@@ -1082,7 +1083,8 @@ cudaError_t launch_list_dists(Rows rows, int64_t n, const int32_t* G, int K, int
     case L2: k_list_dists<L2><<<grid, BLOCK, 0, st>>>(rows, n, G, K, norms, vec4, ids, dists, ctr); break;
     case IP: k_list_dists<IP><<<grid, BLOCK, 0, st>>>(rows, n, G, K, norms, vec4, ids, dists, ctr); break;
     case COS: k_list_dists<COS><<<grid, BLOCK, 0, st>>>(rows, n, G, K, norms, vec4, ids, dists, ctr); break;
-    default: k_list_dists<L1><<<grid, BLOCK, 0, st>>>(rows, n, G, K, norms, vec4, ids, dists, ctr); break;
+    case L1: k_list_dists<L1><<<grid, BLOCK, 0, st>>>(rows, n, G, K, norms, vec4, ids, dists, ctr); break;
+    default: k_list_dists<CHI2><<<grid, BLOCK, 0, st>>>(rows, n, G, K, norms, vec4, ids, dists, ctr); break;
   }
   return cudaGetLastError();
 }

@@ -109,6 +109,26 @@ def sift_manifold(n: int, d: int = 128, latent: int = 16, n_comp: int = 64, sep:
     return X
 
 
+def bovw_like(n: int, d: int = 500, n_topics: int = 64, words: float = 60.0, seed: int = 0,
+              chunk: int = 1 << 16) -> np.ndarray:
+    """Bag-of-visual-words stand-in (NUSWide's 500-d BoVW histograms, chi-square
+    metric): each row draws Poisson counts of `words` expected words from a
+    mixture of two of n_topics sparse topic distributions over d visual words;
+    non-negative integers stored as float32, mostly zeros."""
+    rng = _rng(seed)
+    topics = rng.gamma(0.1, 1.0, size=(n_topics, d))
+    topics /= topics.sum(1, keepdims=True)
+    X = np.empty((n, d), np.float32)
+    for b in range(0, n, chunk):
+        e = min(n, b + chunk)
+        t1 = rng.integers(0, n_topics, size=e - b)
+        t2 = rng.integers(0, n_topics, size=e - b)
+        w = rng.random((e - b, 1))
+        lam = words * (w * topics[t1] + (1.0 - w) * topics[t2])
+        X[b:e] = rng.poisson(lam)
+    return X
+
+
 def gist_like(n: int, d: int = 960, latent: int = 64, seed: int = 0, n_comp: int = 256,
               rank: int = 16, chunk: int = 1 << 16) -> np.ndarray:
     """|M u|: a random d x d mixing M (entries N(0, 1/d)) of u = [z; 0.02 e],

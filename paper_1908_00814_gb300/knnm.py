@@ -16,11 +16,11 @@ import numpy as np
 
 _LIB_PATH = Path(__file__).resolve().parent / "libknnm.so"
 
-L2, IP, COS, L1 = 0, 1, 2, 3
+L2, IP, COS, L1, CHI2 = 0, 1, 2, 3, 4
 FP32, BF16_RERANK, FP16_RERANK = 0, 1, 2
 SYMMETRIC, JOINT = 0, 1
 MAX_ROUNDS = 64
-METRICS = {"l2": L2, "ip": IP, "cos": COS, "l1": L1}
+METRICS = {"l2": L2, "ip": IP, "cos": COS, "l1": L1, "chi2": CHI2}
 
 ERRORS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA error",
           -4: "timeout", -5: "not ready", -6: "device-side error"}

@@ -51,6 +51,8 @@ def data(kind, n, d, seed):
         return datagen.gaussian_mixture(n, d, n_comp=12, seed=seed, normalize=True)
     if kind == "sift":
         return datagen.sift_like(n, d, seed=seed)
+    if kind == "bovw":
+        return datagen.bovw_like(n, d, n_topics=10, words=3.0 * d, seed=seed)
     if kind == "hub":   # one row at the centre of a thin shell: it is in every list
         rng = np.random.default_rng(seed)
         X = rng.normal(size=(n, d))
@@ -72,6 +74,8 @@ CASES = [
     ("gmm", 700, 12, 32, "l2", 1),
     ("gmm", 600, 12, 1, "l2", 5),
     ("gmm", 997, 13, 9, "l2", 9),   # d not a multiple of 4: scalar loads
+    ("bovw", 2500, 100, 16, "chi2", 32),
+    ("bovw", 1200, 50, 10, "chi2", 20),   # d not a multiple of 4
 ]
 
 
@@ -155,7 +159,7 @@ def test_hierarchical_search_matches_oracle(torch, km, ctx, orc, hierarchy, ef, 
     assert st["dist_evals"] == int(want_ev.sum())
 
 
-@pytest.mark.parametrize("metric", ["l2", "l1", "ip", "cos"])
+@pytest.mark.parametrize("metric", ["l2", "l1", "ip", "cos", "chi2"])
 @pytest.mark.parametrize("kind", ["float", "int"])
 def test_flat_search_matches_oracle(torch, km, ctx, orc, metric, kind):
     """Float rows take the estimate-then-canonical route, small-integer rows the
@@ -169,6 +173,8 @@ def test_flat_search_matches_oracle(torch, km, ctx, orc, metric, kind):
         X = datagen.gaussian_mixture(5000, 20, n_comp=10, seed=8, normalize=metric == "cos")
         Q = np.concatenate([X[:50], datagen.gaussian_mixture(150, 20, n_comp=10, seed=9,
                                                             normalize=metric == "cos")])
+        if metric == "chi2":   # histogram-like: non-negative
+            X, Q = np.abs(X), np.abs(Q)
     G, _ = orc.bruteforce_knn(X, 10, metric=mcode)
     want = orc.search(X, [G], Q, 64, 12, metric=mcode, seed=2)
     Xd = cuda(torch, X)

@@ -65,12 +65,14 @@ def assert_same(a, b, what=""):
 def split_data(seed=3, n1=700, n2=600, d=16, kind="gmm"):
     if kind == "sift":
         X = datagen.sift_like(n1 + n2, d, seed=seed)
+    elif kind == "bovw":   # non-negative histograms for the chi-square metric
+        X = datagen.bovw_like(n1 + n2, d, n_topics=8, words=4.0 * d, seed=seed)
     else:
         X = datagen.gaussian_mixture(n1 + n2, d, n_comp=8, seed=seed)
     return X, n1
 
 
-METRIC_NAMES = {0: "l2", 1: "ip", 2: "cos", 3: "l1"}
+METRIC_NAMES = {0: "l2", 1: "ip", 2: "cos", 3: "l1", 4: "chi2"}
 
 
 # ------------------------------------------------------------------ steps
@@ -104,9 +106,9 @@ def test_hand_traced_round(torch, km, ctx):
 
 
 @pytest.mark.parametrize("mode", ["symmetric", "joint", "build"])
-@pytest.mark.parametrize("metric", [0, 1, 2, 3])
+@pytest.mark.parametrize("metric", [0, 1, 2, 3, 4])
 def test_init_parity(torch, km, ctx, orc, mode, metric):
-    X, n1 = split_data(seed=5 + metric)
+    X, n1 = split_data(seed=5 + metric, kind="bovw" if metric == 4 else "gmm")
     n = len(X)
     K = 10
     G1 = G2 = None
@@ -167,10 +169,11 @@ def _join_case(orc, X, n1, K, mode, metric, seed=1, t=2, s=None):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
-@pytest.mark.parametrize("metric", [0, 1, 2, 3])
+@pytest.mark.parametrize("metric", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("mode", ["symmetric", "joint", "build"])
 def test_join_parity(torch, km, ctx, orc, precision, metric, mode):
-    X, n1 = split_data(seed=11 + metric, n1=800, n2=700, d=24)
+    X, n1 = split_data(seed=11 + metric, n1=800, n2=700, d=24,
+                       kind="bovw" if metric == 4 else "gmm")
     K = 12
     m = orc.SYMMETRIC if mode == "symmetric" else orc.JOINT
     split = 0 if mode == "build" else n1
@@ -246,12 +249,15 @@ def test_smerge_config1_parity(torch, km, ctx, orc):
     _smerge_both(torch, km, ctx, orc, X, 5000, 10, 8)
 
 
-@pytest.mark.parametrize("metric", [1, 2, 3])
+@pytest.mark.parametrize("metric", [1, 2, 3, 4])
 def test_smerge_metrics_parity(torch, km, ctx, orc, metric):
-    X = datagen.gaussian_mixture(1800, 24, n_comp=6, seed=40 + metric,
-                                 normalize=(metric == 2))
+    if metric == 4:   # chi-square on non-negative histograms; no tensor-core form
+        X = datagen.bovw_like(1800, 64, n_topics=12, words=120.0, seed=44)
+    else:
+        X = datagen.gaussian_mixture(1800, 24, n_comp=6, seed=40 + metric,
+                                     normalize=(metric == 2))
     _smerge_both(torch, km, ctx, orc, X, 1000, 12, 5, metric=metric,
-                 precisions=("fp32",) if metric == 3 else ("fp32", "bf16", "fp16"))
+                 precisions=("fp32", "bf16") if metric >= 3 else ("fp32", "bf16", "fp16"))
 
 
 def test_smerge_sift_parity(torch, km, ctx, orc):
