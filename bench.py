@@ -186,13 +186,15 @@ def exact_recall(torch, X_dev, ids_dev, queries, K=10, chunk=131072, extra=48, m
     best_d = None
     best_i = None
     n = X_dev.shape[0]
-    if metric == "l1":
+    if metric in ("l1", "chi2"):
         chunk = max(1024, chunk // 32)
 
     def block(Xb):
         Xd = Xb.double()
         if metric == "l1":
             return torch.cdist(Q, Xd, p=1)
+        if metric == "chi2":
+            return chi2_block(torch, Q, Xd)
         dot = Q @ Xd.T
         if metric == "cos":
             den = qn.sqrt()[:, None] * (Xd ** 2).sum(1).sqrt()[None, :]
@@ -219,6 +221,9 @@ def exact_recall(torch, X_dev, ids_dev, queries, K=10, chunk=131072, extra=48, m
         R = X_dev[ids].double()
         if metric == "l1":
             return (R - Q[:, None, :]).abs().sum(-1)
+        if metric == "chi2":
+            s = R + Q[:, None, :]
+            return torch.where(s == 0, 0.0, (R - Q[:, None, :]) ** 2 / s.masked_fill(s == 0, 1.0)).sum(-1)
         if metric == "cos":
             dot = (R * Q[:, None, :]).sum(-1)
             den = qn.sqrt()[:, None] * (R ** 2).sum(-1).sqrt()
@@ -232,6 +237,17 @@ def exact_recall(torch, X_dev, ids_dev, queries, K=10, chunk=131072, extra=48, m
     return hits / (len(queries) * K)
 
 
+def chi2_block(torch, Q, Xd, qchunk=64):
+    """Chi-square distances [len(Q)][len(Xd)] in float64, by query blocks."""
+    out = []
+    for a in range(0, Q.shape[0], qchunk):
+        q = Q[a:a + qchunk, None, :]
+        s = q + Xd[None]
+        out.append(torch.where(s == 0, 0.0, (q - Xd[None]) ** 2 / s.masked_fill(s == 0, 1.0))
+                   .sum(-1))
+    return torch.cat(out, 0)
+
+
 def distance_error(torch, X_dev, ids_dev, dists_dev, queries, metric="l2"):
     """Relative error of the returned FP32 distances against float64 (max, p99)."""
     q = torch.as_tensor(queries, device=X_dev.device, dtype=torch.long)
@@ -240,6 +256,9 @@ def distance_error(torch, X_dev, ids_dev, dists_dev, queries, metric="l2"):
     R = X_dev[ids].double()
     if metric == "l1":
         ref = (R - Q[:, None, :]).abs().sum(-1)
+    elif metric == "chi2":
+        sm = R + Q[:, None, :]
+        ref = torch.where(sm == 0, 0.0, (R - Q[:, None, :]) ** 2 / sm.masked_fill(sm == 0, 1.0)).sum(-1)
     elif metric == "cos":
         dot = (R * Q[:, None, :]).sum(-1)
         ref = 1.0 - dot / ((Q ** 2).sum(-1).sqrt()[:, None] * (R ** 2).sum(-1).sqrt())
@@ -576,6 +595,21 @@ def run_other(args, name):
                 "rounds": stats[-1]["rounds"]}
         head = runs["hmerge_bf16"]
         merge = "H-Merge (Sec. 3.3) beside an NN-Descent build"
+    elif w["kind"] == "symmetric_chi2":
+        # NUSWide-like BoVW histograms under chi-square (Sec. 5): FP32 path only
+        metric = w["metric"]
+        bp = knnm.params(k=K, metric=metric, precision="fp32", max_iters=w["rounds"],
+                         delta=0.001, seed=11)
+        G1, _, _ = ctx.build(S1, bp)
+        bp.seed = 12
+        G2, _, _ = ctx.build(S2, bp)
+        p = knnm.params(k=K, metric=metric, precision="fp32", max_iters=w["rounds"],
+                        sample_rate=w["sample_rate"], delta=0.001, seed=0)
+        ms, out, stats = timed_call(torch, lambda: ctx.merge_symmetric(S1, G1, S2, G2, p),
+                                    steps, warmup)
+        record(f"{metric}_fp32", metric, ms, out, stats, n)
+        head = runs[f"{metric}_fp32"]
+        merge = "symmetric (Alg. 1), chi-square"
     elif w["kind"] == "joint":
         metric = w["metric"]
         G1, _, _ = ctx.build(S1, knnm.params(k=K, metric=metric, precision="fp32",
@@ -826,7 +860,8 @@ def main():
     ap.add_argument("--reference-rows", type=int, default=5000)
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "jmerge_gmm_2m_d96_k16_cos", "smerge_gist_1m_d960_k20",
-                             "hmerge_sift_1m_d128_k20", "hsearch_sift_1m_d128_k20"],
+                             "hmerge_sift_1m_d128_k20", "hsearch_sift_1m_d128_k20",
+                             "smerge_nuswide_260k_d500_k20_chi2"],
                     help="another merge workload (one JSON line of its own)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-batches", type=int, default=16)

@@ -175,6 +175,10 @@ WORKLOADS = {
     "hsearch_sift_1m_d128_k20": dict(kind="hsearch", gen="sift_manifold", n=1_000_000, d=128, k=20,
                                      metric="l2", rounds=10, sample_rate=0.5, seed=1007,
                                      queries=10_000, gen_args={}),
+    "smerge_nuswide_260k_d500_k20_chi2": dict(kind="symmetric_chi2", gen="bovw_like", n=260_000,
+                                              d=500, k=20, metric="chi2", rounds=20,
+                                              sample_rate=0.5, seed=1008,
+                                              gen_args=dict(words=2000.0)),
     "smerge_gist_1m_d960_k20": dict(kind="symmetric", gen="gist_like", n=1_000_000, d=960,
                                     k=20, metric="l1", rounds=10, sample_rate=0.5, seed=1005,
                                     gen_args={}),
@@ -199,6 +203,6 @@ def poisson_arrivals(count: int, rate_per_s: float, seed: int) -> np.ndarray:
 def generate(name: str, n: int | None = None) -> np.ndarray:
     w = WORKLOADS[name]
     gen = {"gaussian_mixture": gaussian_mixture, "sift_like": sift_like,
-           "sift_manifold": sift_manifold,
+           "sift_manifold": sift_manifold, "bovw_like": bovw_like,
            "gist_like": gist_like, "clustered_mixture": clustered_mixture}[w["gen"]]
     return gen(n if n is not None else w["n"], w["d"], seed=w["seed"], **w["gen_args"])
