@@ -24,7 +24,7 @@ _HERE = Path(__file__).resolve().parent
 _SRC = _HERE / "knnm_oracle.c"
 _LIB_PATH = _HERE / "_build" / "libknnm_oracle.so"
 
-L2, IP, COS, L1, CHI2 = 0, 1, 2, 3, 4
+L2, IP, COS, L1, CHI2, JACCARD = 0, 1, 2, 3, 4, 5
 SYMMETRIC, JOINT = 0, 1
 FLAG_OLD, FLAG_NEW = 0, 1
 STREAM_FWD_NEW, STREAM_REV_NEW, STREAM_REV_OLD, STREAM_INIT = 0, 1, 2, 3

@@ -16,7 +16,9 @@
  *     index order, fmaf per term.  L2 is the squared Euclidean distance (same
  *     ranking as l2), IP is 0 - dot, COS is 1 - dot/(|a||b|) (1 when a norm is
  *     zero), L1 adds |a_t - b_t| in order, CHI2 adds (a_t - b_t)^2 / (a_t + b_t)
- *     in order (a term with a_t + b_t = 0 adds 0; meant for non-negative rows).
+ *     in order (a term with a_t + b_t = 0 adds 0; meant for non-negative rows),
+ *     JACCARD is 1 - |A n B| / |A u B| of two sets given as 0/1 rows (the counts
+ *     as sums of min and max; 0 for two empty sets).
  *   - List order: ascending (distance, id); ids unique per list, no self.
  *   - Random numbers: H(seed, t, stream, owner, member) = five chained
  *     SplitMix64 steps (Steele, Lea and Flood, OOPSLA 2014), each absorbing one
@@ -49,7 +51,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { ORC_L2 = 0, ORC_IP = 1, ORC_COS = 2, ORC_L1 = 3, ORC_CHI2 = 4 };
+enum { ORC_L2 = 0, ORC_IP = 1, ORC_COS = 2, ORC_L1 = 3, ORC_CHI2 = 4, ORC_JACCARD = 5 };
 enum { ORC_SYMMETRIC = 0, ORC_JOINT = 1 };
 enum { STREAM_FWD_NEW = 0, STREAM_REV_NEW = 1, STREAM_REV_OLD = 2, STREAM_INIT = 3 };
 enum { FLAG_OLD = 0, FLAG_NEW = 1 };
@@ -96,6 +98,14 @@ float orc_distance(int metric, const float* a, const float* b, int d) {
       acc = acc + (s == 0.0f ? 0.0f : q / s);
     }
     return acc;
+  }
+  if (metric == ORC_JACCARD) {  /* the Kosarak metric of Sec. 5: sets as 0/1 rows */
+    float inter = 0.0f, uni = 0.0f;
+    for (int t = 0; t < d; ++t) {
+      inter = inter + fminf(a[t], b[t]);
+      uni = uni + fmaxf(a[t], b[t]);
+    }
+    return uni == 0.0f ? 0.0f : 1.0f - inter / uni;
   }
   return NAN;
 }

@@ -198,3 +198,34 @@ def test_chi_square_bruteforce_knn_matches_float64(orc):
         want = np.sort(T)[:8]
         assert np.allclose(dists[i], want, rtol=1e-5, atol=1e-6)
         assert np.allclose(T[ids[i]], want, rtol=1e-5, atol=1e-6)
+
+
+def _sets_to_rows(sets, dim):
+    X = np.zeros((len(sets), dim), np.float32)
+    for i, s in enumerate(sets):
+        X[i, list(s)] = 1.0
+    return X
+
+
+def test_jaccard_definition(orc):
+    """Jaccard distance of Kosarak's itemsets (Sec. 5): 1 - |A n B| / |A u B|,
+    computed by the oracle on 0/1 rows; checked against Python sets."""
+    rng = np.random.default_rng(5)
+    dim = 300
+    sets = [set(rng.choice(dim, size=int(rng.integers(0, 40)), replace=False).tolist())
+            for _ in range(60)]
+    sets[0] = set()
+    sets[1] = set()
+    X = _sets_to_rows(sets, dim)
+    for i in range(60):
+        for j in range(0, 60, 7):
+            a, b = sets[i], sets[j]
+            u = len(a | b)
+            want = np.float32(0.0) if u == 0 else np.float32(1.0) - np.float32(len(a & b)) / np.float32(u)
+            got = orc.distance(orc.JACCARD, X[i], X[j])
+            assert got.tobytes() == want.tobytes(), (i, j)
+    assert orc.distance(orc.JACCARD, X[0], X[1]) == 0.0          # two empty sets
+    assert orc.distance(orc.JACCARD, X[0], X[2]) == (1.0 if sets[2] else 0.0)
+    f = lambda a, b: float(orc.distance(orc.JACCARD, *_sets_to_rows([a, b], 10)))
+    assert f({1, 2, 3}, {2, 3, 4}) == np.float32(1.0) - np.float32(2.0) / np.float32(4.0)
+    assert f({1}, {2}) == 1.0 and f({5, 6}, {5, 6}) == 0.0
