@@ -56,7 +56,14 @@ enum {
   KNNM_ERR_DEVICE = -6     /* a kernel reported an internal error */
 };
 
-typedef enum { KNNM_L2 = 0, KNNM_IP = 1, KNNM_COS = 2, KNNM_L1 = 3, KNNM_CHI2 = 4 } knnm_metric;
+typedef enum {
+  KNNM_L2 = 0,
+  KNNM_IP = 1,
+  KNNM_COS = 2,
+  KNNM_L1 = 3,
+  KNNM_CHI2 = 4,
+  KNNM_JACCARD = 5 /* sets only: the knnm_*_sets entry points */
+} knnm_metric;
 
 /* KNNM_FP32: every distance is the canonical FP32 distance, one thread per pair
  * on the CUDA cores.  KNNM_BF16_RERANK: distances are first estimated from
@@ -144,6 +151,26 @@ int knnm_merge_joint(knnm_ctx* ctx, const float* S1, int64_t n1, const int32_t* 
 /* NN-Descent build of S [n][d] (J-Merge with an empty graph); n >= K+1. */
 int knnm_build(knnm_ctx* ctx, const float* S, int64_t n, int d, const knnm_params* params,
                int32_t* out_ids, float* out_dists, knnm_stats* stats);
+
+/* The same three merges on sets (the Kosarak itemsets of Sec. 5) under the
+ * Jaccard distance 1 - |A n B| / |A u B| (0 for two empty sets), params->metric
+ * = KNNM_JACCARD, FP32 only.  All n1 + n2 rows are one CSR array on the device:
+ * row i holds items[offsets[i] .. offsets[i+1]), ascending, no repeats,
+ * non-negative, fewer than 2^23 per row; offsets [n1 + n2 + 1] starts at 0 and
+ * ends at nnz, the length of items.  S1 is rows [0, n1), S2 (or the raw rows)
+ * the rest; G1, G2 and the outputs as in the dense calls (host or device).
+ * Malformed rows are KNNM_ERR_INVALID. */
+int knnm_merge_symmetric_sets(knnm_ctx* ctx, const int64_t* offsets, const int32_t* items,
+                              int64_t nnz, int64_t n1, int64_t n2, const int32_t* G1,
+                              const int32_t* G2, const knnm_params* params, int32_t* out_ids,
+                              float* out_dists, knnm_stats* stats);
+int knnm_merge_joint_sets(knnm_ctx* ctx, const int64_t* offsets, const int32_t* items,
+                          int64_t nnz, int64_t n1, int64_t n2, const int32_t* G1,
+                          const knnm_params* params, int32_t* out_ids, float* out_dists,
+                          knnm_stats* stats);
+int knnm_build_sets(knnm_ctx* ctx, const int64_t* offsets, const int32_t* items, int64_t nnz,
+                    int64_t n, const knnm_params* params, int32_t* out_ids, float* out_dists,
+                    knnm_stats* stats);
 
 /* Merge tree (Sec. 1 and Sec. 3: a graph over a large set made from graphs
  * built independently on its parts, by repeated two-graph merges).  S [n][d]

@@ -98,7 +98,7 @@ struct Derived {
 int derive(knnm_ctx* ctx, const knnm_params* p, int mode, int64_t n1, Derived* out) {
   if (!p) return fail(ctx, KNNM_ERR_INVALID, "params is NULL");
   if (p->k < 1 || p->k > 32) return fail(ctx, KNNM_ERR_INVALID, "k=%d outside 1..32", p->k);
-  if (p->metric < 0 || p->metric > 4) return fail(ctx, KNNM_ERR_INVALID, "bad metric %d", p->metric);
+  if (p->metric < 0 || p->metric > 5) return fail(ctx, KNNM_ERR_INVALID, "bad metric %d", p->metric);
   if (p->precision < KNNM_FP32 || p->precision > KNNM_FP16_RERANK)
     return fail(ctx, KNNM_ERR_INVALID, "bad precision %d", p->precision);
   if (p->max_iters < 0 || p->max_iters > KNNM_MAX_ROUNDS)
@@ -165,6 +165,10 @@ struct MergeIn {
   int64_t n2;
   const int32_t* G2;
   int d;
+  // sets (JACCARD): all n1 + n2 rows as one CSR array on the device
+  const int64_t* set_off = nullptr;
+  const int32_t* set_items = nullptr;
+  int64_t set_nnz = 0;  // entries of set_items
 };
 
 // With size_only set, nothing runs: the scratch the call would take (every
@@ -178,9 +182,17 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   int rc = derive(ctx, params, in.mode, in.n1, &D);
   if (rc) return rc;
   const int64_t N = in.n1 + in.n2;
-  const int d = in.d;
+  const bool sets = in.set_off != nullptr;
+  const int d = sets ? 1 : in.d;
   const int K = D.K;
   if (d < 1) return fail(ctx, KNNM_ERR_INVALID, "d=%d", d);
+  if (sets != (params->metric == KNNM_JACCARD))
+    return fail(ctx, KNNM_ERR_INVALID, sets ? "set rows take the Jaccard metric"
+                                            : "the Jaccard metric takes set rows (knnm_*_sets)");
+  if (sets && !size_only &&
+      (!is_device_ptr(in.set_off) ||
+       (in.set_nnz > 0 && (!in.set_items || !is_device_ptr(in.set_items)))))
+    return fail(ctx, KNNM_ERR_INVALID, "set rows must be device arrays");
   if (in.n1 < 0 || in.n2 < 0 || N > 0x7FFFFFFFLL)
     return fail(ctx, KNNM_ERR_INVALID, "row counts out of range");
   if (!size_only && (!out_ids || !out_dists))
@@ -191,18 +203,22 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
                   (long long)in.n1, (long long)in.n2, K);
     if (in.n1 < D.Kr || in.n2 < D.Kr)
       return fail(ctx, KNNM_ERR_INVALID, "each set needs at least k - floor(r*k) = %d rows", D.Kr);
-    if (!size_only && (!in.S1 || !in.S2 || !in.G1 || !in.G2))
+    if (!size_only && ((!sets && (!in.S1 || !in.S2)) || !in.G1 || !in.G2))
       return fail(ctx, KNNM_ERR_INVALID, "NULL input array");
   } else {
     if (N < K + 1) return fail(ctx, KNNM_ERR_INVALID, "n1+n2 must be >= k+1");
-    if (in.n1 > 0 && (in.n1 < K + 1 || in.n2 < D.Kr || (!size_only && (!in.G1 || !in.S1))))
+    if (in.n1 > 0 && (in.n1 < K + 1 || in.n2 < D.Kr ||
+                      (!size_only && (!in.G1 || (!sets && !in.S1)))))
       return fail(ctx, KNNM_ERR_INVALID,
                   "J-Merge needs n1 >= k+1, n2 >= k - floor(r*k) and G1 when n1 > 0");
-    if (in.n2 > 0 && !in.S2 && !size_only) return fail(ctx, KNNM_ERR_INVALID, "S_new is NULL");
+    if (in.n2 > 0 && !sets && !in.S2 && !size_only)
+      return fail(ctx, KNNM_ERR_INVALID, "S_new is NULL");
   }
   // L1 has no tensor-core form
-  const int precision =
-      params->metric != KNNM_L1 && params->metric != KNNM_CHI2 ? params->precision : KNNM_FP32;
+  const int precision = params->metric != KNNM_L1 && params->metric != KNNM_CHI2 &&
+                                params->metric != KNNM_JACCARD
+                            ? params->precision
+                            : KNNM_FP32;
   if (precision != KNNM_FP32 && d % 8 != 0)
     return fail(ctx, KNNM_ERR_INVALID, "the tensor-core paths need d %% 8 == 0 (d=%d)", d);
 
@@ -210,15 +226,15 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   KNNM_CUDA(cudaSetDevice(ctx->device));
 
   // Where does each array live?
-  const bool s1_dev = size_only || in.n1 == 0 || is_device_ptr(in.S1);
-  const bool s2_dev = size_only || in.n2 == 0 || is_device_ptr(in.S2);
+  const bool s1_dev = size_only || sets || in.n1 == 0 || is_device_ptr(in.S1);
+  const bool s2_dev = size_only || sets || in.n2 == 0 || is_device_ptr(in.S2);
   const bool g1_dev = size_only || !in.G1 || is_device_ptr(in.G1);
   const bool g2_dev = size_only || !in.G2 || is_device_ptr(in.G2);
   const bool oi_dev = size_only || is_device_ptr(out_ids);
   const bool od_dev = size_only || is_device_ptr(out_dists);
 
   // rows staged from the caller's device arrays need 16-byte alignment for bulk copies
-  const bool rows_aligned = d % 4 == 0 && (size_only || !s1_dev || !s2_dev ||
+  const bool rows_aligned = !sets && d % 4 == 0 && (size_only || !s1_dev || !s2_dev ||
                                            ((in.n1 == 0 || aligned16(in.S1)) &&
                                             (in.n2 == 0 || aligned16(in.S2))));
   JoinPath jp;
@@ -355,13 +371,25 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     G2 = P.G2;
   }
   Rows rows{X1, X2 ? X2 : X1, nx1, d};
-  const bool use_bulk =
-      d % 4 == 0 && aligned16(rows.X1) && aligned16(rows.X2) && (nx1 == N || aligned16(rows.X2));
+  rows.off = in.set_off;
+  rows.items = in.set_items;
+  const bool use_bulk = !sets && d % 4 == 0 && aligned16(rows.X1) && aligned16(rows.X2) &&
+                        (nx1 == N || aligned16(rows.X2));
 
   int launches = 1;
   KNNM_CUDA(cudaEventRecord(ctx->ev[0], st));
   KNNM_CUDA(cudaMemsetAsync(P.ctr, 0, sizeof(DevCounters), st));
   KNNM_CUDA(cudaMemsetAsync(&P.ctr->err_row, 0xFF, 8, st));
+  if (sets) {  // CSR offsets non-decreasing from 0, items ascending without repeats
+    KNNM_CUDA(launch_check_sets(in.set_off, in.set_items, in.set_nnz, N, P.ctr, st));
+    KNNM_CUDA(cudaMemcpyAsync(ctx->host_ctr, P.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost,
+                              st));
+    KNNM_CUDA(cudaStreamSynchronize(st));
+    if (ctx->host_ctr->err)
+      return fail(ctx, KNNM_ERR_INVALID, "set row %llu is malformed (offsets or item order)",
+                  (unsigned long long)ctx->host_ctr->err_row);
+    ++launches;
+  }
   if (P.norms) {
     KNNM_CUDA(launch_norms(rows, N, P.norms, st));
     ++launches;
@@ -389,7 +417,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   ia.metric = params->metric;
   ia.seed = params->seed;
   ia.norms = P.norms;
-  ia.vec4 = (d % 4 == 0 && aligned16(rows.X1) && aligned16(rows.X2)) ? 1 : 0;
+  ia.vec4 = (!sets && d % 4 == 0 && aligned16(rows.X1) && aligned16(rows.X2)) ? 1 : 0;
   ia.keys = P.keys;
   ia.flags = P.flags;
   ia.rear = P.rear;
@@ -746,6 +774,33 @@ extern "C" int knnm_build(knnm_ctx* ctx, const float* S, int64_t n, int d,
                           const knnm_params* params, int32_t* out_ids, float* out_dists,
                           knnm_stats* stats) {
   MergeIn in{JOINT, nullptr, 0, nullptr, S, n, nullptr, d};
+  return run_merge(ctx, in, params, out_ids, out_dists, stats);
+}
+
+extern "C" int knnm_merge_symmetric_sets(knnm_ctx* ctx, const int64_t* offsets,
+                                         const int32_t* items, int64_t nnz, int64_t n1,
+                                         int64_t n2, const int32_t* G1, const int32_t* G2,
+                                         const knnm_params* params, int32_t* out_ids,
+                                         float* out_dists, knnm_stats* stats) {
+  if (!offsets || nnz < 0) return fail(ctx, KNNM_ERR_INVALID, "bad set rows");
+  MergeIn in{SYMMETRIC, nullptr, n1, G1, nullptr, n2, G2, 1, offsets, items, nnz};
+  return run_merge(ctx, in, params, out_ids, out_dists, stats);
+}
+
+extern "C" int knnm_merge_joint_sets(knnm_ctx* ctx, const int64_t* offsets, const int32_t* items,
+                                     int64_t nnz, int64_t n1, int64_t n2, const int32_t* G1,
+                                     const knnm_params* params, int32_t* out_ids,
+                                     float* out_dists, knnm_stats* stats) {
+  if (!offsets || nnz < 0) return fail(ctx, KNNM_ERR_INVALID, "bad set rows");
+  MergeIn in{JOINT, nullptr, n1, G1, nullptr, n2, nullptr, 1, offsets, items, nnz};
+  return run_merge(ctx, in, params, out_ids, out_dists, stats);
+}
+
+extern "C" int knnm_build_sets(knnm_ctx* ctx, const int64_t* offsets, const int32_t* items,
+                               int64_t nnz, int64_t n, const knnm_params* params,
+                               int32_t* out_ids, float* out_dists, knnm_stats* stats) {
+  if (!offsets || nnz < 0) return fail(ctx, KNNM_ERR_INVALID, "bad set rows");
+  MergeIn in{JOINT, nullptr, 0, nullptr, nullptr, n, nullptr, 1, offsets, items, nnz};
   return run_merge(ctx, in, params, out_ids, out_dists, stats);
 }
 
@@ -1260,8 +1315,10 @@ extern "C" int knnm_step_join(knnm_ctx* ctx, int mode, const float* X1, int64_t 
       (mode != SYMMETRIC && mode != JOINT))
     return fail(ctx, KNNM_ERR_INVALID, "bad capacities, split or mode");
   const int K = params->k;
-  const int precision =
-      params->metric != KNNM_L1 && params->metric != KNNM_CHI2 ? params->precision : KNNM_FP32;
+  const int precision = params->metric != KNNM_L1 && params->metric != KNNM_CHI2 &&
+                                params->metric != KNNM_JACCARD
+                            ? params->precision
+                            : KNNM_FP32;
   if (precision != KNNM_FP32 && d % 8 != 0)
     return fail(ctx, KNNM_ERR_INVALID, "the tensor-core paths need d %% 8 == 0");
   cudaStream_t st = ctx->stream;

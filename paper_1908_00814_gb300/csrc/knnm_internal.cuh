@@ -21,7 +21,7 @@ constexpr uint64_t KEY_EMPTY = ~0ull;
 constexpr uint8_t FLAG_OLD = 0;
 constexpr uint8_t FLAG_NEW = 1;
 
-enum Metric { L2 = 0, IP = 1, COS = 2, L1 = 3, CHI2 = 4 };
+enum Metric { L2 = 0, IP = 1, COS = 2, L1 = 3, CHI2 = 4, JACCARD = 5 };
 enum Mode { SYMMETRIC = 0, JOINT = 1 };
 enum Stream { STREAM_FWD_NEW = 0, STREAM_REV_NEW = 1, STREAM_REV_OLD = 2, STREAM_INIT = 3 };
 
@@ -179,15 +179,37 @@ __device__ __forceinline__ float canon_norm_global(const float* __restrict__ a, 
 }
 
 // Row i of the dataset split in two arrays (rows < nx1 in X1, the rest in X2).
+// Sets (JACCARD) are rows of a CSR array instead: row i holds the ascending,
+// repeat-free items items[off[i] .. off[i+1]).
 struct Rows {
   const float* X1;
   const float* X2;
   int64_t nx1;
   int d;
+  const int64_t* off = nullptr;
+  const int32_t* items = nullptr;
   __host__ __device__ __forceinline__ const float* row(int64_t i) const {
     return i < nx1 ? X1 + (size_t)i * d : X2 + (size_t)(i - nx1) * d;
   }
 };
+
+// Jaccard distance 1 - |A n B| / |A u B| of sets i and j (0 for two empty
+// sets): the counts are exact integers, then one division and one subtraction.
+__device__ __forceinline__ float jaccard_rows(const Rows& R, int64_t i, int64_t j) {
+  const int64_t ai = __ldg(R.off + i), bi = __ldg(R.off + j);
+  const int na = (int)(__ldg(R.off + i + 1) - ai), nb = (int)(__ldg(R.off + j + 1) - bi);
+  const int32_t* a = R.items + ai;
+  const int32_t* b = R.items + bi;
+  int x = 0, y = 0, inter = 0;
+  while (x < na && y < nb) {
+    const int32_t p = __ldg(a + x), q = __ldg(b + y);
+    inter += p == q;
+    x += p <= q;
+    y += q <= p;
+  }
+  const int uni = na + nb - inter;
+  return uni == 0 ? 0.0f : __fsub_rn(1.0f, __fdiv_rn((float)inter, (float)uni));
+}
 
 // ---------------------------------------------------------------------------
 // Warp utilities (K <= 32 entries: one per lane).
@@ -530,6 +552,10 @@ cudaError_t launch_unpack(int64_t count, const uint64_t* keys, int32_t* ids, flo
 // rmax[i] = max |x| of row i when BF16 holds the row exactly as integers, else -1.
 cudaError_t launch_bf16_prep(Rows rows, int64_t N, __nv_bfloat16* Xb, float4* aux, float* rmax,
                              int half, unsigned long long* inexact, cudaStream_t st);
+
+// Validates set rows (CSR): errors land in ctr (err, err_row).
+cudaError_t launch_check_sets(const int64_t* off, const int32_t* items, int64_t nnz, int64_t n,
+                              DevCounters* ctr, cudaStream_t st);
 
 // Exclusive scan of cnt[0..n) into offs[0..n] (offs[n] = total); tile_sum
 // needs ceil(n / 1024) entries.

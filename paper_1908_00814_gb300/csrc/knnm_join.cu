@@ -290,6 +290,70 @@ __global__ void __launch_bounds__(JT) k_join_fp32(JoinArgs a, int chunk, int pai
 }
 
 // ---------------------------------------------------------------------------
+// Jaccard join on sets (CSR rows): one thread per pair intersects the two
+// sorted item lists from global memory; no rows are staged.
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(JT) k_join_jaccard(JoinArgs a, int pair_cap) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int cap_rows = a.cap_new + a.cap_old;
+  unsigned char* p = smem;
+  JoinShared S;
+  S.kth = (uint64_t*)p;
+  p += (size_t)cap_rows * 8;
+  S.bar = (uint64_t*)p;
+  p += 16;
+  S.cid = (int32_t*)p;
+  p += (size_t)cap_rows * 4;
+  S.cnorm = (float*)p;
+  p += (size_t)cap_rows * 4;
+  S.scal = (int*)p;
+  p += 16;
+  S.pairs = (uint16_t*)p;
+  (void)pair_cap;
+  if (threadIdx.x == 0) S.scal[1] = 0;
+  __syncthreads();
+  unsigned long long evals = 0, gathered = 0;
+  for (int64_t u = blockIdx.x; u < a.N; u += gridDim.x) {
+    int nn, M;
+    load_candidates(a, u, S, nn, M);
+    __syncthreads();
+    const int np = build_pairs(a, nn, M, S);
+    evals += (threadIdx.x == 0) ? (unsigned long long)np : 0ull;
+    gathered += (threadIdx.x == 0 && np > 0) ? (unsigned long long)M : 0ull;
+    for (int q0 = 0; q0 < np; q0 += JT) {
+      const int q = q0 + threadIdx.x;
+      bool hp = false, hq = false;
+      int32_t tp = 0, tq = 0;
+      uint64_t kp = 0, kq = 0;
+      if (q < np) {
+        const uint16_t pr = S.pairs[q];
+        const int i = pr >> 8, j = pr & 0xFF;
+        const int32_t pi = S.cid[i], pj = S.cid[j];
+        const float dist = jaccard_rows(a.rows, pi, pj);
+        kp = make_key(dist, pj);
+        kq = make_key(dist, pi);
+        hp = kp < S.kth[i];
+        hq = kq < S.kth[j];
+        tp = pi;
+        tq = pj;
+      }
+      emit(a, S, hp, tp, kp, hq, tq, kq);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int fill = S.scal[1];
+    a.region_cnt[blockIdx.x] = (unsigned long long)min((uint64_t)fill, a.region_cap);
+    atomicAdd(&a.ctr->proposals, (unsigned long long)fill);
+    if ((uint64_t)fill > a.region_cap)
+      atomicAdd(&a.ctr->overflow, (unsigned long long)((uint64_t)fill - a.region_cap));
+    atomicAdd(&a.ctr->dist_evals, evals);
+    atomicAdd(&a.ctr->gathered, gathered);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // BF16 tensor-core join with FP32 re-rank
 // ---------------------------------------------------------------------------
 
@@ -615,6 +679,12 @@ cudaError_t plan_metric(int precision, int cap_new, int cap_old, int d, JoinPlan
 
 cudaError_t plan_join(int precision, int metric, int cap_new, int cap_old, int d, JoinPlan* out) {
   if (cap_new + cap_old > 255) return cudaErrorInvalidValue;
+  if (metric == JACCARD) {
+    const int cap_rows = cap_new + cap_old;
+    out->chunk = 0;
+    out->smem = ((size_t)cap_rows * 16 + 32 + (size_t)cap_new * cap_rows * 2 + 127) & ~(size_t)127;
+    return occupancy_grid(k_join_jaccard, out->smem, &out->grid);
+  }
   if (precision != 0 && metric != L1 && metric != CHI2 &&
       (cap_new > TC_NEW || cap_new + cap_old > TC_ROWS))
     return cudaErrorInvalidValue;
@@ -629,7 +699,9 @@ cudaError_t plan_join(int precision, int metric, int cap_new, int cap_old, int d
 
 cudaError_t launch_join(int precision, const JoinArgs& a, const JoinPlan& plan, cudaStream_t st) {
   const int pair_cap = a.cap_new * (a.cap_new + a.cap_old);
-  if (precision == 2 && a.metric != L1 && a.metric != CHI2) {
+  if (a.metric == JACCARD) {
+    k_join_jaccard<<<plan.grid, JT, plan.smem, st>>>(a, pair_cap);
+  } else if (precision == 2 && a.metric != L1 && a.metric != CHI2) {
     switch (a.metric) {
       case L2: k_join_bf16<L2, true><<<plan.grid, JT, plan.smem, st>>>(a, pair_cap); break;
       case IP: k_join_bf16<IP, true><<<plan.grid, JT, plan.smem, st>>>(a, pair_cap); break;

@@ -65,13 +65,17 @@ __device__ __forceinline__ void block_add(unsigned long long* dst, unsigned long
 template <int METRIC>
 __device__ __forceinline__ float dist_rows(const Rows& R, int64_t i, int64_t j, const float* norms,
                                            int vec4) {
-  float na = 0.f, nb = 0.f;
-  if (METRIC == COS) {
-    na = norms[i];
-    nb = norms[j];
+  if constexpr (METRIC == JACCARD) {
+    return jaccard_rows(R, i, j);
+  } else {
+    float na = 0.f, nb = 0.f;
+    if (METRIC == COS) {
+      na = norms[i];
+      nb = norms[j];
+    }
+    if (vec4) return canon_dist_global4<METRIC>(R.row(i), R.row(j), R.d, na, nb);
+    return canon_dist_global<METRIC>(R.row(i), R.row(j), R.d, na, nb);
   }
-  if (vec4) return canon_dist_global4<METRIC>(R.row(i), R.row(j), R.d, na, nb);
-  return canon_dist_global<METRIC>(R.row(i), R.row(j), R.d, na, nb);
 }
 
 // Draws `want` distinct ids from [base, base+n_src) \ {i}: candidate c is
@@ -147,6 +151,9 @@ __device__ __forceinline__ void init_cp16(void* dst, const void* src) {
 template <int METRIC>
 __device__ __forceinline__ float staged_dist(const Rows& R, int64_t i, int32_t g, int rows,
                                              const float* norms, float* buf) {
+  if constexpr (METRIC == JACCARD) {  // sets are never staged; kept for completeness
+    return g >= 0 ? jaccard_rows(R, i, g) : 0.0f;
+  } else {
   const int lane = threadIdx.x & 31, d = R.d;
   const float4* xi = reinterpret_cast<const float4*>(R.row(i));
   const float* yj = buf + lane * INIT_STRIDE;
@@ -179,6 +186,7 @@ __device__ __forceinline__ float staged_dist(const Rows& R, int64_t i, int32_t g
     nb = g >= 0 ? norms[g] : 0.f;
   }
   return canon_finish<METRIC>(acc, na, nb);
+  }
 }
 
 template <int METRIC>
@@ -996,6 +1004,7 @@ cudaError_t launch_init(const InitArgs& a, cudaStream_t st) {
     case IP: return launch_init_m<IP>(a, grid, st);
     case COS: return launch_init_m<COS>(a, grid, st);
     case L1: return launch_init_m<L1>(a, grid, st);
+    case JACCARD: return launch_init_m<JACCARD>(a, grid, st);
     default: return launch_init_m<CHI2>(a, grid, st);
   }
 }
@@ -1008,6 +1017,34 @@ cudaError_t launch_exclusive_scan(const int32_t* cnt, int64_t n, unsigned long l
   k_scan_tiles<<<(unsigned)ntiles, 256, 0, st>>>(cnt, n, tile_sum);
   k_scan_sums<<<1, 1024, 0, st>>>(tile_sum, ntiles, total);
   k_scan_apply<<<(unsigned)ntiles, 256, 0, st>>>(cnt, n, tile_sum, offs, total);
+  return cudaGetLastError();
+}
+
+// Set rows: offsets from 0, non-decreasing, within the nnz items; items
+// ascending without repeats and non-negative; rows below 2^23 items (the
+// Jaccard counts stay exact in FP32).  One warp per row.
+__global__ void k_check_sets(const int64_t* off, const int32_t* items, int64_t nnz, int64_t n,
+                             DevCounters* ctr) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n;
+       i += nw) {
+    const int64_t a = off[i], b = off[i + 1];
+    bool bad = (i == 0 && a != 0) || (i == n - 1 && b != nnz) || a < 0 || b < a || b > nnz ||
+               b - a >= (1 << 23);
+    if (!bad)
+      for (int64_t t = a + lane; t < b; t += 32) {
+        const int32_t x = items[t];
+        if (x < 0 || (t > a && items[t - 1] >= x)) bad = true;
+      }
+    if (__any_sync(FULL, bad) && lane == 0) raise_err(ctr, DERR_BAD_ID, i);
+  }
+}
+
+cudaError_t launch_check_sets(const int64_t* off, const int32_t* items, int64_t nnz, int64_t n,
+                              DevCounters* ctr, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_check_sets<<<grid_for_warps(n), BLOCK, 0, st>>>(off, items, nnz, n, ctr);
   return cudaGetLastError();
 }
 

@@ -129,6 +129,42 @@ def bovw_like(n: int, d: int = 500, n_topics: int = 64, words: float = 60.0, see
     return X
 
 
+def itemsets(n: int, dim: int = 27983, n_types: int = 2000, core: int = 40,
+             mean_len: float = 20.0, seed: int = 0):
+    """Kosarak-like itemsets (Jaccard metric) as CSR arrays (offsets int64
+    [n+1], items int32, ascending within a row): items have Zipf(1.2)
+    popularity; each row picks one of n_types basket types with a core of
+    `core` items and draws a log-normal number of items (median mean_len,
+    sigma 0.6, 1..200), four in five from its type's core, the rest by
+    popularity."""
+    rng = _rng(seed)
+    pop = 1.0 / np.arange(1, dim + 1) ** 1.2
+    pop /= pop.sum()
+    perm = rng.permutation(dim)
+    cores = [perm[rng.choice(dim, size=core, replace=False, p=pop)] for _ in range(n_types)]
+    lens = np.clip(np.rint(rng.lognormal(np.log(mean_len), 0.6, size=n)), 1, 200).astype(int)
+    types = rng.integers(0, n_types, size=n)
+    rows = []
+    for i in range(n):
+        k_core = min(core, int(rng.binomial(lens[i], 0.8)))
+        a = rng.choice(cores[types[i]], size=k_core, replace=False)
+        b = perm[rng.choice(dim, size=lens[i] - k_core, p=pop)]
+        rows.append(np.unique(np.concatenate([a, b])))
+    offsets = np.zeros(n + 1, np.int64)
+    offsets[1:] = np.cumsum([len(r) for r in rows])
+    items = np.concatenate(rows).astype(np.int32) if n else np.zeros(0, np.int32)
+    return offsets, items
+
+
+def sets_to_rows(offsets, items, dim) -> np.ndarray:
+    """0/1 rows [n][dim] of CSR sets (the oracle's input form)."""
+    n = len(offsets) - 1
+    X = np.zeros((n, dim), np.float32)
+    for i in range(n):
+        X[i, items[offsets[i]:offsets[i + 1]]] = 1.0
+    return X
+
+
 def gist_like(n: int, d: int = 960, latent: int = 64, seed: int = 0, n_comp: int = 256,
               rank: int = 16, chunk: int = 1 << 16) -> np.ndarray:
     """|M u|: a random d x d mixing M (entries N(0, 1/d)) of u = [z; 0.02 e],

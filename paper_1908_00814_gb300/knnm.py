@@ -16,11 +16,11 @@ import numpy as np
 
 _LIB_PATH = Path(__file__).resolve().parent / "libknnm.so"
 
-L2, IP, COS, L1, CHI2 = 0, 1, 2, 3, 4
+L2, IP, COS, L1, CHI2, JACCARD = 0, 1, 2, 3, 4, 5
 FP32, BF16_RERANK, FP16_RERANK = 0, 1, 2
 SYMMETRIC, JOINT = 0, 1
 MAX_ROUNDS = 64
-METRICS = {"l2": L2, "ip": IP, "cos": COS, "l1": L1, "chi2": CHI2}
+METRICS = {"l2": L2, "ip": IP, "cos": COS, "l1": L1, "chi2": CHI2, "jaccard": JACCARD}
 
 ERRORS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA error",
           -4: "timeout", -5: "not ready", -6: "device-side error"}
@@ -131,6 +131,12 @@ SIGNATURES = {
     "knnm_step_final": (_I, [_P, _I64, _I, _P, _P, _I, _P, _P, _P, _P]),
     "knnm_step_sample_noalloc": (_I, [_P, _I64, _I, _P, _P, _P, _U64, _I, _I, _I, _I, _P, _P,
                                       _P, _P]),
+    "knnm_merge_symmetric_sets": (_I, [_P, _P, _P, _I64, _I64, _I64, _P, _P,
+                                       ctypes.POINTER(Params), _P, _P, ctypes.POINTER(Stats)]),
+    "knnm_merge_joint_sets": (_I, [_P, _P, _P, _I64, _I64, _I64, _P, ctypes.POINTER(Params),
+                                   _P, _P, ctypes.POINTER(Stats)]),
+    "knnm_build_sets": (_I, [_P, _P, _P, _I64, _I64, ctypes.POINTER(Params), _P, _P,
+                             ctypes.POINTER(Stats)]),
     "knnm_merge_tree": (_I, [_P, _P, _I64, _I, _I, _P, _P, ctypes.POINTER(Params), _P, _P,
                              ctypes.POINTER(Stats)]),
     "knnm_hmerge": (_I, [_P, _P, _I64, _I, _I64, ctypes.POINTER(Params), _P, _P, _P, _I, _P,
@@ -284,6 +290,45 @@ class Context:
         self._check(lib().knnm_merge_joint(self.h, _ptr(S1), n1, _ptr(G1), _ptr(S_new), n2, d,
                                            ctypes.byref(p), _ptr(ids), _ptr(dists),
                                            ctypes.byref(st)))
+        return ids, dists, st.as_dict()
+
+    # ------------------------------------------------------------ sets (Jaccard)
+    # offsets [n+1] int64 and items int32: CUDA tensors (CSR rows, ascending items).
+    def _set_outputs(self, offsets, n, k):
+        import torch
+        return (torch.empty((n, k), dtype=torch.int32, device=offsets.device),
+                torch.empty((n, k), dtype=torch.float32, device=offsets.device))
+
+    def merge_symmetric_sets(self, offsets, items, n1, G1, G2, p: Params):
+        n = offsets.shape[0] - 1
+        ids, dists = self._set_outputs(offsets, n, p.k)
+        st = Stats()
+        self._sync_stream()
+        self._check(lib().knnm_merge_symmetric_sets(self.h, _ptr(offsets), _ptr(items),
+                                                    items.shape[0], n1, n - n1, _ptr(G1),
+                                                    _ptr(G2), ctypes.byref(p), _ptr(ids),
+                                                    _ptr(dists), ctypes.byref(st)))
+        return ids, dists, st.as_dict()
+
+    def merge_joint_sets(self, offsets, items, n1, G1, p: Params):
+        n = offsets.shape[0] - 1
+        ids, dists = self._set_outputs(offsets, n, p.k)
+        st = Stats()
+        self._sync_stream()
+        self._check(lib().knnm_merge_joint_sets(self.h, _ptr(offsets), _ptr(items),
+                                                items.shape[0], n1, n - n1, _ptr(G1),
+                                                ctypes.byref(p), _ptr(ids), _ptr(dists),
+                                                ctypes.byref(st)))
+        return ids, dists, st.as_dict()
+
+    def build_sets(self, offsets, items, p: Params):
+        n = offsets.shape[0] - 1
+        ids, dists = self._set_outputs(offsets, n, p.k)
+        st = Stats()
+        self._sync_stream()
+        self._check(lib().knnm_build_sets(self.h, _ptr(offsets), _ptr(items), items.shape[0], n,
+                                          ctypes.byref(p), _ptr(ids), _ptr(dists),
+                                          ctypes.byref(st)))
         return ids, dists, st.as_dict()
 
     def merge_tree(self, S, part_rows, G, p: Params):
