@@ -438,6 +438,86 @@ def query_recall(torch, X_dev, Q_dev, ids_dev, K=10, extra=48, qchunk=1024, chun
     return hits / (Q_dev.shape[0] * K)
 
 
+def jaccard_recall(torch, off, items, dim, ids_dev, queries, K=10, chunk=16384):
+    """recall@K of set lists: exact Jaccard distances of the sampled rows to all
+    rows from 0/1 blocks (FP32 counts are exact), ties at the K-th distance
+    counted as hits."""
+    n = len(off) - 1
+    lens = torch.from_numpy(np.diff(off)).cuda().float()
+
+    def dense(rows):
+        M = torch.zeros((len(rows), dim), dtype=torch.float32, device="cuda")
+        for r, i in enumerate(rows):
+            M[r, torch.from_numpy(items[off[i]:off[i + 1]].astype(np.int64)).cuda()] = 1.0
+        return M
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    Q = dense(queries)
+    qlen = lens[torch.as_tensor(queries, device="cuda")]
+    D = torch.empty((len(queries), n), device="cuda")
+    for b in range(0, n, chunk):
+        B = dense(range(b, min(n, b + chunk)))
+        inter = Q @ B.T
+        uni = qlen[:, None] + lens[None, b:b + B.shape[0]] - inter
+        D[:, b:b + B.shape[0]] = torch.where(uni == 0, 0.0, 1.0 - inter / uni.clamp_min(1.0))
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    q = torch.as_tensor(queries, device="cuda", dtype=torch.long)
+    D[torch.arange(len(queries), device="cuda"), q] = float("inf")
+    kth = torch.sort(D, dim=1).values[:, K - 1]
+    got = ids_dev[q][:, :K].long()
+    gd = torch.gather(D, 1, got)
+    return (gd <= kth[:, None] + 1e-7).sum().item() / (len(queries) * K)
+
+
+def run_sets(args, name):
+    """Jaccard S-Merge of itemsets (the Kosarak metric of Sec. 5): two halves
+    built by NN-Descent, merged; set rows as CSR arrays on the device."""
+    import torch
+    from paper_1908_00814_gb300 import build as kbuild, knnm
+    kbuild.build()
+    torch.cuda.set_device(0)
+    ctx = knnm.Context(0)
+    w = dict(datagen.WORKLOADS[name])
+    n = args.rows or w["n"]
+    K = w["k"]
+    off, items = datagen.itemsets(n, w["dim"], seed=w["seed"], **w["gen_args"])
+    n1 = n // 2
+    offd = torch.from_numpy(off).cuda()
+    itd = torch.from_numpy(items).cuda()
+    o1 = offd[:n1 + 1].contiguous()
+    o2 = (offd[n1:] - offd[n1]).contiguous()
+    i1 = itd[:off[n1]].contiguous()
+    i2 = itd[off[n1]:].contiguous()
+    bp = knnm.params(k=K, metric="jaccard", max_iters=w["rounds"], delta=0.001, seed=11)
+    G1, _, _ = ctx.build_sets(o1, i1, bp)
+    bp.seed = 12
+    G2, _, _ = ctx.build_sets(o2, i2, bp)
+    p = knnm.params(k=K, metric="jaccard", max_iters=w["rounds"], sample_rate=w["sample_rate"],
+                    delta=0.001, seed=0)
+    ms, out, stats = timed_call(torch, lambda: ctx.merge_symmetric_sets(offd, itd, n1, G1, G2, p),
+                                args.steps, args.warmup)
+    queries = datagen.sample_nodes(n, args.recall_queries, seed=0)
+    recall = jaccard_recall(torch, off, items, w["dim"], out[0], queries)
+    st = stats[-1]
+    line = {"metric": METRIC, "value": n / (ms / 1000.0), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": name, "merge": "symmetric (Alg. 1), Jaccard on sets",
+                       "n": n, "dim": w["dim"], "mean_set_size": float(len(items) / n),
+                       "k": K, "metric": "jaccard", "max_rounds": w["rounds"],
+                       "sample_rate": w["sample_rate"], "delta": 0.001,
+                       "inputs": "NN-Descent builds of each half (library), made before timing",
+                       "parallelism": "replicas"},
+            "recall_at_10": recall, "recall_queries": len(queries), "rounds": st["rounds"],
+            "dist_evals": sum(st["dist_evals"]), "ms_join_per_step": sum(st["ms_join"]),
+            "ms_sample_per_step": sum(st["ms_sample"]),
+            "ms_update_per_step": sum(st["ms_update"])}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def run_search(args, name):
     """Graph diversification (Alg. 3) of an H-Merge hierarchy and the top-down
     search on it (Sec. 3.4): 10,000 held-out queries, recall@10 and queries/s
@@ -861,7 +941,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "jmerge_gmm_2m_d96_k16_cos", "smerge_gist_1m_d960_k20",
                              "hmerge_sift_1m_d128_k20", "hsearch_sift_1m_d128_k20",
-                             "smerge_nuswide_260k_d500_k20_chi2"],
+                             "smerge_nuswide_260k_d500_k20_chi2",
+                             "smerge_kosarak_75k_k20_jaccard"],
                     help="another merge workload (one JSON line of its own)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-batches", type=int, default=16)
@@ -880,6 +961,8 @@ def main():
         return run_reference(args, w)
     if args.workload == "hsearch_sift_1m_d128_k20":
         return run_search(args, args.workload)
+    if args.workload == "smerge_kosarak_75k_k20_jaccard":
+        return run_sets(args, args.workload)
     if args.workload != WORKLOAD:
         return run_other(args, args.workload)
     return run_ours(args, w)

@@ -130,12 +130,12 @@ def bovw_like(n: int, d: int = 500, n_topics: int = 64, words: float = 60.0, see
 
 
 def itemsets(n: int, dim: int = 27983, n_types: int = 2000, core: int = 40,
-             mean_len: float = 20.0, seed: int = 0):
+             mean_len: float = 20.0, p_core: float = 0.8, seed: int = 0):
     """Kosarak-like itemsets (Jaccard metric) as CSR arrays (offsets int64
     [n+1], items int32, ascending within a row): items have Zipf(1.2)
     popularity; each row picks one of n_types basket types with a core of
     `core` items and draws a log-normal number of items (median mean_len,
-    sigma 0.6, 1..200), four in five from its type's core, the rest by
+    sigma 0.6, 1..200), a share p_core from its type's core, the rest by
     popularity."""
     rng = _rng(seed)
     pop = 1.0 / np.arange(1, dim + 1) ** 1.2
@@ -144,12 +144,13 @@ def itemsets(n: int, dim: int = 27983, n_types: int = 2000, core: int = 40,
     cores = [perm[rng.choice(dim, size=core, replace=False, p=pop)] for _ in range(n_types)]
     lens = np.clip(np.rint(rng.lognormal(np.log(mean_len), 0.6, size=n)), 1, 200).astype(int)
     types = rng.integers(0, n_types, size=n)
+    k_core = np.minimum(core, rng.binomial(lens, p_core))
+    popular = perm[rng.choice(dim, size=int((lens - k_core).sum()), p=pop)]
+    starts = np.concatenate([[0], np.cumsum(lens - k_core)])
     rows = []
     for i in range(n):
-        k_core = min(core, int(rng.binomial(lens[i], 0.8)))
-        a = rng.choice(cores[types[i]], size=k_core, replace=False)
-        b = perm[rng.choice(dim, size=lens[i] - k_core, p=pop)]
-        rows.append(np.unique(np.concatenate([a, b])))
+        a = cores[types[i]][rng.permutation(core)[:k_core[i]]]
+        rows.append(np.unique(np.concatenate([a, popular[starts[i]:starts[i + 1]]])))
     offsets = np.zeros(n + 1, np.int64)
     offsets[1:] = np.cumsum([len(r) for r in rows])
     items = np.concatenate(rows).astype(np.int32) if n else np.zeros(0, np.int32)
@@ -215,6 +216,10 @@ WORKLOADS = {
                                               d=500, k=20, metric="chi2", rounds=20,
                                               sample_rate=0.5, seed=1008,
                                               gen_args=dict(words=2000.0)),
+    "smerge_kosarak_75k_k20_jaccard": dict(kind="sets", gen="itemsets", n=74_962, dim=27_983,
+                                           k=20, metric="jaccard", rounds=20, sample_rate=0.5,
+                                           seed=1009,
+                                           gen_args=dict(n_types=1500, core=24, p_core=0.9)),
     "smerge_gist_1m_d960_k20": dict(kind="symmetric", gen="gist_like", n=1_000_000, d=960,
                                     k=20, metric="l1", rounds=10, sample_rate=0.5, seed=1005,
                                     gen_args={}),
