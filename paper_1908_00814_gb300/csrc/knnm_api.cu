@@ -1062,7 +1062,6 @@ extern "C" int knnm_hmerge(knnm_ctx* ctx, const float* S, int64_t n, int d, int6
     total.ms_final += ms.ms_final;
   };
   // layer outputs: copy the k/2 lists of an m-row layer when it is asked for
-  int64_t layer_off = 0;
   auto save_layer = [&](int64_t m, const int32_t* lists) {
     int64_t off = 0;
     for (int l = 0; l < n_layers; ++l) {
@@ -1074,7 +1073,6 @@ extern "C" int knnm_hmerge(knnm_ctx* ctx, const float* S, int64_t n, int d, int6
     }
     return true;
   };
-  (void)layer_off;
   int64_t m = first_rows;
   int cur = 0, level = 0;
   {
