@@ -127,6 +127,14 @@ int knnm_set_option(knnm_ctx* ctx, int option, int value);
 const char* knnm_last_error(const knnm_ctx* ctx);
 /* Static name of an error code. */
 const char* knnm_strerror(int code);
+
+/* The library's counter-based hash H(seed, t, stream, owner, member): five
+ * chained SplitMix64 steps (Steele, Lea and Flood, OOPSLA 2014), each
+ * absorbing one word by xor.  Every random choice of the library is a value
+ * of H; e.g. merge j of level l of a merge tree runs with seed
+ * H(seed, l, 6, j, 0).  Host function, no context. */
+uint64_t knnm_hash64(uint64_t seed, uint64_t t, uint64_t stream, uint64_t owner,
+                     uint64_t member);
 /* Fills `p` with the defaults: K=20, L2, FP32, 10 rounds, rho=0.5, r=0.5,
  * delta=0.001, seed=0. */
 void knnm_default_params(knnm_params* p);

@@ -726,6 +726,11 @@ extern "C" int knnm_set_option(knnm_ctx* c, int option, int value) {
   return KNNM_ERR_INVALID;
 }
 
+extern "C" uint64_t knnm_hash64(uint64_t seed, uint64_t t, uint64_t stream, uint64_t owner,
+                                uint64_t member) {
+  return mix_step(hash_prefix(seed, t, stream, owner) ^ member);
+}
+
 extern "C" const char* knnm_strerror(int code) {
   switch (code) {
     case KNNM_OK: return "ok";

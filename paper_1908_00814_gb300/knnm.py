@@ -115,6 +115,7 @@ SIGNATURES = {
     "knnm_last_error": (ctypes.c_char_p, [_P]),
     "knnm_set_option": (_I, [_P, _I, _I]),
     "knnm_strerror": (ctypes.c_char_p, [_I]),
+    "knnm_hash64": (_U64, [_U64, _U64, _U64, _U64, _U64]),
     "knnm_default_params": (None, [ctypes.POINTER(Params)]),
     "knnm_merge_symmetric": (_I, [_P, _P, _I64, _P, _P, _I64, _P, _I, ctypes.POINTER(Params),
                                   _P, _P, ctypes.POINTER(Stats)]),
@@ -185,6 +186,12 @@ class KnnmError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERRORS.get(code, code)}: {msg}")
         self.code = code
+
+
+def hash64(seed, t, stream, owner, member) -> int:
+    """The library's counter-based hash H(seed, t, stream, owner, member)."""
+    m = (1 << 64) - 1
+    return int(lib().knnm_hash64(seed & m, t & m, stream & m, owner & m, member & m))
 
 
 def params(k=20, metric="l2", precision="fp32", max_iters=10, sample_rate=0.5, keep_ratio=0.5,
