@@ -211,6 +211,8 @@ __global__ void __launch_bounds__(BLOCK) k_init(InitArgs a) {
     uint64_t kept = KEY_EMPTY;
     int want;
     int64_t base, n_src;
+    uint64_t pre_dkey = KEY_EMPTY;  // the drawn members' keys when computed with the list
+    bool have_dkey = false;
     if (in) {
       // Divide: recompute distances of the input list, sort, keep the top K_keep.
       int32_t loc = lane < K ? in[lane] : -1;
@@ -222,8 +224,26 @@ __global__ void __launch_bounds__(BLOCK) k_init(InitArgs a) {
       }
       if (__any_sync(FULL, bad) && lane == 0) raise_err(a.ctr, DERR_BAD_ID, i);
       if (__any_sync(FULL, dup) && lane == 0) raise_err(a.ctr, DERR_DUP_ID, i);
+      want = Kr;
+      base = i < a.n1 ? a.n1 : 0;
+      n_src = i < a.n1 ? a.N - a.n1 : a.n1;
       uint64_t key = KEY_EMPTY;
-      if (a.vec4) {
+      if (a.vec4 && K + want <= 32) {
+        // The random members do not depend on the list, so the listed rows
+        // (lanes 0..K-1) and the drawn rows (lanes K..K+want-1) are staged and
+        // compared in one pass.
+        const int32_t drawn = draw_random(a.seed, i, base, n_src, want, K);
+        const int32_t dsh = __shfl_sync(FULL, drawn, (lane - K) & 31);
+        int32_t g = -1;
+        if (lane < K) g = !bad ? (int32_t)(own_base + loc) : -1;
+        else if (lane < K + want) g = dsh;
+        const float dist = staged_dist<METRIC>(a.rows, i, g, K + want, a.norms, wbuf);
+        const uint64_t kk = g >= 0 ? make_key(dist, g) : KEY_EMPTY;
+        key = lane < K ? kk : KEY_EMPTY;
+        const uint64_t dk = __shfl_sync(FULL, kk, (lane + K) & 31);
+        pre_dkey = lane < want ? dk : KEY_EMPTY;
+        have_dkey = true;
+      } else if (a.vec4) {
         const int32_t g = (lane < K && !bad) ? (int32_t)(own_base + loc) : -1;
         const float dist = staged_dist<METRIC>(a.rows, i, g, K, a.norms, wbuf);
         if (g >= 0) key = make_key(dist, g);
@@ -234,9 +254,6 @@ __global__ void __launch_bounds__(BLOCK) k_init(InitArgs a) {
       key = warp_sort32(key);
       if (lane >= Kk && lane < K) a.rear[(size_t)i * Kr + (lane - Kk)] = key;
       kept = lane < Kk ? key : KEY_EMPTY;
-      want = Kr;
-      base = i < a.n1 ? a.n1 : 0;
-      n_src = i < a.n1 ? a.N - a.n1 : a.n1;
     } else {
       // Initialize (Alg. 2): K random members of S1 u S2.
       want = K;
@@ -244,14 +261,16 @@ __global__ void __launch_bounds__(BLOCK) k_init(InitArgs a) {
       n_src = a.N;
       if (Kr > 0 && lane < Kr) a.rear[(size_t)i * Kr + lane] = KEY_EMPTY;
     }
-    int32_t drawn = draw_random(a.seed, i, base, n_src, want, K);
-    uint64_t dkey = KEY_EMPTY;
-    if (a.vec4) {
-      const int32_t g = lane < want ? drawn : -1;
-      const float dist = staged_dist<METRIC>(a.rows, i, g, want, a.norms, wbuf);
-      if (g >= 0) dkey = make_key(dist, g);
-    } else if (lane < want) {
-      dkey = make_key(dist_rows<METRIC>(a.rows, i, drawn, a.norms, a.vec4), drawn);
+    uint64_t dkey = pre_dkey;
+    if (!have_dkey) {
+      const int32_t drawn = draw_random(a.seed, i, base, n_src, want, K);
+      if (a.vec4) {
+        const int32_t g = lane < want ? drawn : -1;
+        const float dist = staged_dist<METRIC>(a.rows, i, g, want, a.norms, wbuf);
+        if (g >= 0) dkey = make_key(dist, g);
+      } else if (lane < want) {
+        dkey = make_key(dist_rows<METRIC>(a.rows, i, drawn, a.norms, a.vec4), drawn);
+      }
     }
     int first = in ? Kk : 0;
     uint64_t shifted = __shfl_sync(FULL, dkey, (lane - first) & 31);
