@@ -683,7 +683,7 @@ __global__ void __launch_bounds__(256) k_scan_apply(const int32_t* cnt, int64_t 
 __global__ void k_scatter(const int32_t* prop_tgt, const uint64_t* prop_key,
                           const unsigned long long* region_cnt, uint64_t region_cap,
                           int32_t* cnt, const unsigned long long* offs, uint64_t* bucket) {
-  constexpr int U = 4;  // proposals per thread in flight: independent atomics overlap
+  constexpr int U = 8;  // proposals per thread in flight: independent atomics overlap
   const uint64_t n = region_cnt[blockIdx.x];
   const uint64_t base = (uint64_t)blockIdx.x * region_cap;
   const uint64_t step = (uint64_t)blockDim.x * gridDim.y * U;
@@ -697,11 +697,14 @@ __global__ void k_scatter(const int32_t* prop_tgt, const uint64_t* prop_key,
       tgt[u] = o < n ? prop_tgt[base + o] : -1;
       key[u] = o < n ? prop_key[base + o] : 0ull;
     }
+    unsigned long long ob[U];  // bucket starts, loaded while the atomics are in flight
+#pragma unroll
+    for (int u = 0; u < U; ++u) ob[u] = tgt[u] >= 0 ? offs[tgt[u]] : 0ull;
 #pragma unroll
     for (int u = 0; u < U; ++u) pos[u] = tgt[u] >= 0 ? atomicSub(&cnt[tgt[u]], 1) - 1 : 0;
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (tgt[u] >= 0) bucket[offs[tgt[u]] + (uint64_t)pos[u]] = key[u];
+      if (tgt[u] >= 0) bucket[ob[u] + (uint64_t)pos[u]] = key[u];
   }
 }
 
