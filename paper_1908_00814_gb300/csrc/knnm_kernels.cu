@@ -403,14 +403,16 @@ __global__ void __launch_bounds__(BLOCK) k_sample_scatter(SampleArgs a) {
     const int32_t vn = hn ? a.new_ids[(size_t)u * a.cap_new + lane] : 0;
     const int32_t vo = lane < of ? a.old_ids[(size_t)u * a.cap_old + lane] : 0;
     const bool ho = lane < of && (!a.active_only || active_by_bucket(a, vo));
-    // both slot claims in flight before either store
+    // bucket starts, keys and both slot claims in flight before either store
+    const unsigned long long bn = hn ? a.roffs[2 * (size_t)vn] : 0ull;
+    const unsigned long long bo = ho ? a.roffs[2 * (size_t)vo + 1] : 0ull;
     const int pn = hn ? atomicSub(&a.rcnt[2 * (size_t)vn], 1) - 1 : 0;
     const int po = ho ? atomicSub(&a.rcnt[2 * (size_t)vo + 1], 1) - 1 : 0;
     if (hn)
-      a.rbucket[a.roffs[2 * (size_t)vn] + (uint64_t)pn] =
+      a.rbucket[bn + (uint64_t)pn] =
           sampling_key(hash_prefix(a.seed, t, STREAM_REV_NEW, (uint64_t)vn), (int32_t)u);
     if (ho)
-      a.rbucket[a.roffs[2 * (size_t)vo + 1] + (uint64_t)po] =
+      a.rbucket[bo + (uint64_t)po] =
           sampling_key(hash_prefix(a.seed, t, STREAM_REV_OLD, (uint64_t)vo), (int32_t)u);
   }
 }
