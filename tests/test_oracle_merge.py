@@ -334,3 +334,29 @@ def test_final_merge_keeps_best_distinct(orc):
     st = orc.State(ids, dists, np.zeros_like(ids, dtype=np.uint8), rid, rd)
     oi, od = orc.final(st)
     assert oi.tolist() == [[3, 1, 7]] and od.tolist() == [[1.0, 2.0, 3.0]]
+
+
+def _metric_data(metric, n, seed):
+    if metric == 4:   # chi-square: non-negative histograms
+        return datagen.bovw_like(n, 12, n_topics=3, words=30.0, seed=seed)
+    if metric == 5:   # Jaccard: sets as 0/1 rows
+        off, items = datagen.itemsets(n, 40, n_types=4, core=10, mean_len=6.0, seed=seed)
+        return datagen.sets_to_rows(off, items, 40)
+    return datagen.gaussian_mixture(n, 5, seed=seed, normalize=metric == 2)
+
+
+@pytest.mark.parametrize("metric", [0, 1, 2, 3, 4, 5])
+def test_exact_cases_hold_for_every_metric(orc, metric):
+    """k = n - 1 builds and brute-force merges of exact graphs give the exact
+    graph under every metric (the merge steps do not depend on the metric)."""
+    X = _metric_data(metric, 9, 3)
+    ids, dists, _ = orc.build_graph(X, 8, metric=metric, max_iters=3)
+    ref_ids, ref_d = orc.bruteforce_knn(X, 8, metric=metric)
+    assert np.array_equal(ids, ref_ids) and np.array_equal(dists, ref_d)
+    X = _metric_data(metric, 80, 5)
+    n1, K = 40, 6
+    G1, _ = orc.bruteforce_knn(X[:n1], K, metric=metric)
+    G2, _ = orc.bruteforce_knn(X[n1:], K, metric=metric)
+    ids, dists = orc.bruteforce_merge(X[:n1], G1, X[n1:], G2, K, metric=metric)
+    ref_ids, ref_d = orc.bruteforce_knn(X, K, metric=metric)
+    assert np.array_equal(ids, ref_ids) and np.array_equal(dists, ref_d)
