@@ -178,7 +178,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   auto t_wall0 = std::chrono::steady_clock::now();
   if (!ctx) return KNNM_ERR_INVALID;
   ctx->err[0] = 0;
-  Derived D;
+  Derived D{};
   int rc = derive(ctx, params, in.mode, in.n1, &D);
   if (rc) return rc;
   const int64_t N = in.n1 + in.n2;
@@ -1183,7 +1183,7 @@ extern "C" int knnm_step_init(knnm_ctx* ctx, int mode, const float* X1, int64_t 
   ctx->err[0] = 0;
   int rc = check_rows(ctx, X1, nx1, X2, N, d);
   if (rc) return rc;
-  Derived D;
+  Derived D{};
   rc = derive(ctx, params, mode, set_split, &D);
   if (rc) return rc;
   if (mode != SYMMETRIC && mode != JOINT) return fail(ctx, KNNM_ERR_INVALID, "bad mode");
