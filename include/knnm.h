@@ -9,6 +9,14 @@
  *     S1 is expanded with a raw set S2.
  *   - knnm_build: J-Merge with an empty existing graph, i.e. NN-Descent, used
  *     to make input graphs.
+ *   - knnm_*_sets: the same three merges on itemsets under the Jaccard
+ *     distance (the paper's Kosarak experiments), rows as CSR arrays.
+ *   - knnm_merge_tree: a graph over many parts by levels of pairwise S-Merges;
+ *     knnm_hmerge: the H-Merge hierarchy (Sec. 3.3).
+ *   - knnm_diversify, knnm_search(_prepare): graph diversification (Alg. 3)
+ *     and the top-down search on the hierarchy (Sec. 3.4).
+ *   - knnm_server_*: J-Merge applied to a stream of raw batches against a
+ *     resident graph.
  * plus one entry point per step of a merge round (knnm_step_*) so that each
  * step can be checked on its own.
  *
