@@ -3,7 +3,7 @@
 Each test pins the oracle to something the paper or the mathematics fixes:
 a round traced by hand, the brute-force merge of Sec. 1, exactness when the
 random init covers the whole other set, the convergence invariant of Sec. 3.4
-(phi non-increasing), the fixpoint that "no new update happens" defines, the
+(phi non-increasing), the fixpoint where a round changes no list, the
 set masks of Alg. 1/2, and brute-force checks of the sampling rule.
 """
 import json
@@ -243,7 +243,7 @@ def test_round_invariants(orc, mode):
 
 @pytest.mark.parametrize("mode", ["symmetric", "joint"])
 def test_literal_fixpoint(orc, mode):
-    """Alg. 1/2 stop when no new update happens: at that point no allowed pair
+    """Alg. 1/2 stop once a round changes no list: at that point no allowed pair
     of any G-script[u] = G[u] u Reverse(G)[u] can enter either endpoint's list."""
     X, n1, n2, K = _small_split(seed=21, n1=60, n2=50, d=4, K=5)
     G1, _ = orc.bruteforce_knn(X[:n1], K)
