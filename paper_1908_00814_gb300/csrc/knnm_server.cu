@@ -385,7 +385,8 @@ extern "C" int knnm_server_create(int device, const float* Sv, int64_t n, const 
   *out = nullptr;
   if (params->k < 1 || params->k > 32 || d < 1 || n < params->k + 1 || cfg->slots < 1 ||
       cfg->slots > 64 || cfg->capacity_rows < n || cfg->capacity_rows > 0x7FFFFFFFLL ||
-      cfg->max_batch_rows < 1)
+      cfg->max_batch_rows < 1 || params->metric < 0 ||
+      params->metric > 4)  // dense rows only: the Jaccard metric takes set rows
     return KNNM_ERR_INVALID;
   knnm_server* S = new knnm_server();
   S->device = device;
