@@ -113,6 +113,8 @@ typedef struct {
   float ms_init, ms_rounds, ms_final;     /* device time of init, all rounds, final merge */
   float ms_total;                         /* wall time of the call */
   uint64_t tc_rounds;                     /* bit t-1 set: round t ran the tensor-core join */
+  int64_t spilled[KNNM_MAX_ROUNDS];       /* proposals inserted straight into the lists
+                                             because the join block's buffer was full */
 } knnm_stats;
 
 typedef struct knnm_ctx knnm_ctx;
@@ -124,12 +126,33 @@ int knnm_create(knnm_ctx** out, int device, void* cuda_stream);
 int knnm_destroy(knnm_ctx* ctx);
 /* Rebinds the context to another stream of the same device. */
 int knnm_set_stream(knnm_ctx* ctx, void* cuda_stream);
-/* Context options.  KNNM_OPT_GRAPHS (default 0): when 1, each local-join round
- * of a whole-merge call (sampler, join, top-k update) is captured once into a
- * CUDA graph and replayed, one graph launch per round.  Results are identical;
- * knnm_stats then times each round as a whole (in ms_join; ms_sample and
- * ms_update stay 0). */
-enum { KNNM_OPT_GRAPHS = 1 };
+/* Context options (knnm_set_option; KNNM_ERR_INVALID for an unknown option or
+ * a value out of range):
+ *   KNNM_OPT_GRAPHS (default 0): when 1, each local-join round of a whole-merge
+ *     call (sampler, join, top-k update) is captured once into a CUDA graph
+ *     and replayed, one graph launch per round.  Results are identical;
+ *     knnm_stats then times each round as a whole (in ms_join; ms_sample and
+ *     ms_update stay 0).
+ *   KNNM_OPT_REGION_CAP (default 0, >= 0): proposals each join block buffers
+ *     before it inserts the rest straight into the live lists by ordered slot
+ *     insertion (the same UpdateNN, without the bucket pass); 0 sizes the
+ *     buffers from N (256 proposals per row in all, at least 1,024 per block).
+ *     Results do not depend on it; small values force the direct-insert path.
+ *   KNNM_OPT_WAIT_POLLS (default -1, >= -1): polls before a device-side wait of
+ *     the join for its staged rows gives up (-1: 2^22).  A wait that gives up
+ *     makes the call return KNNM_ERR_DEVICE with error bit 0x8 in its message;
+ *     the kernel first lets its copies in flight land, so the context stays
+ *     usable.  0 makes every such wait give up at once (tests of that path).
+ *   KNNM_OPT_FAIL_ALLOC (default 0, >= 0): the next `value` scratch
+ *     reservations of the context fail with KNNM_ERR_NOMEM as if the device
+ *     were out of memory (host-side fault injection for tests); the context
+ *     and its existing scratch stay usable. */
+enum {
+  KNNM_OPT_GRAPHS = 1,
+  KNNM_OPT_REGION_CAP = 2,
+  KNNM_OPT_WAIT_POLLS = 3,
+  KNNM_OPT_FAIL_ALLOC = 4
+};
 int knnm_set_option(knnm_ctx* ctx, int option, int value);
 /* Message of the context's last failure ("" if none).  Owned by the context. */
 const char* knnm_last_error(const knnm_ctx* ctx);
@@ -446,15 +469,20 @@ int knnm_step_sample(knnm_ctx* ctx, int64_t N, int K, const int32_t* ids, const 
  * on the calling thread's current device.  Its scratch (packed list keys and
  * the two reverse-sample slot arrays) is one fixed __device__ array of
  * KNNM_NOALLOC_SCRATCH_BYTES inside the library, held by every GPU that loads
- * the library until the process exits.  Limit: N*(K + 2*s)*8 + 256 bytes must
- * fit in it (with K = 20, s = 10 that is about 26,000 rows); larger inputs
- * return KNNM_ERR_INVALID before anything is launched.  The call allocates
- * nothing, neither device nor host memory.  The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture starts.  Every call shares the one array: it
- * resets what must start empty, but calls whose work overlaps on the GPU (other
- * threads, other streams) race on it and must be serialized by the caller.
- * Returns after the stream has finished the call's work. */
+ * the library until the process exits.  Limit, with a(x) = x rounded up to a
+ * multiple of 256:  a(N*K*8) + 2*a(N*s*8) + 256 <= KNNM_NOALLOC_SCRATCH_BYTES
+ * (with K = 20, s = 10 that is about 26,000 rows); larger inputs, and N above
+ * 2^31 - 1, return KNNM_ERR_INVALID before anything is launched.  The call
+ * allocates nothing, neither device nor host memory.  Each call looks up the
+ * array's device address (cudaGetSymbolAddress); the first lookup on a device
+ * loads the library's device code there, so make the first call on each
+ * device before any stream capture starts.  Every call ends by waiting for its
+ * stream (cudaStreamSynchronize), so no call may be made while a stream
+ * capture is active on that stream or, in global capture mode, anywhere in the
+ * process.  Every call shares the one array: it resets what must start empty,
+ * but calls whose work overlaps on the GPU (other threads, other streams) race
+ * on it and must be serialized by the caller.  Returns after the stream has
+ * finished the call's work. */
 int knnm_step_sample_noalloc(void* cuda_stream, int64_t N, int K, const int32_t* ids,
                              const float* dists, uint8_t* flags, uint64_t seed, int t, int s,
                              int cap_new, int cap_old, int32_t* new_ids, int32_t* new_cnt,

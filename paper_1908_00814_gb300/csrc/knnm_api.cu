@@ -22,6 +22,9 @@ struct knnm_ctx {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t rev[4] = {nullptr, nullptr, nullptr, nullptr};  // per-round phases
   int use_graphs = 0;  // replay each round as one captured CUDA graph
+  uint64_t region_cap = 0;    // proposals per join-block region (0: sized from N)
+  uint32_t wait_polls = WAIT_LIMIT;  // polls before a device wait of the join gives up
+  int fail_alloc = 0;         // scratch reservations still to fail (host-side injection)
   cudaStream_t cap_stream = nullptr;  // private stream the round graph is captured on
   char err[512] = {0};
 };
@@ -59,6 +62,11 @@ struct Carver {
 };
 
 int ensure_arena(knnm_ctx* ctx, size_t bytes) {
+  if (ctx->fail_alloc > 0) {
+    --ctx->fail_alloc;
+    return fail(ctx, KNNM_ERR_NOMEM, "cannot reserve %zu bytes of device scratch (injected failure)",
+                bytes);
+  }
   if (bytes <= ctx->arena_bytes) return KNNM_OK;
   if (ctx->arena) {
     cudaStreamSynchronize(ctx->stream);
@@ -255,6 +263,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   // joins of the per-round choice share one allocation.
   const uint64_t per_node = 256;
   auto cap_for = [&](int regions_of) {
+    if (ctx->region_cap) return ctx->region_cap;
     uint64_t c = ((uint64_t)N * per_node + regions_of - 1) / regions_of;
     return c < 1024 ? (uint64_t)1024 : c;
   };
@@ -497,6 +506,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   ja.aux = P.aux;
   ja.rmax = P.rmax;
   ja.use_bulk = use_bulk ? 1 : 0;
+  ja.wait_polls = ctx->wait_polls;
   MergeArgs ma{N, K, P.keys, P.prev, P.flags, P.pcnt, P.offs, P.bucket, P.ctr};
   KNNM_CUDA(cudaMemsetAsync(P.pcnt, 0, (size_t)N * 4, st));
   KNNM_CUDA(cudaMemsetAsync(P.rcnt, 0, (size_t)N * 8, st));
@@ -611,6 +621,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     local.proposals[t - 1] = (int64_t)h.proposals;
     local.reranked[t - 1] = (int64_t)h.reranked;
     local.gathered[t - 1] = (int64_t)h.gathered;
+    local.spilled[t - 1] = (int64_t)h.overflow;
     if (use_tc) local.tc_rounds |= 1ull << (t - 1);
     if (graphs) {
       cudaEventElapsedTime(&local.ms_join[t - 1], ctx->rev[0], ctx->rev[3]);
@@ -721,6 +732,18 @@ extern "C" int knnm_set_option(knnm_ctx* c, int option, int value) {
   if (!c) return KNNM_ERR_INVALID;
   if (option == KNNM_OPT_GRAPHS) {
     c->use_graphs = value ? 1 : 0;
+    return KNNM_OK;
+  }
+  if (option == KNNM_OPT_REGION_CAP && value >= 0) {
+    c->region_cap = (uint64_t)value;
+    return KNNM_OK;
+  }
+  if (option == KNNM_OPT_WAIT_POLLS && value >= -1) {
+    c->wait_polls = value < 0 ? WAIT_LIMIT : (uint32_t)value;
+    return KNNM_OK;
+  }
+  if (option == KNNM_OPT_FAIL_ALLOC && value >= 0) {
+    c->fail_alloc = value;
     return KNNM_OK;
   }
   return KNNM_ERR_INVALID;
@@ -946,6 +969,7 @@ extern "C" int knnm_merge_tree(knnm_ctx* ctx, const float* S, int64_t n, int d, 
         total_st.proposals[level] += ms.proposals[t];
         total_st.reranked[level] += ms.reranked[t];
         total_st.gathered[level] += ms.gathered[t];
+        total_st.spilled[level] += ms.spilled[t];
         total_st.ms_sample[level] += ms.ms_sample[t];
         total_st.ms_join[level] += ms.ms_join[t];
         total_st.ms_update[level] += ms.ms_update[t];
@@ -1057,6 +1081,7 @@ extern "C" int knnm_hmerge(knnm_ctx* ctx, const float* S, int64_t n, int d, int6
       total.proposals[level] += ms.proposals[t];
       total.reranked[level] += ms.reranked[t];
       total.gathered[level] += ms.gathered[t];
+      total.spilled[level] += ms.spilled[t];
       total.ms_sample[level] += ms.ms_sample[t];
       total.ms_join[level] += ms.ms_join[t];
       total.ms_update[level] += ms.ms_update[t];
@@ -1336,6 +1361,7 @@ extern "C" int knnm_step_join(knnm_ctx* ctx, int mode, const float* X1, int64_t 
   if (per_node > 512) per_node = 512;
   uint64_t region_cap = ((uint64_t)N * per_node + regions - 1) / regions;
   if (region_cap < 256) region_cap = 256;
+  if (ctx->region_cap) region_cap = ctx->region_cap;
   uint64_t *keys, *prev, *pkey, *bucket;
   int32_t *ptgt, *pcnt;
   unsigned long long *rcnt, *offs, *tsum, *total;
@@ -1408,6 +1434,7 @@ extern "C" int knnm_step_join(knnm_ctx* ctx, int mode, const float* X1, int64_t 
   ja.aux = aux;
   ja.rmax = rmax;
   ja.use_bulk = (d % 4 == 0 && aligned16(rows.X1) && aligned16(rows.X2)) ? 1 : 0;
+  ja.wait_polls = ctx->wait_polls;
   KNNM_CUDA(cudaMemsetAsync(pcnt, 0, (size_t)N * 4, st));
   if (jp.pipe) {
     KNNM_CUDA(launch_build_records(N, K, keys, params->metric == KNNM_COS ? norms : nullptr,

@@ -482,6 +482,7 @@ struct JoinArgs {
   const float4* aux;        // per-row {bf16 squared norm, bf16 rounding-error norm, bf16 norm, canonical norm}
   const float* rmax;        // per-row max |x| of exact-integer rows, -1 otherwise
   int use_bulk;             // rows may be fetched with bulk async copies
+  uint32_t wait_polls = WAIT_LIMIT;  // polls before an mbarrier wait gives up
 };
 // Pipelined join (knnm_join_pipe.cu): per-node candidate records and rows are
 // staged by a producer warp through NS shared-memory stages.

@@ -152,7 +152,7 @@ __device__ __forceinline__ bool stage_rows(const JoinArgs& a, JoinShared& S, int
       bulk_g2s(dst + (size_t)r * stride_bytes, row_ptr(S.cid[r]) + off,
                (uint32_t)(elems * sizeof(T)), S.bar);
   }
-  bool ok = mbar_wait_bounded(S.bar, phase, WAIT_LIMIT);
+  bool ok = mbar_wait_bounded(S.bar, phase, a.wait_polls);
   if (!ok) {
     if (threadIdx.x == 0) atomicOr(&a.ctr->err, (unsigned long long)DERR_WAIT_TIMEOUT);
     mbar_wait_bounded(S.bar, phase, WAIT_LIMIT);

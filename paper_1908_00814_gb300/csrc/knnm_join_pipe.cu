@@ -190,7 +190,14 @@ __device__ __forceinline__ void cp16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
                : "memory");
 }
-__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// Every cp.async of this lane has landed (committed or not).
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Bounded wait of the whole warp: true only when every lane saw the phase
+// complete, so that a timeout sends all lanes down the same path.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  return __all_sync(FULL, mbar_wait_bounded(bar, parity, limit));
+}
 
 struct Rec {
   const int32_t* cid;
@@ -489,11 +496,21 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) k_join_ring(JoinArgs a, Pip
   auto slot_of = [&](int64_t j) { return (int)(j % NREC); };
   auto par_of = [&](int64_t j) { return (uint32_t)((j / NREC) & 1); };
   auto rec_at = [&](int64_t j) { return recs + (size_t)slot_of(j) * RB; };
+  // Phases armed but not yet waited for, per slot (bit x) with their parity:
+  // after a timeout they are waited out before the warp leaves, so that no
+  // copy or arrival is still in flight into the block's shared memory.
+  unsigned rec_pend = 0, rec_parb = 0, row_pend = 0, row_parb = 0;
+  auto arm = [&](unsigned& pend, unsigned& parb, int64_t j) {
+    const int x = slot_of(j);
+    pend |= 1u << x;
+    parb = (parb & ~(1u << x)) | (par_of(j) << x);
+  };
   auto fetch_rec = [&](int64_t j) {
     const unsigned char* src = P.rec + (size_t)(g0 + j * GW) * RB;
     unsigned char* dst = rec_at(j);
     for (int c = lane; c < (RB >> 4); c += 32) cp16(dst + c * 16, src + c * 16);
     cp_arrive(recbar + slot_of(j));
+    arm(rec_pend, rec_parb, j);
   };
   auto fetch_rows = [&](int64_t j, int base, int M, bool staged) {
     if (staged) {
@@ -512,6 +529,7 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) k_join_ring(JoinArgs a, Pip
       }
     }
     cp_arrive(rowbar + slot_of(j));
+    arm(row_pend, row_parb, j);
   };
 
   // prologue: records of the first NREC - 1 nodes
@@ -527,10 +545,11 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) k_join_ring(JoinArgs a, Pip
     // fetch rows of nodes j .. j + AHEAD while their records are in and the ring has room
     while (next_rows < count && next_rows <= j + AHEAD) {
       const int sl = slot_of(next_rows);
-      if (!mbar_wait_bounded(recbar + sl, par_of(next_rows), WAIT_LIMIT)) {
+      if (!warp_wait(recbar + sl, par_of(next_rows), a.wait_polls)) {
         failed = true;
         break;
       }
+      rec_pend &= ~(1u << sl);
       __syncwarp();
       const Rec rn = read_rec(a, rec_at(next_rows), P.cap);
       const bool st = rn.nn > 0 && rn.M > 1;
@@ -549,10 +568,11 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) k_join_ring(JoinArgs a, Pip
     }
     if (failed) break;
     const int sl = slot_of(j);
-    if (!mbar_wait_bounded(rowbar + sl, par_of(j), WAIT_LIMIT)) {
+    if (!warp_wait(rowbar + sl, par_of(j), a.wait_polls)) {
       failed = true;
       break;
     }
+    row_pend &= ~(1u << sl);
     __syncwarp();
     // the record slot of node j - 1 is free: fetch the record of node j + NREC - 1
     if (j + NREC - 1 < count) fetch_rec(j + NREC - 1);
@@ -583,8 +603,16 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) k_join_ring(JoinArgs a, Pip
     __syncwarp();
     ring_head += used;
   }
-  if (failed && lane == 0) atomicOr(&a.ctr->err, (unsigned long long)DERR_WAIT_TIMEOUT);
   cp_wait_all();
+  if (failed) {
+    if (lane == 0) atomicOr(&a.ctr->err, (unsigned long long)DERR_WAIT_TIMEOUT);
+    // the copies have landed; let their arrivals land too (bounded as well)
+#pragma unroll
+    for (int x = 0; x < NREC; ++x) {
+      if ((rec_pend >> x) & 1u) warp_wait(recbar + x, (rec_parb >> x) & 1u, WAIT_LIMIT);
+      if ((row_pend >> x) & 1u) warp_wait(rowbar + x, (row_parb >> x) & 1u, WAIT_LIMIT);
+    }
+  }
   for (int o = 16; o > 0; o >>= 1) {
     evals += __shfl_xor_sync(FULL, evals, o);
     gathered += __shfl_xor_sync(FULL, gathered, o);

@@ -1,16 +1,17 @@
 // knnm_noalloc.cu -- knnm_step_sample_noalloc: the round sampler for callers
 // that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being built by someone else, plug-ins whose host application owns every
-// allocation, or processes that must not grow their device footprint after
-// start-up.  This entry point runs the same sampler kernels as
-// knnm_step_sample, but its scratch (the packed list keys, the two reverse
-// slot arrays and the counters) lives in one file-scope __device__ array of
-// fixed size instead of memory taken from an allocator.  That array belongs
-// to the loaded library: every GPU that loads the library holds it until the
-// process exits.  The caller still provides every input and output array.
-#include <mutex>
+// Some callers cannot call cudaMalloc: plug-ins whose host application owns
+// every device allocation, and processes that must not grow their device
+// footprint after start-up (cudaMalloc/cudaFree can synchronize the device and
+// stall other streams on a request path).  This entry point runs the same
+// sampler kernels as knnm_step_sample, but its scratch (the packed list keys,
+// the two reverse slot arrays and the counters) lives in one file-scope
+// __device__ array of fixed size instead of memory taken from an allocator.
+// That array belongs to the loaded library: every GPU that loads the library
+// holds it until the process exits.  The caller still provides every input and
+// output array.  Each call waits for its stream at the end, so no call may be
+// made while a stream capture is active.
 
 #include "../../include/knnm.h"
 #include "knnm_internal.cuh"
@@ -19,26 +20,20 @@ using namespace knnm;
 
 // The fixed scratch.  In host code this name is only a host-side stand-in for
 // the device array, not a device address: it is never passed to a kernel.
-// The device address is looked up with cudaGetSymbolAddress, once per device.
 static __device__ __align__(256) unsigned char g_sample_scratch[KNNM_NOALLOC_SCRATCH_BYTES];
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
-
-// Device address of g_sample_scratch on the current device (looked up the
-// first time a device is seen, with that device current).
-cudaError_t scratch_address(int device, unsigned char** out) {
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_sample_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[device] = p;
-  }
-  *out = (unsigned char*)g_scratch_addr[device];
+// Device address of g_sample_scratch on the current device.  Looked up on
+// every call (cheap, allocates nothing once the library's device code is
+// loaded), so an address never outlives a reset of the device's context.  The
+// first lookup on a device loads the library's device code there, array
+// included.
+cudaError_t scratch_address(unsigned char** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_sample_scratch);
+  if (e != cudaSuccess) return e;
+  *out = (unsigned char*)p;
   return cudaSuccess;
 }
 
@@ -50,19 +45,17 @@ extern "C" int knnm_step_sample_noalloc(void* cuda_stream, int64_t N, int K, con
                                         const float* dists, uint8_t* flags, uint64_t seed, int t,
                                         int s, int cap_new, int cap_old, int32_t* new_ids,
                                         int32_t* new_cnt, int32_t* old_ids, int32_t* old_cnt) {
-  if (N < 1 || K < 1 || K > 32 || s < 1 || s > K || cap_new < 2 * s || cap_old < K + s || !ids ||
-      !dists || !flags || !new_ids || !new_cnt || !old_ids || !old_cnt)
+  if (N < 1 || N > 0x7FFFFFFFLL || K < 1 || K > 32 || s < 1 || s > K || cap_new < 2 * s ||
+      cap_old < K + s || !ids || !dists || !flags || !new_ids || !new_cnt || !old_ids || !old_cnt)
     return KNNM_ERR_INVALID;
+  // N < 2^31 and K + 2s <= 96: the products below cannot overflow.
   const size_t keys_b = align256((size_t)N * K * 8);
   const size_t slots_b = align256((size_t)N * s * 8);
   const size_t need = keys_b + 2 * slots_b + align256(sizeof(DevCounters));
   if (need > (size_t)KNNM_NOALLOC_SCRATCH_BYTES) return KNNM_ERR_INVALID;  // too large
 
-  int device = 0;
-  if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kMaxDevices)
-    return KNNM_ERR_CUDA;
   unsigned char* base = nullptr;
-  if (scratch_address(device, &base) != cudaSuccess) return KNNM_ERR_CUDA;
+  if (scratch_address(&base) != cudaSuccess) return KNNM_ERR_CUDA;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   uint64_t* keys = (uint64_t*)base;
   uint64_t* rev_new = (uint64_t*)(base + keys_b);

@@ -19,6 +19,7 @@ _LIB_PATH = Path(__file__).resolve().parent / "libknnm.so"
 L2, IP, COS, L1, CHI2, JACCARD = 0, 1, 2, 3, 4, 5
 FP32, BF16_RERANK, FP16_RERANK = 0, 1, 2
 SYMMETRIC, JOINT = 0, 1
+OPT_GRAPHS, OPT_REGION_CAP, OPT_WAIT_POLLS, OPT_FAIL_ALLOC = 1, 2, 3, 4
 MAX_ROUNDS = 64
 METRICS = {"l2": L2, "ip": IP, "cos": COS, "l1": L1, "chi2": CHI2, "jaccard": JACCARD}
 
@@ -45,7 +46,8 @@ class Stats(ctypes.Structure):
                 ("ms_update", ctypes.c_float * MAX_ROUNDS),
                 ("ms_init", ctypes.c_float), ("ms_rounds", ctypes.c_float),
                 ("ms_final", ctypes.c_float), ("ms_total", ctypes.c_float),
-                ("tc_rounds", ctypes.c_uint64)]
+                ("tc_rounds", ctypes.c_uint64),
+                ("spilled", ctypes.c_int64 * MAX_ROUNDS)]
 
     def as_dict(self):
         r = self.rounds
@@ -53,7 +55,7 @@ class Stats(ctypes.Structure):
                "ms_rounds": self.ms_rounds, "ms_final": self.ms_final, "ms_total": self.ms_total,
                "tc_rounds": [bool((self.tc_rounds >> t) & 1) for t in range(r)]}
         for name in ("updates", "dist_evals", "proposals", "reranked", "gathered", "ms_sample",
-                     "ms_join", "ms_update"):
+                     "ms_join", "ms_update", "spilled"):
             out[name] = list(getattr(self, name)[:r])
         return out
 
@@ -243,7 +245,11 @@ class Context:
 
     def set_graphs(self, on: bool = True):
         """Replay each merge round as one captured CUDA graph."""
-        self._check(lib().knnm_set_option(self.h, 1, int(on)))
+        self._check(lib().knnm_set_option(self.h, OPT_GRAPHS, int(on)))
+
+    def set_option(self, option: int, value: int):
+        """knnm_set_option (OPT_REGION_CAP, OPT_WAIT_POLLS, OPT_FAIL_ALLOC, ...)."""
+        self._check(lib().knnm_set_option(self.h, option, int(value)))
 
     def close(self):
         if getattr(self, "h", None):

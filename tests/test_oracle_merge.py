@@ -360,3 +360,65 @@ def test_exact_cases_hold_for_every_metric(orc, metric):
     ids, dists = orc.bruteforce_merge(X[:n1], G1, X[n1:], G2, K, metric=metric)
     ref_ids, ref_d = orc.bruteforce_knn(X, K, metric=metric)
     assert np.array_equal(ids, ref_ids) and np.array_equal(dists, ref_d)
+
+
+def _literal_script(ids):
+    """Alg. 1's G-script as printed: G[u] united with Reverse(G)[u] = {v : u in G[v]}."""
+    n = len(ids)
+    script = [set(map(int, ids[u])) for u in range(n)]
+    for v in range(n):
+        for u in ids[v]:
+            script[int(u)].add(v)
+    return [sorted(s) for s in script]
+
+
+def _sampled_sets(orc, st, flag, s, seed=5, t=3):
+    st.flags[:] = flag
+    new_ids, new_cnt, old_ids, old_cnt = orc.sample(st, seed, t, s)
+    new = [sorted(new_ids[u, :new_cnt[u]].tolist()) for u in range(len(st.ids))]
+    old = [sorted(old_ids[u, :old_cnt[u]].tolist()) for u in range(len(st.ids))]
+    return new, old
+
+
+def test_sampled_mode_reduces_to_literal_script_hand(orc):
+    """Alg. 1's Reverse and union steps: when the sample size covers every list
+    entry and every in-edge, the sampled mode takes everything, so its new set
+    (all flags new) or old set (all flags old) is the literal G-script, here the
+    hand-traced one of the 3 + 3 fixture."""
+    fx = json.load(open(os.path.join(GOLDEN, "hand_round_3p3.json")))
+    st = _hand_state(orc, fx)
+    s = len(fx["points"])  # >= K and >= every in-degree
+    new, old = _sampled_sets(orc, st, orc.FLAG_NEW, s)
+    assert new == fx["graph_script"] and all(len(o) == 0 for o in old)
+    assert np.all(st.flags == orc.FLAG_OLD)  # every sampled forward entry turns old
+    new, old = _sampled_sets(orc, st, orc.FLAG_OLD, s)
+    assert old == fx["graph_script"] and all(len(x) == 0 for x in new)
+
+
+@pytest.mark.parametrize("K", [6, 10])
+def test_sampled_mode_reduces_to_literal_script_random(orc, K):
+    """Same reduction on 300 rows with a random graph (hubs included): the sets
+    equal G[u] united with Reverse(G)[u] computed here from the ids alone."""
+    X = datagen.gaussian_mixture(300, 4, n_comp=3, seed=9)
+    st = orc.init(orc.JOINT, X, 0, K, 0, seed=21)
+    # make row 0 a hub: many lists point at it, so s must exceed K
+    for u in range(1, 120):
+        if 0 not in st.ids[u]:
+            st.ids[u, -1] = 0
+    indeg = np.bincount(st.ids.ravel(), minlength=300)
+    s = int(max(K, indeg.max()))
+    assert s > K
+    script = _literal_script(st.ids)
+    new, old = _sampled_sets(orc, st, orc.FLAG_NEW, s)
+    assert new == script and all(len(o) == 0 for o in old)
+    new, old = _sampled_sets(orc, st, orc.FLAG_OLD, s)
+    assert old == script and all(len(x) == 0 for x in new)
+    # one short of the largest in-degree: only the lists of the rows with that
+    # in-degree are cut (one reverse entry each); every other row is unchanged
+    new, _ = _sampled_sets(orc, st, orc.FLAG_NEW, s - 1)
+    for u in range(300):
+        if indeg[u] < s:
+            assert new[u] == script[u]
+        else:
+            assert set(new[u]) <= set(script[u]) and set(st.ids[u].tolist()) <= set(new[u])
+            assert len(script[u]) - 1 <= len(new[u]) <= len(script[u])

@@ -68,3 +68,23 @@ def test_noalloc_rejects_oversize(torch, km):
     ids, dists, flags = _state(torch, n, K, 3)
     out = _outputs(torch, n, K, s)
     assert km.step_sample_noalloc(ids, dists, flags, 1, 1, s, *out) == -1
+
+
+def test_noalloc_limit_is_the_stated_formula(torch, km):
+    """The header's limit, a(N*K*8) + 2*a(N*s*8) + 256 <= the array size with a()
+    rounding up to 256 bytes: the largest N that fits runs, one more row is
+    rejected before anything is launched."""
+    K, s = 20, 10
+    a = lambda x: (x + 255) // 256 * 256
+    cap = 8 << 20
+    n = cap // (8 * (K + 2 * s))
+    while a(n * K * 8) + 2 * a(n * s * 8) + 256 > cap:
+        n -= 1
+    while a((n + 1) * K * 8) + 2 * a((n + 1) * s * 8) + 256 <= cap:
+        n += 1
+    ids, dists, flags = _state(torch, n + 1, K, 4)
+    out = _outputs(torch, n + 1, K, s)
+    assert km.step_sample_noalloc(ids, dists, flags, 1, 1, s, *out) == -1
+    ids, dists, flags = _state(torch, n, K, 4)  # ids within [0, n)
+    out = _outputs(torch, n, K, s)
+    assert km.step_sample_noalloc(ids, dists, flags, 1, 1, s, *out) == 0
