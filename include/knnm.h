@@ -498,6 +498,20 @@ int knnm_step_join(knnm_ctx* ctx, int mode, const float* X1, int64_t nx1, const 
                    const int32_t* new_cnt, const int32_t* old_ids, const int32_t* old_cnt,
                    int64_t* updates, int64_t* dist_evals);
 
+/* The tensor-core distance estimate of the join (Alg. 1 / Alg. 2 compare step,
+ * the BF16/FP16 precisions) for the pairs (pi[r], pj[r]), r < P, of rows of X
+ * [n][d] (device pointers; d % 8 == 0, d <= 2048): est[r] is the estimate as
+ * the tensor-core join computes it (16-bit rows, tensor-core Gram value with
+ * FP32 accumulation), bound[r] the proven bound on |est - canonical| that the
+ * join uses to decide whether a pair needs its canonical FP32 distance (0 when
+ * both rows are small non-negative integers: the estimate is then exact), and
+ * canon[r] the canonical FP32 distance.  metric: KNNM_L2, KNNM_IP or KNNM_COS;
+ * precision: KNNM_BF16_RERANK or KNNM_FP16_RERANK.  Pair indices outside
+ * 0..n-1 are KNNM_ERR_INVALID (checked before any launch). */
+int knnm_step_tc_estimate(knnm_ctx* ctx, const float* X, int64_t n, int d, int metric,
+                          int precision, const int32_t* pi, const int32_t* pj, int64_t P,
+                          float* est, float* bound, float* canon);
+
 /* Merge and Sort (Alg. 1 last step): first K distinct ids of each working list
  * merged with its rear list. */
 int knnm_step_final(knnm_ctx* ctx, int64_t N, int K, const int32_t* ids, const float* dists,

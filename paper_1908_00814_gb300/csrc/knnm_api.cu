@@ -1489,6 +1489,48 @@ extern "C" int knnm_step_final(knnm_ctx* ctx, int64_t N, int K, const int32_t* i
   return KNNM_OK;
 }
 
+extern "C" int knnm_step_tc_estimate(knnm_ctx* ctx, const float* X, int64_t n, int d, int metric,
+                                     int precision, const int32_t* pi, const int32_t* pj,
+                                     int64_t P, float* est, float* bound, float* canon) {
+  if (!ctx) return KNNM_ERR_INVALID;
+  ctx->err[0] = 0;
+  if (n < 1 || n > 0x7FFFFFFFLL || d < 8 || d > 2048 || d % 8 != 0 || P < 0 || !X ||
+      (P > 0 && (!pi || !pj || !est || !bound || !canon)))
+    return fail(ctx, KNNM_ERR_INVALID, "bad estimate arguments (n=%lld d=%d P=%lld)", (long long)n,
+                d, (long long)P);
+  if (metric != KNNM_L2 && metric != KNNM_IP && metric != KNNM_COS)
+    return fail(ctx, KNNM_ERR_INVALID, "metric %d has no tensor-core form", metric);
+  if (precision != KNNM_BF16_RERANK && precision != KNNM_FP16_RERANK)
+    return fail(ctx, KNNM_ERR_INVALID, "precision %d is not a tensor-core precision", precision);
+  cudaStream_t st = ctx->stream;
+  KNNM_CUDA(cudaSetDevice(ctx->device));
+  if (P == 0) return KNNM_OK;
+  // every pair index must name a row: checked on the host before any launch
+  std::vector<int32_t> hi((size_t)P), hj((size_t)P);
+  KNNM_CUDA(cudaMemcpyAsync(hi.data(), pi, (size_t)P * 4, cudaMemcpyDeviceToHost, st));
+  KNNM_CUDA(cudaMemcpyAsync(hj.data(), pj, (size_t)P * 4, cudaMemcpyDeviceToHost, st));
+  KNNM_CUDA(cudaStreamSynchronize(st));
+  for (int64_t r = 0; r < P; ++r)
+    if (hi[r] < 0 || hi[r] >= n || hj[r] < 0 || hj[r] >= n)
+      return fail(ctx, KNNM_ERR_INVALID, "pair %lld names a row outside 0..%lld", (long long)r,
+                  (long long)(n - 1));
+  const int dx = ((d + 15) & ~15) + 16;
+  __nv_bfloat16* Xe = nullptr;
+  auto carve = [&](Carver& c) { Xe = c.take<__nv_bfloat16>((size_t)n * dx); };
+  Carver c0;
+  carve(c0);
+  int rc = ensure_arena(ctx, c0.off);
+  if (rc) return rc;
+  Carver c1;
+  c1.base = (char*)ctx->arena;
+  carve(c1);
+  Rows rows{X, X, n, d};
+  KNNM_CUDA(launch_bf16_ext(rows, n, dx, Xe, precision == KNNM_FP16_RERANK, nullptr, st));
+  KNNM_CUDA(launch_tc_estimate(precision, metric, Xe, dx, rows, pi, pj, P, est, bound, canon, st));
+  KNNM_CUDA(cudaStreamSynchronize(st));
+  return KNNM_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Graph diversification (Alg. 3) and the top-down search (Sec. 3.4)
 // ---------------------------------------------------------------------------

@@ -507,6 +507,11 @@ cudaError_t plan_pipe(int precision, int metric, int cap_new, int cap_old, int d
                       size_t* smem, int* grid);
 cudaError_t launch_pipe(int precision, const JoinArgs& a, const PipeArgs& P, size_t smem,
                         int grid, cudaStream_t st);
+// Tensor-core estimates, error bounds (0 for exact integer rows) and canonical
+// distances of the pairs (pi[r], pj[r]), computed as the tensor-core join does.
+cudaError_t launch_tc_estimate(int precision, int metric, const __nv_bfloat16* Xe, int dx,
+                               Rows rows, const int32_t* pi, const int32_t* pj, int64_t P,
+                               float* est, float* bound, float* canon, cudaStream_t st);
 // 16-bit rows (BF16, or FP16 when half != 0; stored through __nv_bfloat16
 // pointers as raw 16-bit elements) with their error-data tails.
 cudaError_t launch_bf16_ext(Rows rows, int64_t N, int dx, __nv_bfloat16* Xe, int half,

@@ -726,6 +726,77 @@ cudaError_t setup_ring(size_t smem, int threads, int* per_sm) {
                                                        smem);
 }
 
+// Tensor-core estimates of given pairs exactly as node_tc computes them: the
+// 16-bit extended rows are staged with the ring's row stride, the Gram value of
+// pair r comes from the same mma16816 chain over k0 = 0, 16, ... (A row r of a
+// 16-row tile against B row r), and is finished by exact_value / bound_tc.
+// One warp per 16 pairs; the canonical FP32 distance is computed beside it.
+template <int METRIC, bool HALF>
+__global__ void __launch_bounds__(32) k_tc_estimate(const __nv_bfloat16* Xe, int dx, Rows rows,
+                                                    const int32_t* pi, const int32_t* pj,
+                                                    int64_t P, float* est, float* bound,
+                                                    float* canon) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  const int lane = threadIdx.x;
+  const int d = rows.d, dpad = (d + 15) & ~15;
+  const int row_bytes = dx * 2, stride = row_bytes + 16, cpr = row_bytes >> 4;
+  unsigned char* A = sm;
+  unsigned char* B = sm + (size_t)16 * stride;
+  float* G = (float*)(sm + (size_t)32 * stride);  // 16 x 17
+  for (int64_t g = blockIdx.x; g * 16 < P; g += gridDim.x) {
+    const int64_t base = g * 16;
+    for (int c = lane; c < 32 * cpr; c += 32) {
+      const int r = c / cpr, o = c - r * cpr;
+      const int64_t q = base + (r & 15) < P ? base + (r & 15) : base;
+      const int32_t id = r < 16 ? pi[q] : pj[q];
+      const uint4 v = *reinterpret_cast<const uint4*>(
+          reinterpret_cast<const unsigned char*>(Xe + (size_t)id * dx) + o * 16);
+      *reinterpret_cast<uint4*>((r < 16 ? A + (size_t)r * stride : B + (size_t)(r - 16) * stride) +
+                                o * 16) = v;
+    }
+    __syncwarp();
+    float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
+    const unsigned char* pa = A + (size_t)(lane & 15) * stride + (lane >> 4) * 16;
+    const unsigned char* pb0 = B + (size_t)(lane & 7) * stride + ((lane >> 3) & 1) * 16;
+    const unsigned char* pb1 = B + (size_t)(8 + (lane & 7)) * stride + ((lane >> 3) & 1) * 16;
+    for (int k0 = 0; k0 < dpad; k0 += 16) {
+      uint32_t x0, x1, x2, x3, y0, y1;
+      ldm_x4(x0, x1, x2, x3, pa + k0 * 2);
+      ldm_x2(y0, y1, pb0 + k0 * 2);
+      mma16816<HALF>(c0, x0, x1, x2, x3, y0, y1);
+      ldm_x2(y0, y1, pb1 + k0 * 2);
+      mma16816<HALF>(c1, x0, x1, x2, x3, y0, y1);
+    }
+    const int r0 = lane >> 2, col = 2 * (lane & 3);
+    G[r0 * 17 + col] = c0[0];
+    G[r0 * 17 + col + 1] = c0[1];
+    G[(r0 + 8) * 17 + col] = c0[2];
+    G[(r0 + 8) * 17 + col + 1] = c0[3];
+    G[r0 * 17 + 8 + col] = c1[0];
+    G[r0 * 17 + 8 + col + 1] = c1[1];
+    G[(r0 + 8) * 17 + 8 + col] = c1[2];
+    G[(r0 + 8) * 17 + 8 + col + 1] = c1[3];
+    __syncwarp();
+    if (lane < 16 && base + lane < P) {
+      const float gv = G[lane * 17 + lane];
+      const unsigned char* ti = A + (size_t)lane * stride + dpad * 2;
+      const unsigned char* tj = B + (size_t)lane * stride + dpad * 2;
+      const float4 ai = *(const float4*)ti, aj = *(const float4*)tj;
+      const float ri = *(const float*)(ti + 16), rj = *(const float*)(tj + 16);
+      float e, b = 0.0f;
+      if (exact_rows(ri, rj))
+        e = exact_value<METRIC>(gv, ai, aj);
+      else
+        b = bound_tc<METRIC>(gv, ai, aj, d, &e);
+      est[base + lane] = e;
+      bound[base + lane] = b;
+      canon[base + lane] =
+          canon_dist_global<METRIC>(rows.row(pi[base + lane]), rows.row(pj[base + lane]), d, ai.w, aj.w);
+    }
+    __syncwarp();
+  }
+}
+
 }  // namespace
 
 cudaError_t plan_pipe(int precision, int metric, int cap_new, int cap_old, int d, PipeArgs* P,
@@ -837,6 +908,31 @@ cudaError_t launch_bf16_ext(Rows rows, int64_t N, int dx, __nv_bfloat16* Xe, int
     k_bf16_ext<true><<<blocks, EXT_WARPS * 32, 0, st>>>(rows, N, dx, Xe, inexact);
   else
     k_bf16_ext<false><<<blocks, EXT_WARPS * 32, 0, st>>>(rows, N, dx, Xe, inexact);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_estimate(int precision, int metric, const __nv_bfloat16* Xe, int dx,
+                               Rows rows, const int32_t* pi, const int32_t* pj, int64_t P,
+                               float* est, float* bound, float* canon, cudaStream_t st) {
+  if (P == 0) return cudaSuccess;
+  const size_t smem = (size_t)32 * (dx * 2 + 16) + 16 * 17 * 4;
+  const int64_t groups = (P + 15) / 16;
+  const unsigned grid = (unsigned)(groups < 65535 ? groups : 65535);
+  cudaError_t e = cudaSuccess;
+#define KNNM_EST(M, H)                                                                      \
+  do {                                                                                      \
+    e = cudaFuncSetAttribute(k_tc_estimate<M, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             (int)smem);                                                    \
+    if (e != cudaSuccess) return e;                                                         \
+    k_tc_estimate<M, H><<<grid, 32, smem, st>>>(Xe, dx, rows, pi, pj, P, est, bound, canon); \
+  } while (0)
+  const bool h = precision == 2;
+  switch (metric) {
+    case L2: if (h) KNNM_EST(L2, true); else KNNM_EST(L2, false); break;
+    case IP: if (h) KNNM_EST(IP, true); else KNNM_EST(IP, false); break;
+    default: if (h) KNNM_EST(COS, true); else KNNM_EST(COS, false); break;
+  }
+#undef KNNM_EST
   return cudaGetLastError();
 }
 

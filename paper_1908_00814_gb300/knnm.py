@@ -132,6 +132,7 @@ SIGNATURES = {
                             _P, _I, _I, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int64),
                             ctypes.POINTER(ctypes.c_int64)]),
     "knnm_step_final": (_I, [_P, _I64, _I, _P, _P, _I, _P, _P, _P, _P]),
+    "knnm_step_tc_estimate": (_I, [_P, _P, _I64, _I, _I, _I, _P, _P, _I64, _P, _P, _P]),
     "knnm_step_sample_noalloc": (_I, [_P, _I64, _I, _P, _P, _P, _U64, _I, _I, _I, _I, _P, _P,
                                       _P, _P]),
     "knnm_merge_symmetric_sets": (_I, [_P, _P, _P, _I64, _I64, _I64, _P, _P,
@@ -511,6 +512,21 @@ class Context:
                                          _ptr(new_cnt), _ptr(old_ids), _ptr(old_cnt),
                                          ctypes.byref(upd), ctypes.byref(ev)))
         return int(upd.value), int(ev.value)
+
+    def step_tc_estimate(self, X, pi, pj, metric="l2", precision="bf16"):
+        """(estimate, bound, canonical) of each pair (pi[r], pj[r]) of rows of X,
+        as the tensor-core join computes them (device tensors)."""
+        import torch
+        n, d = X.shape
+        P = pi.shape[0]
+        est, bound, canon = (torch.empty(P, dtype=torch.float32, device=X.device)
+                             for _ in range(3))
+        prec = {"bf16": BF16_RERANK, "fp16": FP16_RERANK}[precision]
+        self._sync_stream()
+        self._check(lib().knnm_step_tc_estimate(self.h, _ptr(X), n, d, METRICS[metric], prec,
+                                                _ptr(pi), _ptr(pj), P, _ptr(est), _ptr(bound),
+                                                _ptr(canon)))
+        return est, bound, canon
 
     def step_final(self, ids, dists, rear_ids, rear_dists):
         import torch
