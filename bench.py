@@ -904,9 +904,9 @@ def run_ours(args, w):
             "recall_at_10": recall, "recall_queries": len(queries),
             "distance_error": dist_err,
             "rounds": st_bf[-1]["rounds"], "updates_per_round": st_bf[-1]["updates"],
-            "per_round": {k: st_bf[-1][k] for k in ("dist_evals", "proposals", "reranked",
-                                                    "gathered", "ms_sample", "ms_join",
-                                                    "ms_update")},
+            "per_round": {k: st_bf[-1][k] for k in ("dist_evals", "proposals", "spilled",
+                                                    "reranked", "gathered", "ms_sample",
+                                                    "ms_join", "ms_update")},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches, "input_build_rounds": build_rounds}
     if not args.no_fp32:

@@ -133,11 +133,12 @@ int knnm_set_stream(knnm_ctx* ctx, void* cuda_stream);
  *     and replayed, one graph launch per round.  Results are identical;
  *     knnm_stats then times each round as a whole (in ms_join; ms_sample and
  *     ms_update stay 0).
- *   KNNM_OPT_REGION_CAP (default 0, >= 0): proposals each join block buffers
- *     before it inserts the rest straight into the live lists by ordered slot
- *     insertion (the same UpdateNN, without the bucket pass); 0 sizes the
- *     buffers from N (256 proposals per row in all, at least 1,024 per block).
- *     Results do not depend on it; small values force the direct-insert path.
+ *   KNNM_OPT_BUCKET_CAP (default 0, 0..4096): slots per target for the
+ *     proposals a join round offers to UpdateNN; a proposal arriving at a full
+ *     bucket is inserted straight into its target's live list by ordered slot
+ *     insertion (the same top-K union, without the bucket).  0 takes 12*K
+ *     rounded up to 32, within 64..512.  Results do not depend on it; small
+ *     values force the direct-insert path.
  *   KNNM_OPT_WAIT_POLLS (default -1, >= -1): polls before a device-side wait of
  *     the join for its staged rows gives up (-1: 2^22).  A wait that gives up
  *     makes the call return KNNM_ERR_DEVICE with error bit 0x8 in its message;
@@ -149,7 +150,7 @@ int knnm_set_stream(knnm_ctx* ctx, void* cuda_stream);
  *     and its existing scratch stay usable. */
 enum {
   KNNM_OPT_GRAPHS = 1,
-  KNNM_OPT_REGION_CAP = 2,
+  KNNM_OPT_BUCKET_CAP = 2,
   KNNM_OPT_WAIT_POLLS = 3,
   KNNM_OPT_FAIL_ALLOC = 4
 };
@@ -436,6 +437,15 @@ int knnm_server_destroy(knnm_server* srv);
  * nx1 == N).  `set_split` is n1: rows below it are S1, the rest S2.
  * `mode` 0 = S-Merge, 1 = J-Merge (and build with set_split = 0).
  * ------------------------------------------------------------------------- */
+
+/* Sizes a merge derives from its parameters, for sizing the step arrays:
+ * K_keep = floor(keep_ratio*K) entries each input list keeps at Divide (Alg. 1;
+ * K in a J-Merge with set_split == 0, i.e. a build), Kr = K - K_keep rear
+ * entries (and appended random members), and the sample size
+ * s = max(1, floor(sample_rate*K)) capped at K.  Any output pointer may be
+ * NULL.  KNNM_ERR_INVALID for parameters a merge would reject. */
+int knnm_list_widths(const knnm_params* params, int mode, int64_t set_split, int* K_keep,
+                     int* Kr, int* s);
 
 /* Divide / Append (Alg. 1) and Initialize (Alg. 2).  G1 rows cover
  * 0..set_split-1; G2 rows cover set_split..N-1 in S-Merge and must be NULL in

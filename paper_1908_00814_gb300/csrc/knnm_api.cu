@@ -22,7 +22,7 @@ struct knnm_ctx {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t rev[4] = {nullptr, nullptr, nullptr, nullptr};  // per-round phases
   int use_graphs = 0;  // replay each round as one captured CUDA graph
-  uint64_t region_cap = 0;    // proposals per join-block region (0: sized from N)
+  int bucket_cap = 0;         // proposal slots per target and round (0: from K)
   uint32_t wait_polls = WAIT_LIMIT;  // polls before a device wait of the join gives up
   int fail_alloc = 0;         // scratch reservations still to fail (host-side injection)
   cudaStream_t cap_stream = nullptr;  // private stream the round graph is captured on
@@ -136,7 +136,6 @@ struct JoinPath {
   PipeArgs pa;
   size_t smem = 0;
   int grid = 0;
-  int regions() const { return pipe ? grid : plan.grid; }
 };
 
 int choose_join(knnm_ctx* ctx, int precision, int metric, int cap_new, int cap_old, int d,
@@ -155,6 +154,15 @@ int choose_join(knnm_ctx* ctx, int precision, int metric, int cap_new, int cap_o
     return fail(ctx, KNNM_ERR_INVALID, "no join configuration for cap %d+%d, d=%d: %s", cap_new,
                 cap_old, d, cudaGetErrorString(e));
   return KNNM_OK;
+}
+
+// Bucket slots per target and round for the join's proposals: enough that
+// only targets offered far more than the average (hubs) spill into direct
+// inserts.
+int proposal_slots(const knnm_ctx* ctx, int K) {
+  if (ctx->bucket_cap > 0) return ctx->bucket_cap;
+  int b = (24 * K + 31) & ~31;
+  return b < 64 ? 64 : (b > 1024 ? 1024 : b);
 }
 
 }  // namespace
@@ -259,39 +267,23 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   const bool adaptive = tc && choose_join(ctx, KNNM_FP32, params->metric, D.cap_new, D.cap_old,
                                           d, rows_aligned, &jp32) == KNNM_OK;
   if (tc && !adaptive) ctx->err[0] = 0;
-  // One proposal region per join block, sized for that join's grid; the two
-  // joins of the per-round choice share one allocation.
-  const uint64_t per_node = 256;
-  auto cap_for = [&](int regions_of) {
-    if (ctx->region_cap) return ctx->region_cap;
-    uint64_t c = ((uint64_t)N * per_node + regions_of - 1) / regions_of;
-    return c < 1024 ? (uint64_t)1024 : c;
-  };
-  const int regions = adaptive ? std::max(jp.regions(), jp32.regions()) : jp.regions();
-  const uint64_t region_cap = cap_for(jp.regions());
-  const uint64_t region_cap32 = adaptive ? cap_for(jp32.regions()) : region_cap;
-  const uint64_t prop_slots =
-      std::max((uint64_t)jp.regions() * region_cap,
-               adaptive ? (uint64_t)jp32.regions() * region_cap32 : (uint64_t)0);
-
+  const int bcap = proposal_slots(ctx, K);
   // Carve the scratch (two passes: size, then pointers).
   struct Ptrs {
     float* X;
     int32_t *G1, *G2, *oi;
     float* od;
-    uint64_t *keys, *prev, *rear, *rev_new, *rev_old, *prop_key;
+    uint64_t *keys, *prev, *rear, *rev_new, *rev_old;
     uint8_t* flags;
-    int32_t *new_ids, *new_cnt, *old_ids, *old_cnt, *prop_tgt;
+    int32_t *new_ids, *new_cnt, *old_ids, *old_cnt;
     float* norms;
     __nv_bfloat16* Xb;
     float4* aux;
     float* rmax;
     __nv_bfloat16* Xe;
     unsigned char* rec;
-    unsigned long long* region_cnt;
     DevCounters* ctr;
     int32_t* pcnt;
-    unsigned long long *offs, *tile_sum, *total;
     uint64_t* bucket;
     int32_t* rcnt;
     unsigned long long *roffs, *rtile, *rtotal;
@@ -328,15 +320,9 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     P.rec = (jp.pipe || (adaptive && jp32.pipe))
                 ? c.take<unsigned char>((size_t)N * rec_bytes(jp.pipe ? jp.pa.cap : jp32.pa.cap))
                 : nullptr;
-    P.prop_tgt = c.take<int32_t>(prop_slots);
-    P.prop_key = c.take<uint64_t>(prop_slots);
-    P.region_cnt = c.take<unsigned long long>((size_t)regions);
     P.ctr = c.take<DevCounters>(1);
     P.pcnt = c.take<int32_t>((size_t)N);
-    P.offs = c.take<unsigned long long>((size_t)N + 1);
-    P.tile_sum = c.take<unsigned long long>((size_t)(N + 1023) / 1024 + 1);
-    P.total = c.take<unsigned long long>(1);
-    P.bucket = c.take<uint64_t>(prop_slots);
+    P.bucket = c.take<uint64_t>((size_t)N * bcap);
   };
   Carver sizer;
   carve(sizer);
@@ -495,19 +481,17 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   ja.new_cnt = P.new_cnt;
   ja.old_ids = P.old_ids;
   ja.old_cnt = P.old_cnt;
-  ja.prop_tgt = P.prop_tgt;
-  ja.prop_key = P.prop_key;
-  ja.region_cap = region_cap;
-  ja.region_cnt = P.region_cnt;
+  ja.bucket = P.bucket;
+  ja.bcnt = P.pcnt;
+  ja.bcap = bcap;
   ja.live_keys = P.keys;
-  ja.prop_cnt = P.pcnt;
   ja.ctr = P.ctr;
   ja.Xb = P.Xb;
   ja.aux = P.aux;
   ja.rmax = P.rmax;
   ja.use_bulk = use_bulk ? 1 : 0;
   ja.wait_polls = ctx->wait_polls;
-  MergeArgs ma{N, K, P.keys, P.prev, P.flags, P.pcnt, P.offs, P.bucket, P.ctr};
+  MergeArgs ma{N, K, P.keys, P.prev, P.flags, P.pcnt, bcap, P.bucket, P.ctr};
   KNNM_CUDA(cudaMemsetAsync(P.pcnt, 0, (size_t)N * 4, st));
   KNNM_CUDA(cudaMemsetAsync(P.rcnt, 0, (size_t)N * 8, st));
 
@@ -520,8 +504,6 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     const bool timed = t > 0;
     KNNM_CUDA(cudaMemsetAsync(P.ctr, 0, sizeof(DevCounters), rs));
     KNNM_CUDA(cudaMemsetAsync(&P.ctr->err_row, 0xFF, 8, rs));
-    if (adaptive)  // the two joins fill different numbers of proposal regions
-      KNNM_CUDA(cudaMemsetAsync(P.region_cnt, 0, (size_t)regions * 8, rs));
     sa.t = t;
     if (timed) KNNM_CUDA(cudaEventRecord(ctx->rev[0], rs));
     KNNM_CUDA(launch_sample(sa, rs));
@@ -529,15 +511,12 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     const bool alt = adaptive && !use_tc;  // a tensor-core precision taking the FP32 join
     const JoinPath& j = alt ? jp32 : jp;
     const int jprec = alt ? KNNM_FP32 : precision;
-    const uint64_t rcap = alt ? region_cap32 : region_cap;
-    ja.region_cap = rcap;
     if (j.pipe)
       KNNM_CUDA(launch_pipe(jprec, ja, j.pa, j.smem, j.grid, rs));
     else
       KNNM_CUDA(launch_join(jprec, ja, j.plan, rs));
     if (timed) KNNM_CUDA(cudaEventRecord(ctx->rev[2], rs));
-    KNNM_CUDA(launch_bucket_update(ma, P.prop_tgt, P.prop_key, P.region_cnt, rcap, j.regions(),
-                                   P.tile_sum, P.total, rs));
+    KNNM_CUDA(launch_bucket_update(ma, rs));
     if (timed) KNNM_CUDA(cudaEventRecord(ctx->rev[3], rs));
     if (sa.t_dev) KNNM_CUDA(launch_bump_int(P.tdev, rs));
     KNNM_CUDA(cudaMemcpyAsync(ctx->host_ctr, P.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost,
@@ -734,8 +713,8 @@ extern "C" int knnm_set_option(knnm_ctx* c, int option, int value) {
     c->use_graphs = value ? 1 : 0;
     return KNNM_OK;
   }
-  if (option == KNNM_OPT_REGION_CAP && value >= 0) {
-    c->region_cap = (uint64_t)value;
+  if (option == KNNM_OPT_BUCKET_CAP && value >= 0 && value <= 4096) {
+    c->bucket_cap = value;
     return KNNM_OK;
   }
   if (option == KNNM_OPT_WAIT_POLLS && value >= -1) {
@@ -747,6 +726,18 @@ extern "C" int knnm_set_option(knnm_ctx* c, int option, int value) {
     return KNNM_OK;
   }
   return KNNM_ERR_INVALID;
+}
+
+extern "C" int knnm_list_widths(const knnm_params* params, int mode, int64_t set_split,
+                                int* K_keep, int* Kr, int* s) {
+  if (mode != SYMMETRIC && mode != JOINT) return KNNM_ERR_INVALID;
+  Derived D{};
+  const int rc = derive(nullptr, params, mode, set_split, &D);
+  if (rc) return rc;
+  if (K_keep) *K_keep = D.K_keep;
+  if (Kr) *Kr = D.Kr;
+  if (s) *s = D.s;
+  return KNNM_OK;
 }
 
 extern "C" uint64_t knnm_hash64(uint64_t seed, uint64_t t, uint64_t stream, uint64_t owner,
@@ -1355,16 +1346,10 @@ extern "C" int knnm_step_join(knnm_ctx* ctx, int mode, const float* X1, int64_t 
   rc = choose_join(ctx, precision, params->metric, cap_new, cap_old, d,
                    d % 4 == 0 && aligned16(X1) && aligned16(X2 ? X2 : X1), &jp);
   if (rc) return rc;
-  const int regions = jp.regions();
   const bool tc = precision != KNNM_FP32;
-  uint64_t per_node = (uint64_t)2 * cap_new * (cap_new + cap_old);
-  if (per_node > 512) per_node = 512;
-  uint64_t region_cap = ((uint64_t)N * per_node + regions - 1) / regions;
-  if (region_cap < 256) region_cap = 256;
-  if (ctx->region_cap) region_cap = ctx->region_cap;
-  uint64_t *keys, *prev, *pkey, *bucket;
-  int32_t *ptgt, *pcnt;
-  unsigned long long *rcnt, *offs, *tsum, *total;
+  const int bcap = proposal_slots(ctx, K);
+  uint64_t *keys, *prev, *bucket;
+  int32_t* pcnt;
   float* norms;
   __nv_bfloat16* Xb;
   float4* aux;
@@ -1375,19 +1360,13 @@ extern "C" int knnm_step_join(knnm_ctx* ctx, int mode, const float* X1, int64_t 
   auto carve = [&](Carver& c) {
     keys = c.take<uint64_t>((size_t)N * K);
     prev = c.take<uint64_t>((size_t)N * K);
-    ptgt = c.take<int32_t>(region_cap * regions);
-    pkey = c.take<uint64_t>(region_cap * regions);
-    rcnt = c.take<unsigned long long>((size_t)regions);
     norms = c.take<float>((size_t)N);
     Xb = tc && !jp.pipe ? c.take<__nv_bfloat16>((size_t)N * d) : nullptr;
     aux = tc && !jp.pipe ? c.take<float4>((size_t)N) : nullptr;
     rmax = tc && !jp.pipe ? c.take<float>((size_t)N) : nullptr;
     ctr = c.take<DevCounters>(1);
     pcnt = c.take<int32_t>((size_t)N);
-    offs = c.take<unsigned long long>((size_t)N + 1);
-    tsum = c.take<unsigned long long>((size_t)(N + 1023) / 1024 + 1);
-    total = c.take<unsigned long long>(1);
-    bucket = c.take<uint64_t>(region_cap * regions);
+    bucket = c.take<uint64_t>((size_t)N * bcap);
     Xe = tc && jp.pipe ? c.take<__nv_bfloat16>((size_t)N * jp.pa.dx) : nullptr;
     rec = jp.pipe ? c.take<unsigned char>((size_t)N * rec_bytes(jp.pa.cap)) : nullptr;
   };
@@ -1423,12 +1402,10 @@ extern "C" int knnm_step_join(knnm_ctx* ctx, int mode, const float* X1, int64_t 
   ja.new_cnt = new_cnt;
   ja.old_ids = old_ids;
   ja.old_cnt = old_cnt;
-  ja.prop_tgt = ptgt;
-  ja.prop_key = pkey;
-  ja.region_cap = region_cap;
-  ja.region_cnt = rcnt;
+  ja.bucket = bucket;
+  ja.bcnt = pcnt;
+  ja.bcap = bcap;
   ja.live_keys = keys;
-  ja.prop_cnt = pcnt;
   ja.ctr = ctr;
   ja.Xb = Xb;
   ja.aux = aux;
@@ -1446,8 +1423,8 @@ extern "C" int knnm_step_join(knnm_ctx* ctx, int mode, const float* X1, int64_t 
   } else {
     KNNM_CUDA(launch_join(precision, ja, jp.plan, st));
   }
-  MergeArgs ma{N, K, keys, prev, flags, pcnt, offs, bucket, ctr};
-  KNNM_CUDA(launch_bucket_update(ma, ptgt, pkey, rcnt, region_cap, regions, tsum, total, st));
+  MergeArgs ma{N, K, keys, prev, flags, pcnt, bcap, bucket, ctr};
+  KNNM_CUDA(launch_bucket_update(ma, st));
   KNNM_CUDA(launch_unpack((int64_t)N * K, keys, ids, dists, st));
   rc = read_counters(ctx, ctr);
   if (rc) return rc;

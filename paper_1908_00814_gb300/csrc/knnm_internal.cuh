@@ -303,6 +303,94 @@ __device__ __forceinline__ void slots_insert(uint64_t* slots, int m, uint64_t x)
   }
 }
 
+// slots_insert for a key that is usually no improvement: one read of the m-th
+// slot rejects it (slots only decrease, so a key not below the current m-th
+// can never be among the m smallest, and an equal key is already held).
+__device__ __forceinline__ void slots_insert_checked(uint64_t* slots, int m, uint64_t x) {
+  if (x >= *((volatile uint64_t*)(slots + m - 1))) return;
+  slots_insert(slots, m, x);
+}
+
+// Proposal sink of the join, the input of UpdateNN.  A proposal for target v
+// takes the next slot of v's bucket (bcap slots, claimed by an atomic on v's
+// count).  Once v's bucket is full it is inserted straight into v's live
+// list.  Either way it ends in the top-K union of the round.  Each lane offers
+// up to NP proposals; n_prop / n_direct count this lane's offers and direct
+// inserts.
+template <int NP>
+__device__ __forceinline__ void emit_to_buckets(uint64_t* bucket, int32_t* bcnt, int bcap,
+                                                uint64_t* live, int K, const bool (&has)[NP],
+                                                const int32_t (&tgt)[NP],
+                                                const uint64_t (&key)[NP],
+                                                unsigned long long& n_prop,
+                                                unsigned long long& n_direct) {
+  int pos[NP];
+#pragma unroll
+  for (int x = 0; x < NP; ++x) pos[x] = has[x] ? atomicAdd(bcnt + tgt[x], 1) : 0;
+#pragma unroll
+  for (int x = 0; x < NP; ++x) {
+    if (has[x]) {
+      ++n_prop;
+      if (pos[x] < bcap) {
+        bucket[(size_t)tgt[x] * bcap + pos[x]] = key[x];
+      } else {
+        ++n_direct;
+        slots_insert_checked(live + (size_t)tgt[x] * K, K, key[x]);
+      }
+    }
+  }
+}
+
+// The same sink with the slot claims of one batch kept in flight while the
+// warp computes the next batch: offer() first writes the previous batch (whose
+// atomics have returned by then), then claims slots for the new one, one
+// atomic per proposal.  finish() writes the last batch.
+template <int NP>
+struct DeferredSink {
+  bool has[NP];
+  int32_t tgt[NP];
+  uint64_t key[NP];
+  int pos[NP];
+  unsigned long long nprop = 0, ndirect = 0;
+
+  __device__ __forceinline__ DeferredSink() {
+#pragma unroll
+    for (int x = 0; x < NP; ++x) {
+      has[x] = false;
+      tgt[x] = 0;
+      key[x] = 0ull;
+      pos[x] = 0;
+    }
+  }
+  __device__ __forceinline__ void finish(uint64_t* bucket, int bcap, uint64_t* live, int K) {
+#pragma unroll
+    for (int x = 0; x < NP; ++x) {
+      if (has[x]) {
+        ++nprop;
+        if (pos[x] < bcap) {
+          bucket[(size_t)tgt[x] * bcap + pos[x]] = key[x];
+        } else {
+          ++ndirect;
+          slots_insert_checked(live + (size_t)tgt[x] * K, K, key[x]);
+        }
+        has[x] = false;
+      }
+    }
+  }
+  __device__ __forceinline__ void offer(uint64_t* bucket, int32_t* bcnt, int bcap, uint64_t* live,
+                                        int K, const bool (&h)[NP], const int32_t (&t)[NP],
+                                        const uint64_t (&k)[NP]) {
+    finish(bucket, bcap, live, K);
+#pragma unroll
+    for (int x = 0; x < NP; ++x) {
+      has[x] = h[x];
+      tgt[x] = t[x];
+      key[x] = k[x];
+      pos[x] = h[x] ? atomicAdd(bcnt + t[x], 1) : 0;
+    }
+  }
+};
+
 // ---------------------------------------------------------------------------
 // mbarrier + bulk async copy (the TMA engine's non-tensor form).
 // ---------------------------------------------------------------------------
@@ -410,6 +498,7 @@ struct SampleArgs {
   int K_list = 0;                // list length, for the k-th key of each candidate
   uint64_t* kth = nullptr;       // [N] round-start k-th key of every list (small: stays in L2)
   // Bucketed reverse sampling (used when rcnt is set; rev_new/rev_old unused):
+  // Bucketed reverse sampling (used when rcnt is set; rev_new/rev_old unused):
   int32_t* rcnt = nullptr;             // [2N] in-edges per (target, stream); zero on entry and exit
   unsigned long long* roffs = nullptr;  // [2N+1] bucket offsets
   uint64_t* rbucket = nullptr;         // [N*K] reverse sampling keys grouped by (target, stream)
@@ -470,12 +559,10 @@ struct JoinArgs {
   const int32_t* new_cnt;
   const int32_t* old_ids;
   const int32_t* old_cnt;
-  int32_t* prop_tgt;   // proposal buffer: block b writes region b
-  uint64_t* prop_key;
-  uint64_t region_cap;  // proposals per region
-  unsigned long long* region_cnt;  // [grid] proposals written per region
-  uint64_t* live_keys;  // lists receiving direct inserts when a region is full
-  int32_t* prop_cnt;    // [N] proposals written per target (bucket sizes)
+  uint64_t* bucket;     // [N][bcap] proposal keys per target (UpdateNN input)
+  int32_t* bcnt;        // [N] proposals offered per target this round (zero on entry)
+  int bcap;             // bucket slots per target
+  uint64_t* live_keys;  // lists receiving direct inserts once a bucket is full
   DevCounters* ctr;
   // BF16 path
   const __nv_bfloat16* Xb;  // [N][d] bf16 copy
@@ -532,18 +619,14 @@ struct MergeArgs {
   uint64_t* keys;             // [N][K] lists, merged in place
   const uint64_t* prev_keys;  // [N][K] round-start snapshot (flags / c_t)
   uint8_t* flags;             // [N][K] round-start flags in, merged flags out
-  int32_t* cnt;               // [N] per-target proposal counts; consumed back to zero
-  unsigned long long* offs;   // [N+1] bucket offsets (written by the scan)
-  uint64_t* bucket;           // proposal keys grouped by target
+  int32_t* cnt;               // [N] proposals offered per target; consumed back to zero
+  int bcap;                   // bucket slots per target
+  const uint64_t* bucket;     // [N][bcap] proposal keys per target
   DevCounters* ctr;
 };
-// Scan of the counts, scatter of the proposal regions into buckets, and the
-// per-node merge of list and bucket (UpdateNN of the whole round) with flags
-// and c_t.  tile_sum needs ceil(N / 1024) entries.
-cudaError_t launch_bucket_update(const MergeArgs& a, const int32_t* prop_tgt,
-                                 const uint64_t* prop_key, const unsigned long long* region_cnt,
-                                 uint64_t region_cap, int regions, unsigned long long* tile_sum,
-                                 unsigned long long* total, cudaStream_t st);
+// The per-node merge of list and bucket (UpdateNN of the whole round) with
+// flags and c_t.
+cudaError_t launch_bucket_update(const MergeArgs& a, cudaStream_t st);
 
 cudaError_t launch_final(int64_t N, int K, const uint64_t* keys, int Kr, const uint64_t* rear,
                          int32_t* out_ids, float* out_dists, cudaStream_t st);

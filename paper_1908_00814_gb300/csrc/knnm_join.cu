@@ -17,8 +17,8 @@
 //
 // A proposal (p <- q, d) is written only when its key (d, q) is below p's
 // k-th key (read when the block starts node u): no other proposal can enter
-// the top-k union.  Proposals go to the block's own region of the proposal
-// buffer; if the region is full they are inserted into the live lists at once.
+// the top-k union.  Proposals go to their target's bucket; once a bucket is
+// full they are inserted into the target's live list at once.
 #include "knnm_internal.cuh"
 
 namespace knnm {
@@ -42,7 +42,7 @@ struct JoinShared {
   float* cnorm;      // [cap_rows] canonical norms (COS)
   uint16_t* pairs;   // [pair_cap] (i << 8) | j
   uint64_t* bar;     // mbarrier
-  int* scal;         // [0] npairs, [1] fill of this block's proposal region
+  int* scal;         // [0] npairs, [1] proposals offered, [2] re-rank count, [3] direct inserts
 };
 
 // Loads the candidate list of node u (ids, k-th keys, norms); returns nn, M.
@@ -101,37 +101,20 @@ __device__ __forceinline__ int build_pairs(const JoinArgs& a, int nn, int M, Joi
   return S.scal[0];
 }
 
-// Writes this warp's proposals (up to two per lane) to the block's region.
+// Offers this warp's proposals (up to two per lane) to UpdateNN; the block
+// counts offers in S.scal[1] and direct inserts in S.scal[3].
 __device__ __forceinline__ void emit(const JoinArgs& a, JoinShared& S, bool hp, int32_t tp,
                                      uint64_t kp, bool hq, int32_t tq, uint64_t kq) {
-  const int lane = threadIdx.x & 31;
-  const unsigned bp = __ballot_sync(FULL, hp), bq = __ballot_sync(FULL, hq);
-  const int n = __popc(bp) + __popc(bq);
-  if (n == 0) return;
-  int base = 0;
-  if (lane == 0) base = atomicAdd(&S.scal[1], n);
-  base = __shfl_sync(FULL, base, 0);
-  const unsigned lt = (1u << lane) - 1u;
-  const uint64_t region = (uint64_t)blockIdx.x * a.region_cap;
-  if (hp) {
-    uint64_t pos = (uint64_t)base + __popc(bp & lt);
-    if (pos < a.region_cap) {
-      a.prop_tgt[region + pos] = tp;
-      a.prop_key[region + pos] = kp;
-      atomicAdd(&a.prop_cnt[tp], 1);
-    } else {
-      slots_insert(a.live_keys + (size_t)tp * a.K, a.K, kp);
-    }
-  }
-  if (hq) {
-    uint64_t pos = (uint64_t)base + __popc(bp) + __popc(bq & lt);
-    if (pos < a.region_cap) {
-      a.prop_tgt[region + pos] = tq;
-      a.prop_key[region + pos] = kq;
-      atomicAdd(&a.prop_cnt[tq], 1);
-    } else {
-      slots_insert(a.live_keys + (size_t)tq * a.K, a.K, kq);
-    }
+  const bool has[2] = {hp, hq};
+  const int32_t tgt[2] = {tp, tq};
+  const uint64_t key[2] = {kp, kq};
+  unsigned long long np_ = 0, nd_ = 0;
+  emit_to_buckets<2>(a.bucket, a.bcnt, a.bcap, a.live_keys, a.K, has, tgt, key, np_, nd_);
+  const unsigned n = __reduce_add_sync(FULL, (unsigned)np_);
+  const unsigned nd = __reduce_add_sync(FULL, (unsigned)nd_);
+  if ((threadIdx.x & 31) == 0 && n) {
+    atomicAdd(&S.scal[1], (int)n);
+    if (nd) atomicAdd(&S.scal[3], (int)nd);
   }
 }
 
@@ -214,6 +197,7 @@ __global__ void __launch_bounds__(JT) k_join_fp32(JoinArgs a, int chunk, int pai
     mbar_init(S.bar, 1);
     fence_mbar_init();
     S.scal[1] = 0;
+    S.scal[3] = 0;
   }
   __syncthreads();
   uint32_t phase = 0;
@@ -279,11 +263,8 @@ __global__ void __launch_bounds__(JT) k_join_fp32(JoinArgs a, int chunk, int pai
     }
   }
   if (threadIdx.x == 0) {
-    const int fill = S.scal[1];
-    a.region_cnt[blockIdx.x] = (unsigned long long)min((uint64_t)fill, a.region_cap);
-    atomicAdd(&a.ctr->proposals, (unsigned long long)fill);
-    if ((uint64_t)fill > a.region_cap)
-      atomicAdd(&a.ctr->overflow, (unsigned long long)((uint64_t)fill - a.region_cap));
+    atomicAdd(&a.ctr->proposals, (unsigned long long)S.scal[1]);
+    atomicAdd(&a.ctr->overflow, (unsigned long long)S.scal[3]);
     atomicAdd(&a.ctr->dist_evals, evals);
     atomicAdd(&a.ctr->gathered, gathered);
   }
@@ -311,7 +292,7 @@ __global__ void __launch_bounds__(JT) k_join_jaccard(JoinArgs a, int pair_cap) {
   p += 16;
   S.pairs = (uint16_t*)p;
   (void)pair_cap;
-  if (threadIdx.x == 0) S.scal[1] = 0;
+  if (threadIdx.x == 0) S.scal[1] = S.scal[3] = 0;
   __syncthreads();
   unsigned long long evals = 0, gathered = 0;
   for (int64_t u = blockIdx.x; u < a.N; u += gridDim.x) {
@@ -343,11 +324,8 @@ __global__ void __launch_bounds__(JT) k_join_jaccard(JoinArgs a, int pair_cap) {
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    const int fill = S.scal[1];
-    a.region_cnt[blockIdx.x] = (unsigned long long)min((uint64_t)fill, a.region_cap);
-    atomicAdd(&a.ctr->proposals, (unsigned long long)fill);
-    if ((uint64_t)fill > a.region_cap)
-      atomicAdd(&a.ctr->overflow, (unsigned long long)((uint64_t)fill - a.region_cap));
+    atomicAdd(&a.ctr->proposals, (unsigned long long)S.scal[1]);
+    atomicAdd(&a.ctr->overflow, (unsigned long long)S.scal[3]);
     atomicAdd(&a.ctr->dist_evals, evals);
     atomicAdd(&a.ctr->gathered, gathered);
   }
@@ -481,6 +459,7 @@ __global__ void __launch_bounds__(JT) k_join_bf16(JoinArgs a, int pair_cap) {
     mbar_init(S.bar, 1);
     fence_mbar_init();
     S.scal[1] = 0;
+    S.scal[3] = 0;
   }
   // zero the padding rows once: rows >= M of a node are never read as pairs but
   // feed the MMA tiles
@@ -607,11 +586,8 @@ __global__ void __launch_bounds__(JT) k_join_bf16(JoinArgs a, int pair_cap) {
   if (threadIdx.x == 0) {
     unsigned long long tot = 0;
     for (int w = 0; w < JT / 32; ++w) tot += red[w];
-    const int fill = S.scal[1];
-    a.region_cnt[blockIdx.x] = (unsigned long long)min((uint64_t)fill, a.region_cap);
-    atomicAdd(&a.ctr->proposals, (unsigned long long)fill);
-    if ((uint64_t)fill > a.region_cap)
-      atomicAdd(&a.ctr->overflow, (unsigned long long)((uint64_t)fill - a.region_cap));
+    atomicAdd(&a.ctr->proposals, (unsigned long long)S.scal[1]);
+    atomicAdd(&a.ctr->overflow, (unsigned long long)S.scal[3]);
     atomicAdd(&a.ctr->dist_evals, tot);
     atomicAdd(&a.ctr->reranked, reranked);
     atomicAdd(&a.ctr->gathered, gathered);

@@ -104,40 +104,6 @@ __device__ __forceinline__ float exact_value(float g, float4 ai, float4 aj) {
   return canon_finish<METRIC>(g, ai.w, aj.w);
 }
 
-// Proposals of one warp (up to two per lane) into the block's region.
-__device__ __forceinline__ void emit_props(const JoinArgs& a, int* fill, bool hp, int32_t tp,
-                                           uint64_t kp, bool hq, int32_t tq, uint64_t kq) {
-  const int lane = threadIdx.x & 31;
-  const unsigned bp = __ballot_sync(FULL, hp), bq = __ballot_sync(FULL, hq);
-  const int n = __popc(bp) + __popc(bq);
-  if (n == 0) return;
-  int base = 0;
-  if (lane == 0) base = atomicAdd(fill, n);
-  base = __shfl_sync(FULL, base, 0);
-  const unsigned lt = (1u << lane) - 1u;
-  const uint64_t region = (uint64_t)blockIdx.x * a.region_cap;
-  if (hp) {
-    const uint64_t pos = (uint64_t)base + __popc(bp & lt);
-    if (pos < a.region_cap) {
-      a.prop_tgt[region + pos] = tp;
-      a.prop_key[region + pos] = kp;
-      atomicAdd(&a.prop_cnt[tp], 1);
-    } else {
-      slots_insert(a.live_keys + (size_t)tp * a.K, a.K, kp);
-    }
-  }
-  if (hq) {
-    const uint64_t pos = (uint64_t)base + __popc(bp) + __popc(bq & lt);
-    if (pos < a.region_cap) {
-      a.prop_tgt[region + pos] = tq;
-      a.prop_key[region + pos] = kq;
-      atomicAdd(&a.prop_cnt[tq], 1);
-    } else {
-      slots_insert(a.live_keys + (size_t)tq * a.K, a.K, kq);
-    }
-  }
-}
-
 // Allowed partners of candidate i among the M candidates, as a bit mask over
 // j: j > i, j < M and the set test of Alg. 1 (S-Merge: the other set) or
 // Alg. 2 (J-Merge: not both in S1).  s1 = bit mask of candidates in S1.
@@ -149,40 +115,12 @@ __device__ __forceinline__ uint64_t partner_mask(int mode, int i, int M, uint64_
   return live & above & set;
 }
 
-// Writes the warp's proposals: each lane holds up to NP (target, key) slots
-// flagged in `has`; slot x of every lane goes out with one ballot, and one
-// shared atomic reserves the warp's span of the region.
-template <int NP>
-__device__ __forceinline__ void emit_many(const JoinArgs& a, int* fill, const bool (&has)[NP],
-                                          const int32_t (&tgt)[NP], const uint64_t (&key)[NP]) {
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  unsigned b[NP];
-  int total = 0;
-#pragma unroll
-  for (int x = 0; x < NP; ++x) {
-    b[x] = __ballot_sync(FULL, has[x]);
-    total += __popc(b[x]);
-  }
-  if (total == 0) return;
-  int base = 0;
-  if (lane == 0) base = atomicAdd(fill, total);
-  base = __shfl_sync(FULL, base, 0);
-  const uint64_t region = (uint64_t)blockIdx.x * a.region_cap;
-#pragma unroll
-  for (int x = 0; x < NP; ++x) {
-    if (has[x]) {
-      const uint64_t pos = (uint64_t)base + __popc(b[x] & lt);
-      if (pos < a.region_cap) {
-        a.prop_tgt[region + pos] = tgt[x];
-        a.prop_key[region + pos] = key[x];
-        atomicAdd(&a.prop_cnt[tgt[x]], 1);
-      } else {
-        slots_insert(a.live_keys + (size_t)tgt[x] * a.K, a.K, key[x]);
-      }
-    }
-    base += __popc(b[x]);
-  }
+// Offers the warp's proposals (up to 4 per lane) to UpdateNN; their bucket
+// slots are claimed now and written at the warp's next offer.
+using Sink = DeferredSink<4>;
+__device__ __forceinline__ void emit_many(const JoinArgs& a, Sink& sink, const bool (&has)[4],
+                                          const int32_t (&tgt)[4], const uint64_t (&key)[4]) {
+  sink.offer(a.bucket, a.bcnt, a.bcap, a.live_keys, a.K, has, tgt, key);
 }
 
 
@@ -260,7 +198,7 @@ __device__ __forceinline__ void cp_arrive(uint64_t* bar) {
 // ---------------------------------------------------------------------------
 template <int METRIC, typename RowPtr>
 __device__ __forceinline__ void node_fp32(const JoinArgs& a, const Rec& rc, int np,
-                                          const uint16_t* pairs, RowPtr row_ptr, int* fill) {
+                                          const uint16_t* pairs, RowPtr row_ptr, Sink& sink) {
   const int lane = threadIdx.x & 31;
   const int d = a.rows.d;
   for (int q0 = 0; q0 < np;) {
@@ -318,7 +256,7 @@ __device__ __forceinline__ void node_fp32(const JoinArgs& a, const Rec& rc, int 
       has[2 * t] = live && key[2 * t] < rc.kth[i];
       has[2 * t + 1] = live && key[2 * t + 1] < rc.kth[jj];
     }
-    emit_many<4>(a, fill, has, tgt, key);
+    emit_many(a, sink, has, tgt, key);
     q0 += 32 * pl;
   }
 }
@@ -329,7 +267,7 @@ __device__ __forceinline__ void node_fp32(const JoinArgs& a, const Rec& rc, int 
 template <int METRIC, bool HALF, typename RowPtr>
 __device__ __forceinline__ void node_tc(const JoinArgs& a, const Rec& rc, int np,
                                         uint16_t* pairs, int np0, RowPtr row_ptr, float* G,
-                                        int* fill, unsigned long long& reranked) {
+                                        Sink& sink, unsigned long long& reranked) {
   const int lane = threadIdx.x & 31;
   const int d = a.rows.d;
   const int dpad = (d + 15) & ~15;
@@ -407,7 +345,7 @@ __device__ __forceinline__ void node_tc(const JoinArgs& a, const Rec& rc, int np
           }
         }
       }
-      emit_many<4>(a, fill, has, tgt, key);
+      emit_many(a, sink, has, tgt, key);
       // entries up to q0 + 63 are consumed, so the front of the list is free
       const unsigned lt = (1u << lane) - 1u;
       const unsigned b0 = __ballot_sync(FULL, mark[0]), b1 = __ballot_sync(FULL, mark[1]);
@@ -422,25 +360,26 @@ __device__ __forceinline__ void node_tc(const JoinArgs& a, const Rec& rc, int np
   if (lane == 0) reranked += (unsigned long long)nr;
   for (int q0 = 0; q0 < nr; q0 += 32) {
     const int q = q0 + lane;
-    bool hp = false, hq = false;
-    int32_t tp = 0, tq = 0;
-    uint64_t kp = 0, kq = 0;
+    bool has[4] = {false, false, false, false};
+    int32_t tgt[4] = {0, 0, 0, 0};
+    uint64_t key[4] = {0ull, 0ull, 0ull, 0ull};
     if (q < nr) {
       const uint16_t pr = pairs[q];
       const int i = pr >> 8, jj = pr & 0xFF;
-      tp = rc.cid[i];
-      tq = rc.cid[jj];
+      const int32_t tp = rc.cid[i], tq = rc.cid[jj];
       const float4 ai = *(const float4*)(row_ptr(i) + dpad * 2);
       const float4 aj = *(const float4*)(row_ptr(jj) + dpad * 2);
       const float dist =
           a.use_bulk ? canon_dist_global4<METRIC>(a.rows.row(tp), a.rows.row(tq), d, ai.w, aj.w)
                      : canon_dist_global<METRIC>(a.rows.row(tp), a.rows.row(tq), d, ai.w, aj.w);
-      kp = make_key(dist, tq);
-      kq = make_key(dist, tp);
-      hp = kp < rc.kth[i];
-      hq = kq < rc.kth[jj];
+      tgt[0] = tp;
+      tgt[1] = tq;
+      key[0] = make_key(dist, tq);
+      key[1] = make_key(dist, tp);
+      has[0] = key[0] < rc.kth[i];
+      has[1] = key[1] < rc.kth[jj];
     }
-    emit_props(a, fill, hp, tp, kp, hq, tq, kq);
+    emit_many(a, sink, has, tgt, key);
   }
 }
 
@@ -471,8 +410,7 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) k_join_ring(JoinArgs a, Pip
   uint64_t* rowbar = recbar + NREC;
   uint16_t* pairs = (uint16_t*)(rowbar + NREC);
   float* G = (float*)((unsigned char*)pairs + (((size_t)P.pair_cap * 2 + 15) & ~(size_t)15));
-  int* fill = (int*)(smem + (size_t)W * P.warp_bytes);
-  unsigned long long* red = (unsigned long long*)(fill + 4);
+  unsigned long long* red = (unsigned long long*)(smem + (size_t)W * P.warp_bytes);
   if (lane == 0) {
     for (int x = 0; x < NREC; ++x) {
       mbar_init(recbar + x, 32);
@@ -480,10 +418,7 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) k_join_ring(JoinArgs a, Pip
     }
     fence_mbar_init();
   }
-  if (threadIdx.x == 0) {
-    *fill = 0;
-    red[0] = red[1] = red[2] = 0ull;
-  }
+  if (threadIdx.x < 8) red[threadIdx.x] = 0ull;
   __syncthreads();
 
   const int cpr = P.row_bytes >> 4;  // 16-byte chunks per row
@@ -491,6 +426,7 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) k_join_ring(JoinArgs a, Pip
   const int64_t g0 = (int64_t)blockIdx.x * W + warp;
   const int64_t count = a.N > g0 ? (a.N - 1 - g0) / GW + 1 : 0;  // nodes of this warp
   unsigned long long evals = 0, gathered = 0, reranked = 0;
+  Sink sink;
   bool failed = false;
 
   auto slot_of = [&](int64_t j) { return (int)(j % NREC); };
@@ -595,14 +531,16 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) k_join_ring(JoinArgs a, Pip
       const int np = list_pairs(a, rc, pairs, &np0);
       if (lane == 0) evals += (unsigned long long)np;
       if (TC) {
-        node_tc<METRIC, HALF>(a, rc, np, pairs, np0, row_ptr, G, fill, reranked);
+        node_tc<METRIC, HALF>(a, rc, np, pairs, np0, row_ptr, G, sink, reranked);
       } else {
-        node_fp32<METRIC>(a, rc, np, pairs, row_ptr, fill);
+        node_fp32<METRIC>(a, rc, np, pairs, row_ptr, sink);
       }
     }
     __syncwarp();
     ring_head += used;
   }
+  sink.finish(a.bucket, a.bcap, a.live_keys, a.K);
+  unsigned long long nprop = sink.nprop, ndirect = sink.ndirect;
   cp_wait_all();
   if (failed) {
     if (lane == 0) atomicOr(&a.ctr->err, (unsigned long long)DERR_WAIT_TIMEOUT);
@@ -617,22 +555,23 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) k_join_ring(JoinArgs a, Pip
     evals += __shfl_xor_sync(FULL, evals, o);
     gathered += __shfl_xor_sync(FULL, gathered, o);
     reranked += __shfl_xor_sync(FULL, reranked, o);
+    nprop += __shfl_xor_sync(FULL, nprop, o);
+    ndirect += __shfl_xor_sync(FULL, ndirect, o);
   }
   if (lane == 0) {
     atomicAdd(&red[0], evals);
     atomicAdd(&red[1], gathered);
     atomicAdd(&red[2], reranked);
+    atomicAdd(&red[3], nprop);
+    atomicAdd(&red[4], ndirect);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    const int f = *fill;
-    a.region_cnt[blockIdx.x] = (unsigned long long)min((uint64_t)f, a.region_cap);
-    atomicAdd(&a.ctr->proposals, (unsigned long long)f);
-    if ((uint64_t)f > a.region_cap)
-      atomicAdd(&a.ctr->overflow, (unsigned long long)((uint64_t)f - a.region_cap));
     atomicAdd(&a.ctr->dist_evals, red[0]);
     atomicAdd(&a.ctr->gathered, red[1]);
     atomicAdd(&a.ctr->reranked, red[2]);
+    atomicAdd(&a.ctr->proposals, red[3]);
+    atomicAdd(&a.ctr->overflow, red[4]);
   }
 }
 

@@ -584,15 +584,14 @@ __global__ void __launch_bounds__(BLOCK) k_build_records(int64_t N, int K, const
 }
 
 // ---------------------------------------------------------------------------
-// Bucketed UpdateNN: the join counted proposals per target; an exclusive scan
-// turns the counts into bucket offsets, a scatter pass moves every proposal
-// key into its target's bucket, and one warp per node merges its list with its
-// bucket (top-K distinct keys), sets the flags against the round-start
-// snapshot and counts c_t.
+// Bucketed UpdateNN: the join put every proposal into its target's bucket (or,
+// once the bucket was full, straight into the target's live list); one warp
+// per node merges its list with its bucket (top-K distinct keys), sets the
+// flags against the round-start snapshot and counts c_t.  The exclusive scan
+// below serves the sampler's reverse buckets.
 // ---------------------------------------------------------------------------
 
 constexpr int SCAN_TILE = 1024;  // elements per scan block (256 threads x 4)
-constexpr int SCATTER_SPLIT = 8;  // blocks per proposal region in the scatter
 
 __global__ void __launch_bounds__(256) k_scan_tiles(const int32_t* cnt, int64_t n,
                                                     unsigned long long* tile_sum) {
@@ -679,37 +678,6 @@ __global__ void __launch_bounds__(256) k_scan_apply(const int32_t* cnt, int64_t 
   if (blockIdx.x == 0 && threadIdx.x == 0) offs[n] = *total;
 }
 
-// SCATTER_SPLIT blocks per proposal region: moves each key into its target's
-// bucket.
-// Counts are consumed (decremented back to zero) to find the slot.
-__global__ void k_scatter(const int32_t* prop_tgt, const uint64_t* prop_key,
-                          const unsigned long long* region_cnt, uint64_t region_cap,
-                          int32_t* cnt, const unsigned long long* offs, uint64_t* bucket) {
-  constexpr int U = 8;  // proposals per thread in flight: independent atomics overlap
-  const uint64_t n = region_cnt[blockIdx.x];
-  const uint64_t base = (uint64_t)blockIdx.x * region_cap;
-  const uint64_t step = (uint64_t)blockDim.x * gridDim.y * U;
-  for (uint64_t o0 = ((uint64_t)blockIdx.y * blockDim.x) * U + threadIdx.x; o0 < n; o0 += step) {
-    int32_t tgt[U];
-    uint64_t key[U];
-    int pos[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const uint64_t o = o0 + (uint64_t)u * blockDim.x;
-      tgt[u] = o < n ? prop_tgt[base + o] : -1;
-      key[u] = o < n ? prop_key[base + o] : 0ull;
-    }
-    unsigned long long ob[U];  // bucket starts, loaded while the atomics are in flight
-#pragma unroll
-    for (int u = 0; u < U; ++u) ob[u] = tgt[u] >= 0 ? offs[tgt[u]] : 0ull;
-#pragma unroll
-    for (int u = 0; u < U; ++u) pos[u] = tgt[u] >= 0 ? atomicSub(&cnt[tgt[u]], 1) - 1 : 0;
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (tgt[u] >= 0) bucket[ob[u] + (uint64_t)pos[u]] = key[u];
-  }
-}
-
 __global__ void __launch_bounds__(BLOCK) k_merge_lists(MergeArgs a) {
   __shared__ unsigned long long red[WARPS_PER_BLOCK];
   __shared__ uint64_t stage[WARPS_PER_BLOCK][32];
@@ -723,7 +691,9 @@ __global__ void __launch_bounds__(BLOCK) k_merge_lists(MergeArgs a) {
     const int64_t v = w0 + p * nwarps;
     if (v >= a.N) continue;
     uint64_t cur = lane < K ? a.keys[(size_t)v * K + lane] : KEY_EMPTY;
-    const uint64_t b0 = a.offs[v], b1 = a.offs[v + 1];
+    const int cv = a.cnt[v];
+    const uint64_t b0 = (uint64_t)v * a.bcap, b1 = b0 + (uint64_t)min(cv, a.bcap);
+    if (lane == 0 && cv) a.cnt[v] = 0;  // the next round's join starts from zero
     for (uint64_t c = b0; c < b1; c += 32) {
       uint64_t x = c + lane < b1 ? a.bucket[c + lane] : KEY_EMPTY;
       const uint64_t kth = __shfl_sync(FULL, cur, K - 1);
@@ -1113,17 +1083,7 @@ cudaError_t launch_build_records(int64_t N, int K, const uint64_t* keys, const f
   return cudaGetLastError();
 }
 
-cudaError_t launch_bucket_update(const MergeArgs& a, const int32_t* prop_tgt,
-                                 const uint64_t* prop_key, const unsigned long long* region_cnt,
-                                 uint64_t region_cap, int regions, unsigned long long* tile_sum,
-                                 unsigned long long* total, cudaStream_t st) {
-  const int64_t ntiles = (a.N + SCAN_TILE - 1) / SCAN_TILE;
-  k_scan_tiles<<<(unsigned)ntiles, 256, 0, st>>>(a.cnt, a.N, tile_sum);
-  k_scan_sums<<<1, 1024, 0, st>>>(tile_sum, ntiles, total);
-  k_scan_apply<<<(unsigned)ntiles, 256, 0, st>>>(a.cnt, a.N, tile_sum,
-                                                 (unsigned long long*)a.offs, total);
-  k_scatter<<<dim3((unsigned)regions, SCATTER_SPLIT), 256, 0, st>>>(
-      prop_tgt, prop_key, region_cnt, region_cap, a.cnt, a.offs, a.bucket);
+cudaError_t launch_bucket_update(const MergeArgs& a, cudaStream_t st) {
   k_merge_lists<<<grid_for_warps(a.N), BLOCK, 0, st>>>(a);
   return cudaGetLastError();
 }

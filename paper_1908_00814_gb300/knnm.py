@@ -19,7 +19,7 @@ _LIB_PATH = Path(__file__).resolve().parent / "libknnm.so"
 L2, IP, COS, L1, CHI2, JACCARD = 0, 1, 2, 3, 4, 5
 FP32, BF16_RERANK, FP16_RERANK = 0, 1, 2
 SYMMETRIC, JOINT = 0, 1
-OPT_GRAPHS, OPT_REGION_CAP, OPT_WAIT_POLLS, OPT_FAIL_ALLOC = 1, 2, 3, 4
+OPT_GRAPHS, OPT_BUCKET_CAP, OPT_WAIT_POLLS, OPT_FAIL_ALLOC = 1, 2, 3, 4
 MAX_ROUNDS = 64
 METRICS = {"l2": L2, "ip": IP, "cos": COS, "l1": L1, "chi2": CHI2, "jaccard": JACCARD}
 
@@ -118,6 +118,7 @@ SIGNATURES = {
     "knnm_set_option": (_I, [_P, _I, _I]),
     "knnm_strerror": (ctypes.c_char_p, [_I]),
     "knnm_hash64": (_U64, [_U64, _U64, _U64, _U64, _U64]),
+    "knnm_list_widths": (_I, [ctypes.POINTER(Params), _I, _I64, _P, _P, _P]),
     "knnm_default_params": (None, [ctypes.POINTER(Params)]),
     "knnm_merge_symmetric": (_I, [_P, _P, _I64, _P, _P, _I64, _P, _I, ctypes.POINTER(Params),
                                   _P, _P, ctypes.POINTER(Stats)]),
@@ -197,6 +198,16 @@ def hash64(seed, t, stream, owner, member) -> int:
     return int(lib().knnm_hash64(seed & m, t & m, stream & m, owner & m, member & m))
 
 
+def list_widths(p: Params, mode: int, set_split: int):
+    """(K_keep, Kr, s) that a merge with these parameters uses (knnm_list_widths)."""
+    kk, kr, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    rc = lib().knnm_list_widths(ctypes.byref(p), mode, set_split, ctypes.byref(kk),
+                                ctypes.byref(kr), ctypes.byref(s))
+    if rc != 0:
+        raise KnnmError(rc, "invalid merge parameters")
+    return kk.value, kr.value, s.value
+
+
 def params(k=20, metric="l2", precision="fp32", max_iters=10, sample_rate=0.5, keep_ratio=0.5,
            delta=0.001, seed=0) -> Params:
     p = Params()
@@ -249,7 +260,7 @@ class Context:
         self._check(lib().knnm_set_option(self.h, OPT_GRAPHS, int(on)))
 
     def set_option(self, option: int, value: int):
-        """knnm_set_option (OPT_REGION_CAP, OPT_WAIT_POLLS, OPT_FAIL_ALLOC, ...)."""
+        """knnm_set_option (OPT_BUCKET_CAP, OPT_WAIT_POLLS, OPT_FAIL_ALLOC, ...)."""
         self._check(lib().knnm_set_option(self.h, option, int(value)))
 
     def close(self):
@@ -467,10 +478,7 @@ class Context:
         import torch
         N, d = X.shape
         K = p.k
-        K_keep = int(float(np.float32(p.keep_ratio)) * K)
-        if mode == JOINT and set_split == 0:
-            K_keep = K
-        Kr = K - K_keep
+        Kr = list_widths(p, mode, set_split)[1]
         dev = X.device
         ids = torch.empty((N, K), dtype=torch.int32, device=dev)
         dists = torch.empty((N, K), dtype=torch.float32, device=dev)

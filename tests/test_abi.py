@@ -63,3 +63,19 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(knnm, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         knnm.lib()
+
+
+@pytest.mark.parametrize("K", [1, 7, 10, 20, 31, 32])
+@pytest.mark.parametrize("r,rho", [(0.5, 0.5), (0.3, 0.25), (0.0, 1.0), (1.0, 0.1)])
+def test_list_widths_match_the_oracle(built_lib, orc, K, r, rho):
+    """The sizes the library derives (no GPU call): K_keep = floor(r K) as the
+    oracle's Divide keeps, Kr = K - K_keep, s = max(1, floor(rho K)); a build
+    (J-Merge of an empty graph) keeps all K."""
+    from paper_1908_00814_gb300 import knnm
+    p = knnm.params(k=K, keep_ratio=r, sample_rate=rho)
+    kk, kr, s = knnm.list_widths(p, knnm.SYMMETRIC, 100)
+    assert kk == orc.keep_count(K, r) and kr == K - kk
+    assert s == min(K, orc.sample_count(K, rho))
+    assert knnm.list_widths(p, knnm.JOINT, 0)[:2] == (K, 0)
+    with pytest.raises(knnm.KnnmError):
+        knnm.list_widths(knnm.params(k=33), knnm.SYMMETRIC, 100)

@@ -1,10 +1,10 @@
 """Paths that a normal run seldom or never takes, forced through context
 options of the C ABI and checked against the CPU oracle:
 
-* the join's direct insert: when a join block's proposal buffer is full, the
-  remaining proposals go straight into the live lists by ordered slot
-  insertion (the lock-free form of UpdateNN) instead of through the bucketed
-  update.  With tiny buffers most proposals take that path; the merged graph
+* the join's direct insert: when a target's proposal bucket is full, further
+  proposals for it go straight into its live list by ordered slot insertion
+  (the lock-free form of UpdateNN) instead of through the bucketed update.
+  With tiny buckets most proposals take that path; the merged graph
   must still equal the oracle's bit for bit (synchronous UpdateNN is the top-K
   of the round-start list and all proposals, whatever the insertion order);
 * a device-side wait that gives up: the join's waits for its staged rows are
@@ -62,13 +62,13 @@ def _inputs(orc, kind, n1, n2, d, K, seed):
     return X, G1, G2
 
 
-@pytest.mark.parametrize("region_cap", [16, 700])
+@pytest.mark.parametrize("bucket_cap", [1, 12])
 @pytest.mark.parametrize("precision,kind", [("fp32", "gmm"), ("bf16", "sift"), ("bf16", "gmm")])
-def test_direct_insert_path_is_bit_exact(torch, km, orc, region_cap, precision, kind):
+def test_direct_insert_path_is_bit_exact(torch, km, orc, bucket_cap, precision, kind):
     n1, n2, d, K, rounds = 1300, 1100, 32, 12, 6
     X, G1, G2 = _inputs(orc, kind, n1, n2, d, K, seed=31)
     ctx = km.Context(0)
-    ctx.set_option(km.OPT_REGION_CAP, region_cap)
+    ctx.set_option(km.OPT_BUCKET_CAP, bucket_cap)
     p = km.params(k=K, precision=precision, max_iters=rounds, delta=0.0, seed=4)
     gi, gd, st = ctx.merge_symmetric(cuda(torch, X[:n1]), cuda(torch, G1), cuda(torch, X[n1:]),
                                      cuda(torch, G2), p)
