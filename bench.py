@@ -9,9 +9,10 @@ before timing.  The whole merge (init + rounds + final merge) is one step.
 
 Reported: points merged per second of the BF16 tensor-core + FP32 re-rank path
 (the headline), the plain FP32 path beside it, recall@10 of the merged graph
-against the exact graph on 1,000 sampled nodes, the roofline of the dominant
-kernel, the end-to-end rate through the C ABI with host buffers, and the CPU
-oracle timed on a bounded sample of the same workload.
+against the exact graph on 10,000 sampled nodes, the roofline of the dominant
+kernel and of each round phase (sampler, join, top-k update), the end-to-end
+rate through the C ABI with host buffers, and the CPU oracle timed on a
+bounded sample of the same workload.
 
 Multi-GPU: the merge does not shard; N ranks run N independent replicas of the
 workload (weak scaling) and the value is the sum of their points over the
@@ -143,6 +144,28 @@ def oracle_sample(w, per_half, seed_off=0):
     return S1, G1, S2, G2
 
 
+def host_cpu():
+    """Host CPU of this run: logical cores available and the model name."""
+    model = None
+    arm_parts = {"0xd4f": "Arm Neoverse-V2", "0xd40": "Arm Neoverse-V1", "0xd0c": "Arm Neoverse-N1"}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                low = line.lower()
+                if low.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+                if low.startswith("cpu part") and model is None:
+                    part = line.split(":", 1)[1].strip().lower()
+                    model = arm_parts.get(part, "Arm CPU part " + part)
+    except OSError:
+        pass
+    if model is None:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
 def time_oracle_merge(w, S1, G1, S2, G2, seed=0):
     import oracle
     t0 = time.perf_counter()
@@ -168,7 +191,8 @@ def run_reference(args, w):
             "data": "synthetic", "config": workload_config(w, "fp32 (CPU oracle)"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"S-Merge of {per_half} rows of each half "
-                                       f"({2 * per_half} points) per step, single-threaded"},
+                                       f"({2 * per_half} points) per step, single-threaded",
+                             **host_cpu()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -834,11 +858,12 @@ def run_ours(args, w):
     recall = exact_recall(torch, Xd, out_bf[0], queries, K=10)
     dist_err = distance_error(torch, Xd, out_bf[0], out_bf[1], queries[:500])
 
-    # roofline of the dominant kernel (per-round device times from the library's events)
+    # roofline of each phase (per-round device times from the library's events)
     tot = {"sample": 0.0, "join": 0.0, "update": 0.0}
-    bytes_join = 0.0
+    nbytes = {"sample": 0.0, "join": 0.0, "update": 0.0}
     launches_join = 0
     launches = 0
+    N = w["n"]
     for st in st_bf:
         launches += st["kernel_launches"]
         tot["sample"] += sum(st["ms_sample"])
@@ -846,15 +871,32 @@ def run_ours(args, w):
         tot["update"] += sum(st["ms_update"])
         launches_join += st["rounds"]
         for r in range(st["rounds"]):
-            # per staged row: the BF16 row, its id, k-th key and error data;
-            # per re-ranked pair: both FP32 rows; per proposal: target + key;
-            # per node: the two list lengths
-            bytes_join += (st["gathered"][r] * (d * 2 + 4 + 8 + 16)
-                           + st["reranked"][r] * 2 * d * 4
-                           + st["proposals"][r] * 12 + w["n"] * 8)
+            G, P = st["gathered"][r], st["proposals"][r]
+            # sampler: lists and flags read, snapshot written, k-th keys; per
+            # list entry its forward id (written, read back), reverse key
+            # (written, read back) and in-edge count; per staged candidate
+            # its record entry (id, k-th key); per node the record header
+            # and the four set counts
+            nbytes["sample"] += N * K * (9 + 8 + 8 + 16 + 4) + N * (8 + 16 + 16) + G * 12
+            # join: per staged row the 16-bit row with its error data, its id
+            # and k-th key; per re-ranked pair both FP32 rows; per proposal its
+            # key and its target's count; per node the candidate counts
+            nbytes["join"] += (G * (d * 2 + 4 + 8 + 16) + st["reranked"][r] * 2 * d * 4
+                               + P * 12 + N * 8)
+            # update: per proposal its key; per node the list, the round-start
+            # snapshot and flags read, list and flags written, its count
+            nbytes["update"] += P * 8 + N * K * (8 + 8 + 1 + 8 + 1) + N * 8
     dominant = max(tot, key=tot.get)
+    bytes_join = nbytes["join"]
     achieved = bytes_join / (tot["join"] / 1000.0) / 1e9 if tot["join"] > 0 else 0.0
     hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    phase_roofline = {
+        ph: {"bound": "hbm", "achieved": nbytes[ph] / (tot[ph] / 1000.0) / 1e9 if tot[ph] else 0.0,
+             "peak": hbm, "unit": "GB/s",
+             "frac": nbytes[ph] / (tot[ph] / 1000.0) / 1e9 / hbm if tot[ph] else 0.0,
+             "algorithmic_bytes_per_merge": nbytes[ph] / len(st_bf),
+             "ms_per_merge": tot[ph] / len(st_bf)}
+        for ph in tot}
     traffic, traffic_note = join_traffic()
     roofline = {"kernel": "k_join_ring (BF16 tensor-core join)", "bound": "hbm",
                 "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
@@ -891,7 +933,7 @@ def run_ours(args, w):
         per_half = args.cpu_rows
         S1h, G1h, S2h, G2h = oracle_sample(w, per_half)
         t = time_oracle_merge(w, S1h, G1h, S2h, G2h)
-        cpu = {"value": 2 * per_half / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": 2 * per_half / t, "unit": UNIT, "cores": 1, "kind": "oracle", **host_cpu(),
                "sample": f"S-Merge of the first {per_half} rows of each half "
                          f"({2 * per_half} points), inputs from the oracle's own NN-Descent "
                          f"build, single-threaded, {t:.1f} s"}
@@ -907,7 +949,8 @@ def run_ours(args, w):
             "per_round": {k: st_bf[-1][k] for k in ("dist_evals", "proposals", "spilled",
                                                     "reranked", "gathered", "ms_sample",
                                                     "ms_join", "ms_update")},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "roofline": roofline, "phase_roofline": phase_roofline, "cpu_baseline": cpu,
+            "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches, "input_build_rounds": build_rounds}
     if not args.no_fp32:
         line["fp32_plain"] = {"value": world * w["n"] / (ms_fp / 1000.0), "ms_per_step": ms_fp,

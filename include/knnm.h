@@ -522,6 +522,35 @@ int knnm_step_tc_estimate(knnm_ctx* ctx, const float* X, int64_t n, int d, int m
                           int precision, const int32_t* pi, const int32_t* pj, int64_t P,
                           float* est, float* bound, float* canon);
 
+/* knnm_step_join restricted to the nodes u in [row_lo, row_hi): only the pairs
+ * of those nodes' candidate sets are compared (the local join of Alg. 1 /
+ * Alg. 2 for a slice of the nodes), and their proposals update the lists of
+ * every target, in or out of the range.  One rank's share of a round of the
+ * sharded S-Merge (nodes partitioned by id range); the full range is
+ * knnm_step_join. */
+int knnm_step_join_rows(knnm_ctx* ctx, int mode, const float* X1, int64_t nx1, const float* X2,
+                        int64_t N, int64_t set_split, int d, const knnm_params* params,
+                        int32_t* ids, float* dists, uint8_t* flags, int cap_new, int cap_old,
+                        const int32_t* new_ids, const int32_t* new_cnt, const int32_t* old_ids,
+                        const int32_t* old_cnt, int64_t row_lo, int64_t row_hi,
+                        int64_t* updates, int64_t* dist_evals);
+
+/* UpdateNN of rows whose proposals were applied on several devices (Alg. 1
+ * UpdateNN, synchronous reading: the new list is the top K of the round-start
+ * list and all proposals).  part_ids/part_dists [parts][n][K] (device) hold
+ * each part's list of the same n rows, each already the top K of the
+ * round-start list and that part's proposals; the result is the first K
+ * distinct (distance, id) entries of all parts, which is the top K of the
+ * round-start list and every part's proposals.  start_ids/start_dists/
+ * start_flags [n][K] are the round-start lists with the flags the sampler left;
+ * an output entry that was in its start list keeps that flag, any other is
+ * flagged new, and *updates receives how many such new entries there are (c_t
+ * of these rows).  Ids < 0 in a part are empty places. */
+int knnm_step_union(knnm_ctx* ctx, int64_t n, int K, int parts, const int32_t* part_ids,
+                    const float* part_dists, const int32_t* start_ids, const float* start_dists,
+                    const uint8_t* start_flags, int32_t* out_ids, float* out_dists,
+                    uint8_t* out_flags, int64_t* updates);
+
 /* Merge and Sort (Alg. 1 last step): first K distinct ids of each working list
  * merged with its rear list. */
 int knnm_step_final(knnm_ctx* ctx, int64_t N, int K, const int32_t* ids, const float* dists,

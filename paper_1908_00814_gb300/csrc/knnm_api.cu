@@ -1318,12 +1318,17 @@ extern "C" int knnm_step_sample(knnm_ctx* ctx, int64_t N, int K, const int32_t* 
   return read_counters(ctx, ctr);
 }
 
-extern "C" int knnm_step_join(knnm_ctx* ctx, int mode, const float* X1, int64_t nx1,
-                              const float* X2, int64_t N, int64_t set_split, int d,
-                              const knnm_params* params, int32_t* ids, float* dists,
-                              uint8_t* flags, int cap_new, int cap_old, const int32_t* new_ids,
-                              const int32_t* new_cnt, const int32_t* old_ids,
-                              const int32_t* old_cnt, int64_t* updates, int64_t* dist_evals) {
+namespace {
+
+// The join and UpdateNN of one round for the nodes u in [row_lo, row_hi)
+// (every node for the full range): only pairs of those nodes' candidate sets
+// are compared; their proposals update every target's list.
+int step_join_rows(knnm_ctx* ctx, int mode, const float* X1, int64_t nx1, const float* X2,
+                   int64_t N, int64_t set_split, int d, const knnm_params* params, int32_t* ids,
+                   float* dists, uint8_t* flags, int cap_new, int cap_old,
+                   const int32_t* new_ids, const int32_t* new_cnt_in, const int32_t* old_ids,
+                   const int32_t* old_cnt_in, int64_t row_lo, int64_t row_hi, int64_t* updates,
+                   int64_t* dist_evals) {
   if (!ctx) return KNNM_ERR_INVALID;
   ctx->err[0] = 0;
   int rc = check_rows(ctx, X1, nx1, X2, N, d);
@@ -1346,10 +1351,14 @@ extern "C" int knnm_step_join(knnm_ctx* ctx, int mode, const float* X1, int64_t 
   rc = choose_join(ctx, precision, params->metric, cap_new, cap_old, d,
                    d % 4 == 0 && aligned16(X1) && aligned16(X2 ? X2 : X1), &jp);
   if (rc) return rc;
+  if (row_lo < 0 || row_hi > N || row_lo > row_hi)
+    return fail(ctx, KNNM_ERR_INVALID, "node range [%lld, %lld) outside 0..%lld", (long long)row_lo,
+                (long long)row_hi, (long long)N);
   const bool tc = precision != KNNM_FP32;
+  const bool masked = row_lo > 0 || row_hi < N;
   const int bcap = proposal_slots(ctx, K);
   uint64_t *keys, *prev, *bucket;
-  int32_t* pcnt;
+  int32_t *pcnt, *mnew = nullptr, *mold = nullptr;
   float* norms;
   __nv_bfloat16* Xb;
   float4* aux;
@@ -1367,6 +1376,10 @@ extern "C" int knnm_step_join(knnm_ctx* ctx, int mode, const float* X1, int64_t 
     ctr = c.take<DevCounters>(1);
     pcnt = c.take<int32_t>((size_t)N);
     bucket = c.take<uint64_t>((size_t)N * bcap);
+    if (masked) {
+      mnew = c.take<int32_t>((size_t)N);
+      mold = c.take<int32_t>((size_t)N);
+    }
     Xe = tc && jp.pipe ? c.take<__nv_bfloat16>((size_t)N * jp.pa.dx) : nullptr;
     rec = jp.pipe ? c.take<unsigned char>((size_t)N * rec_bytes(jp.pa.cap)) : nullptr;
   };
@@ -1378,6 +1391,13 @@ extern "C" int knnm_step_join(knnm_ctx* ctx, int mode, const float* X1, int64_t 
   c1.base = (char*)ctx->arena;
   carve(c1);
   Rows rows{X1, X2 ? X2 : X1, nx1, d};
+  const int32_t* new_cnt = new_cnt_in;
+  const int32_t* old_cnt = old_cnt_in;
+  if (masked) {
+    KNNM_CUDA(launch_mask_counts(N, row_lo, row_hi, new_cnt_in, old_cnt_in, mnew, mold, st));
+    new_cnt = mnew;
+    old_cnt = mold;
+  }
   KNNM_CUDA(cudaMemsetAsync(ctr, 0, sizeof(DevCounters), st));
   KNNM_CUDA(cudaMemsetAsync(&ctr->err_row, 0xFF, 8, st));
   KNNM_CUDA(launch_pack((int64_t)N * K, ids, dists, keys, st));
@@ -1434,6 +1454,62 @@ extern "C" int knnm_step_join(knnm_ctx* ctx, int mode, const float* X1, int64_t 
                 (unsigned long long)ctx->host_ctr->err_row);
   if (updates) *updates = (int64_t)ctx->host_ctr->updates;
   if (dist_evals) *dist_evals = (int64_t)ctx->host_ctr->dist_evals;
+  return KNNM_OK;
+}
+
+}  // namespace
+
+extern "C" int knnm_step_join(knnm_ctx* ctx, int mode, const float* X1, int64_t nx1,
+                              const float* X2, int64_t N, int64_t set_split, int d,
+                              const knnm_params* params, int32_t* ids, float* dists,
+                              uint8_t* flags, int cap_new, int cap_old, const int32_t* new_ids,
+                              const int32_t* new_cnt, const int32_t* old_ids,
+                              const int32_t* old_cnt, int64_t* updates, int64_t* dist_evals) {
+  return step_join_rows(ctx, mode, X1, nx1, X2, N, set_split, d, params, ids, dists, flags,
+                        cap_new, cap_old, new_ids, new_cnt, old_ids, old_cnt, 0, N, updates,
+                        dist_evals);
+}
+
+extern "C" int knnm_step_join_rows(knnm_ctx* ctx, int mode, const float* X1, int64_t nx1,
+                                   const float* X2, int64_t N, int64_t set_split, int d,
+                                   const knnm_params* params, int32_t* ids, float* dists,
+                                   uint8_t* flags, int cap_new, int cap_old,
+                                   const int32_t* new_ids, const int32_t* new_cnt,
+                                   const int32_t* old_ids, const int32_t* old_cnt,
+                                   int64_t row_lo, int64_t row_hi, int64_t* updates,
+                                   int64_t* dist_evals) {
+  return step_join_rows(ctx, mode, X1, nx1, X2, N, set_split, d, params, ids, dists, flags,
+                        cap_new, cap_old, new_ids, new_cnt, old_ids, old_cnt, row_lo, row_hi,
+                        updates, dist_evals);
+}
+
+extern "C" int knnm_step_union(knnm_ctx* ctx, int64_t n, int K, int parts,
+                               const int32_t* part_ids, const float* part_dists,
+                               const int32_t* start_ids, const float* start_dists,
+                               const uint8_t* start_flags, int32_t* out_ids, float* out_dists,
+                               uint8_t* out_flags, int64_t* updates) {
+  if (!ctx) return KNNM_ERR_INVALID;
+  ctx->err[0] = 0;
+  if (n < 0 || K < 1 || K > 32 || parts < 1 || (n > 0 && (!part_ids || !part_dists ||
+      !start_ids || !start_dists || !start_flags || !out_ids || !out_dists || !out_flags)))
+    return fail(ctx, KNNM_ERR_INVALID, "bad union arguments");
+  cudaStream_t st = ctx->stream;
+  KNNM_CUDA(cudaSetDevice(ctx->device));
+  DevCounters* ctr = nullptr;
+  auto carve = [&](Carver& c) { ctr = c.take<DevCounters>(1); };
+  Carver c0;
+  carve(c0);
+  int rc = ensure_arena(ctx, c0.off);
+  if (rc) return rc;
+  Carver c1;
+  c1.base = (char*)ctx->arena;
+  carve(c1);
+  KNNM_CUDA(cudaMemsetAsync(ctr, 0, sizeof(DevCounters), st));
+  KNNM_CUDA(launch_union(n, K, parts, part_ids, part_dists, start_ids, start_dists, start_flags,
+                         out_ids, out_dists, out_flags, ctr, st));
+  rc = read_counters(ctx, ctr);
+  if (rc) return rc;
+  if (updates) *updates = (int64_t)ctx->host_ctr->updates;
   return KNNM_OK;
 }
 

@@ -631,6 +631,17 @@ cudaError_t launch_bucket_update(const MergeArgs& a, cudaStream_t st);
 cudaError_t launch_final(int64_t N, int K, const uint64_t* keys, int Kr, const uint64_t* rear,
                          int32_t* out_ids, float* out_dists, cudaStream_t st);
 
+// Candidate counts with every node outside [lo, hi) set to 0.
+cudaError_t launch_mask_counts(int64_t N, int64_t lo, int64_t hi, const int32_t* in_new,
+                               const int32_t* in_old, int32_t* out_new, int32_t* out_old,
+                               cudaStream_t st);
+// Per row: the first K distinct keys of `parts` lists [parts][n][K], flags
+// against the start lists, c_t added to ctr->updates.
+cudaError_t launch_union(int64_t n, int K, int parts, const int32_t* part_ids,
+                         const float* part_dists, const int32_t* start_ids,
+                         const float* start_dists, const uint8_t* start_flags, int32_t* out_ids,
+                         float* out_dists, uint8_t* out_flags, DevCounters* ctr, cudaStream_t st);
+
 // Conversions between the packed working lists and the (ids, dists) arrays.
 cudaError_t launch_pack(int64_t count, const int32_t* ids, const float* dists, uint64_t* keys,
                         cudaStream_t st);

@@ -792,6 +792,90 @@ __global__ void __launch_bounds__(BLOCK) k_merge_lists(MergeArgs a) {
   block_add(&a.ctr->updates, cnt, red);
 }
 
+// Candidate counts of the nodes in [lo, hi) kept, all others zeroed (a join
+// restricted to those nodes: every other node then has no pair).
+__global__ void k_mask_counts(int64_t N, int64_t lo, int64_t hi, const int32_t* in_new,
+                              const int32_t* in_old, int32_t* out_new, int32_t* out_old) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= N) return;
+  const bool own = u >= lo && u < hi;
+  out_new[u] = own ? in_new[u] : 0;
+  out_old[u] = own ? in_old[u] : 0;
+}
+
+// Top-K union of `parts` lists per row (UpdateNN applied to the union of the
+// proposals behind each partial list): the first K distinct keys of all parts,
+// flags against the round-start list (an entry already there keeps its flag,
+// any other is new), and c_t.  One warp per row.
+__global__ void __launch_bounds__(BLOCK) k_union(int64_t n, int K, int parts,
+                                                 const int32_t* part_ids, const float* part_dists,
+                                                 const int32_t* start_ids,
+                                                 const float* start_dists,
+                                                 const uint8_t* start_flags, int32_t* out_ids,
+                                                 float* out_dists, uint8_t* out_flags,
+                                                 DevCounters* ctr) {
+  __shared__ unsigned long long red[WARPS_PER_BLOCK];
+  __shared__ uint64_t stage[WARPS_PER_BLOCK][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
+  const int64_t w0 = (int64_t)blockIdx.x * WARPS_PER_BLOCK + w;
+  const int64_t passes = (n + nwarps - 1) / nwarps;
+  unsigned long long cnt = 0;
+  auto key_at = [&](const int32_t* I, const float* D, size_t at) {
+    const int32_t id = I[at];
+    return id < 0 ? KEY_EMPTY : make_key(D[at], id);
+  };
+  for (int64_t pass = 0; pass < passes; ++pass) {
+    const int64_t v = w0 + pass * nwarps;
+    if (v >= n) continue;  // warp-uniform
+    uint64_t cur = KEY_EMPTY;
+    for (int p = 0; p < parts; ++p) {
+      uint64_t e0 = cur;
+      uint64_t e1 = lane < K ? key_at(part_ids, part_dists, ((size_t)p * n + v) * K + lane)
+                             : KEY_EMPTY;
+      warp_sort64(e0, e1);
+      uint64_t p0 = __shfl_up_sync(FULL, e0, 1);
+      uint64_t p1 = __shfl_up_sync(FULL, e1, 1);
+      const uint64_t last0 = __shfl_sync(FULL, e0, 31);
+      if (lane == 0) p1 = last0;
+      const bool k0 = e0 != KEY_EMPTY && (lane == 0 || e0 != p0);
+      const bool k1 = e1 != KEY_EMPTY && e1 != p1;
+      const unsigned m0 = __ballot_sync(FULL, k0), m1 = __ballot_sync(FULL, k1);
+      const int pos0 = __popc(m0 & lanemask_lt()), pos1 = __popc(m0) + __popc(m1 & lanemask_lt());
+      stage[w][lane] = KEY_EMPTY;
+      __syncwarp();
+      if (k0 && pos0 < 32) stage[w][pos0] = e0;
+      if (k1 && pos1 < 32) stage[w][pos1] = e1;
+      __syncwarp();
+      cur = lane < K ? stage[w][lane] : KEY_EMPTY;
+      __syncwarp();
+    }
+    // flags against the round-start list (ascending, empty places last)
+    const uint64_t pk =
+        lane < K ? key_at(start_ids, start_dists, (size_t)v * K + lane) : KEY_EMPTY;
+    const uint8_t pf = lane < K ? start_flags[(size_t)v * K + lane] : FLAG_NEW;
+    int at = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const uint64_t probe = __shfl_sync(FULL, pk, at + step - 1);
+      if (probe <= cur) at += step;
+    }
+    const uint64_t lastk = __shfl_sync(FULL, pk, 31);
+    if (at == 31 && lastk <= cur) at = 32;
+    const int idx = at > 0 ? at - 1 : 0;
+    const uint64_t o = __shfl_sync(FULL, pk, idx);
+    const uint8_t of = (uint8_t)__shfl_sync(FULL, (int)pf, idx);
+    const bool found = cur != KEY_EMPTY && at > 0 && idx < K && o == cur;
+    if (lane < K) {
+      out_ids[(size_t)v * K + lane] = cur == KEY_EMPTY ? -1 : key_id(cur);
+      out_dists[(size_t)v * K + lane] = cur == KEY_EMPTY ? __int_as_float(0x7f800000) : key_dist(cur);
+      out_flags[(size_t)v * K + lane] = found ? of : FLAG_NEW;
+    }
+    cnt += __popc(__ballot_sync(FULL, lane < K && cur != KEY_EMPTY && !found));
+  }
+  block_add(&ctr->updates, cnt, red);
+}
+
 // ---------------------------------------------------------------------------
 // Merge and Sort with the rear lists (final step)
 // ---------------------------------------------------------------------------
@@ -1085,6 +1169,26 @@ cudaError_t launch_build_records(int64_t N, int K, const uint64_t* keys, const f
 
 cudaError_t launch_bucket_update(const MergeArgs& a, cudaStream_t st) {
   k_merge_lists<<<grid_for_warps(a.N), BLOCK, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mask_counts(int64_t N, int64_t lo, int64_t hi, const int32_t* in_new,
+                               const int32_t* in_old, int32_t* out_new, int32_t* out_old,
+                               cudaStream_t st) {
+  if (N == 0) return cudaSuccess;
+  k_mask_counts<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, lo, hi, in_new, in_old, out_new,
+                                                             out_old);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_union(int64_t n, int K, int parts, const int32_t* part_ids,
+                         const float* part_dists, const int32_t* start_ids,
+                         const float* start_dists, const uint8_t* start_flags, int32_t* out_ids,
+                         float* out_dists, uint8_t* out_flags, DevCounters* ctr, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_union<<<grid_for_warps(n), BLOCK, 0, st>>>(n, K, parts, part_ids, part_dists, start_ids,
+                                               start_dists, start_flags, out_ids, out_dists,
+                                               out_flags, ctr);
   return cudaGetLastError();
 }
 

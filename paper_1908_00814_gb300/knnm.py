@@ -133,6 +133,11 @@ SIGNATURES = {
                             _P, _I, _I, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int64),
                             ctypes.POINTER(ctypes.c_int64)]),
     "knnm_step_final": (_I, [_P, _I64, _I, _P, _P, _I, _P, _P, _P, _P]),
+    "knnm_step_join_rows": (_I, [_P, _I, _P, _I64, _P, _I64, _I64, _I, ctypes.POINTER(Params),
+                                 _P, _P, _P, _I, _I, _P, _P, _P, _P, _I64, _I64,
+                                 ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "knnm_step_union": (_I, [_P, _I64, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P,
+                             ctypes.POINTER(ctypes.c_int64)]),
     "knnm_step_tc_estimate": (_I, [_P, _P, _I64, _I, _I, _I, _P, _P, _I64, _P, _P, _P]),
     "knnm_step_sample_noalloc": (_I, [_P, _I64, _I, _P, _P, _P, _U64, _I, _I, _I, _I, _P, _P,
                                       _P, _P]),
@@ -520,6 +525,36 @@ class Context:
                                          _ptr(new_cnt), _ptr(old_ids), _ptr(old_cnt),
                                          ctypes.byref(upd), ctypes.byref(ev)))
         return int(upd.value), int(ev.value)
+
+    def step_join_rows(self, mode, X, set_split, p: Params, ids, dists, flags, cands, lo, hi):
+        """step_join for the nodes in [lo, hi) only (their proposals reach every row)."""
+        N, d = X.shape
+        new_ids, new_cnt, old_ids, old_cnt = cands
+        upd = ctypes.c_int64(0)
+        ev = ctypes.c_int64(0)
+        self._sync_stream()
+        self._check(lib().knnm_step_join_rows(self.h, mode, _ptr(X), N, None, N, set_split, d,
+                                              ctypes.byref(p), _ptr(ids), _ptr(dists),
+                                              _ptr(flags), new_ids.shape[1], old_ids.shape[1],
+                                              _ptr(new_ids), _ptr(new_cnt), _ptr(old_ids),
+                                              _ptr(old_cnt), lo, hi, ctypes.byref(upd),
+                                              ctypes.byref(ev)))
+        return int(upd.value), int(ev.value)
+
+    def step_union(self, part_ids, part_dists, start_ids, start_dists, start_flags):
+        """Top-K union of parts [P][n][K] against the start lists [n][K]:
+        (ids, dists, flags, c_t) of the n rows (device tensors)."""
+        import torch
+        P, n, K = part_ids.shape
+        oi = torch.empty((n, K), dtype=torch.int32, device=part_ids.device)
+        od = torch.empty((n, K), dtype=torch.float32, device=part_ids.device)
+        of = torch.empty((n, K), dtype=torch.uint8, device=part_ids.device)
+        upd = ctypes.c_int64(0)
+        self._sync_stream()
+        self._check(lib().knnm_step_union(self.h, n, K, P, _ptr(part_ids), _ptr(part_dists),
+                                          _ptr(start_ids), _ptr(start_dists), _ptr(start_flags),
+                                          _ptr(oi), _ptr(od), _ptr(of), ctypes.byref(upd)))
+        return oi, od, of, int(upd.value)
 
     def step_tc_estimate(self, X, pi, pj, metric="l2", precision="bf16"):
         """(estimate, bound, canonical) of each pair (pi[r], pj[r]) of rows of X,
