@@ -678,6 +678,79 @@ __global__ void __launch_bounds__(256) k_scan_apply(const int32_t* cnt, int64_t 
   if (blockIdx.x == 0 && threadIdx.x == 0) offs[n] = *total;
 }
 
+// The list `cur` (ascending, lanes >= K empty) after offering it the keys of
+// `x` (one per lane, KEY_EMPTY for none): the first K distinct keys of both.
+// Keys at or above the current K-th cannot enter (an equal key is already
+// held); a few survivors are inserted one by one, more are sorted and merged.
+__device__ __forceinline__ uint64_t offer_chunk(uint64_t cur, uint64_t x, int K, uint64_t* stage) {
+  const int lane = threadIdx.x & 31;
+  if (x >= __shfl_sync(FULL, cur, K - 1)) x = KEY_EMPTY;
+  unsigned live = __ballot_sync(FULL, x != KEY_EMPTY);
+  if (!live) return cur;
+  if (__popc(live) <= 6) {
+    // few survivors: insert them one by one (rank insertion across the warp)
+    while (live) {
+      const int src = __ffs(live) - 1;
+      live &= live - 1u;
+      const uint64_t y = __shfl_sync(FULL, x, src);
+      const uint64_t kk = __shfl_sync(FULL, cur, K - 1);
+      if (y >= kk || __any_sync(FULL, cur == y)) continue;
+      const int pos = __popc(__ballot_sync(FULL, cur < y));
+      const uint64_t up = __shfl_up_sync(FULL, cur, 1);
+      cur = lane == pos ? y : (lane > pos ? up : cur);
+      if (lane >= K) cur = KEY_EMPTY;
+    }
+    return cur;
+  }
+  {
+    // many survivors: sort the chunk and drop its repeats, keep the 32
+    // smallest of (list, chunk) and remove keys the list already holds; that
+    // is the answer unless repeats pushed distinct keys past 32
+    const uint64_t xs = warp_sort32(x);
+    const uint64_t xp = __shfl_up_sync(FULL, xs, 1);
+    const bool keep_x = xs != KEY_EMPTY && (lane == 0 || xs != xp);
+    const unsigned kx = __ballot_sync(FULL, keep_x);
+    stage[lane] = KEY_EMPTY;
+    __syncwarp();
+    if (keep_x) stage[__popc(kx & lanemask_lt())] = xs;
+    __syncwarp();
+    const uint64_t xd = stage[lane];  // sorted, repeats dropped, KEY_EMPTY after
+    __syncwarp();
+    const uint64_t m = warp_merge_lo32(cur, xd);
+    const uint64_t mp = __shfl_up_sync(FULL, m, 1);
+    const bool keep = m != KEY_EMPTY && (lane == 0 || m != mp);
+    const unsigned km = __ballot_sync(FULL, keep);
+    if (__popc(km) >= K || __shfl_sync(FULL, m, 31) == KEY_EMPTY) {
+      stage[lane] = KEY_EMPTY;
+      __syncwarp();
+      if (keep) stage[__popc(km & lanemask_lt())] = m;
+      __syncwarp();
+      cur = lane < K ? stage[lane] : KEY_EMPTY;
+      __syncwarp();
+      return cur;
+    }
+  }
+  uint64_t e0 = cur, e1 = x;
+  warp_sort64(e0, e1);
+  uint64_t p0 = __shfl_up_sync(FULL, e0, 1);
+  uint64_t p1 = __shfl_up_sync(FULL, e1, 1);
+  const uint64_t last0 = __shfl_sync(FULL, e0, 31);
+  if (lane == 0) p1 = last0;
+  const bool k0 = e0 != KEY_EMPTY && (lane == 0 || e0 != p0);
+  const bool k1 = e1 != KEY_EMPTY && e1 != p1;
+  const unsigned m0 = __ballot_sync(FULL, k0), m1 = __ballot_sync(FULL, k1);
+  const unsigned lt = (1u << lane) - 1u;
+  const int pos0 = __popc(m0 & lt), pos1 = __popc(m0) + __popc(m1 & lt);
+  stage[lane] = KEY_EMPTY;
+  __syncwarp();
+  if (k0 && pos0 < 32) stage[pos0] = e0;
+  if (k1 && pos1 < 32) stage[pos1] = e1;
+  __syncwarp();
+  cur = lane < K ? stage[lane] : KEY_EMPTY;
+  __syncwarp();
+  return cur;
+}
+
 __global__ void __launch_bounds__(BLOCK) k_merge_lists(MergeArgs a) {
   __shared__ unsigned long long red[WARPS_PER_BLOCK];
   __shared__ uint64_t stage[WARPS_PER_BLOCK][32];
@@ -694,73 +767,33 @@ __global__ void __launch_bounds__(BLOCK) k_merge_lists(MergeArgs a) {
     const int cv = a.cnt[v];
     const uint64_t b0 = (uint64_t)v * a.bcap, b1 = b0 + (uint64_t)min(cv, a.bcap);
     if (lane == 0 && cv) a.cnt[v] = 0;  // the next round's join starts from zero
-    for (uint64_t c = b0; c < b1; c += 32) {
-      uint64_t x = c + lane < b1 ? a.bucket[c + lane] : KEY_EMPTY;
-      const uint64_t kth = __shfl_sync(FULL, cur, K - 1);
-      if (x >= kth) x = KEY_EMPTY;
-      unsigned live = __ballot_sync(FULL, x != KEY_EMPTY);
-      if (!live) continue;
-      if (__popc(live) <= 6) {
-        // few survivors: insert them one by one (rank insertion across the warp)
-        while (live) {
-          const int src = __ffs(live) - 1;
-          live &= live - 1u;
-          const uint64_t y = __shfl_sync(FULL, x, src);
-          const uint64_t kk = __shfl_sync(FULL, cur, K - 1);
-          if (y >= kk || __any_sync(FULL, cur == y)) continue;
-          const int pos = __popc(__ballot_sync(FULL, cur < y));
-          const uint64_t up = __shfl_up_sync(FULL, cur, 1);
-          cur = lane == pos ? y : (lane > pos ? up : cur);
-          if (lane >= K) cur = KEY_EMPTY;
-        }
-        continue;
+    // The bucket in groups of four 32-key chunks: each lane's smallest key of
+    // the group goes first (those are the likely winners), which lowers the
+    // K-th key before the other three chunks are offered, so that most of
+    // their keys are rejected by one compare.
+    if (b1 - b0 <= 32) {
+      cur = offer_chunk(cur, b0 + lane < b1 ? a.bucket[b0 + lane] : KEY_EMPTY, K, stage[w]);
+    } else for (uint64_t g = b0; g < b1; g += 128) {
+      uint64_t x[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint64_t at = g + 32 * q + lane;
+        x[q] = at < b1 ? a.bucket[at] : KEY_EMPTY;
       }
-      {
-        // many survivors: sort the chunk and drop its repeats, keep the 32
-        // smallest of (list, chunk) and remove keys the list already holds;
-        // that is the answer unless repeats pushed distinct keys past 32
-        const uint64_t xs = warp_sort32(x);
-        const uint64_t xp = __shfl_up_sync(FULL, xs, 1);
-        const bool keep_x = xs != KEY_EMPTY && (lane == 0 || xs != xp);
-        const unsigned kx = __ballot_sync(FULL, keep_x);
-        stage[w][lane] = KEY_EMPTY;
-        __syncwarp();
-        if (keep_x) stage[w][__popc(kx & lanemask_lt())] = xs;
-        __syncwarp();
-        const uint64_t xd = stage[w][lane];  // sorted, repeats dropped, KEY_EMPTY after
-        __syncwarp();
-        const uint64_t m = warp_merge_lo32(cur, xd);
-        const uint64_t mp = __shfl_up_sync(FULL, m, 1);
-        const bool keep = m != KEY_EMPTY && (lane == 0 || m != mp);
-        const unsigned km = __ballot_sync(FULL, keep);
-        if (__popc(km) >= K || __shfl_sync(FULL, m, 31) == KEY_EMPTY) {
-          stage[w][lane] = KEY_EMPTY;
-          __syncwarp();
-          if (keep) stage[w][__popc(km & lanemask_lt())] = m;
-          __syncwarp();
-          cur = lane < K ? stage[w][lane] : KEY_EMPTY;
-          __syncwarp();
-          continue;
+      uint64_t mn = x[0];
+      int mi = 0;
+#pragma unroll
+      for (int q = 1; q < 4; ++q)
+        if (x[q] < mn) {
+          mn = x[q];
+          mi = q;
         }
-      }
-      uint64_t e0 = cur, e1 = x;
-      warp_sort64(e0, e1);
-      uint64_t p0 = __shfl_up_sync(FULL, e0, 1);
-      uint64_t p1 = __shfl_up_sync(FULL, e1, 1);
-      const uint64_t last0 = __shfl_sync(FULL, e0, 31);
-      if (lane == 0) p1 = last0;
-      const bool k0 = e0 != KEY_EMPTY && (lane == 0 || e0 != p0);
-      const bool k1 = e1 != KEY_EMPTY && e1 != p1;
-      const unsigned m0 = __ballot_sync(FULL, k0), m1 = __ballot_sync(FULL, k1);
-      const unsigned lt = (1u << lane) - 1u;
-      const int pos0 = __popc(m0 & lt), pos1 = __popc(m0) + __popc(m1 & lt);
-      stage[w][lane] = KEY_EMPTY;
-      __syncwarp();
-      if (k0 && pos0 < 32) stage[w][pos0] = e0;
-      if (k1 && pos1 < 32) stage[w][pos1] = e1;
-      __syncwarp();
-      cur = lane < K ? stage[w][lane] : KEY_EMPTY;
-      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q == mi) x[q] = KEY_EMPTY;
+      cur = offer_chunk(cur, mn, K, stage[w]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cur = offer_chunk(cur, x[q], K, stage[w]);
     }
     // flags against the round-start snapshot: an entry is old when the same key
     // was in the list at round start.  The snapshot is sorted ascending (empty
