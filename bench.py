@@ -43,6 +43,7 @@ from paper_1908_00814_gb300 import datagen  # noqa: E402
 WORKLOAD = "smerge_sift_1m_d128_k20"
 METRIC = "points merged/sec at recall@10>=0.95 (BF16+rerank vs FP32 plain); serving p50/p99 batch latency"
 UNIT = "points/s"
+BUILD_RATE_960 = 0.75  # sample rate of the 960-d workload's input builds
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
@@ -298,10 +299,12 @@ def distance_error(torch, X_dev, ids_dev, dists_dev, queries, metric="l2"):
 SERVE = "serve_sift_2m_d128_k16"
 
 
-def run_serving(args, torch, knnm, ctx):
+def run_serving(args, torch, knnm, ctx, fp32_arm=False):
     """Serving loop (J-Merge of raw batches into a resident graph): a closed-loop
     run gives the saturation rate, then an open-loop run with Poisson arrivals
-    at 0.8 x that rate gives the batch latencies."""
+    at 0.8 x that rate gives the batch latencies.  With fp32_arm, the same
+    closed-loop batches are also merged one at a time by a plain FP32 server
+    (one slot, no CUDA graphs, no overlap) from the same resident graph."""
     import threading
     w = datagen.WORKLOADS[SERVE]
     n0 = args.serve_resident or w["n"]
@@ -319,6 +322,12 @@ def run_serving(args, torch, knnm, ctx):
                     delta=0.001, seed=0)
     srv = knnm.Server(X0, G0, p, slots=slots, capacity_rows=total, max_batch_rows=64000,
                       use_graphs=True)
+    plain = None
+    if fp32_arm:
+        p32 = knnm.params(k=K, precision="fp32", max_iters=w["rounds"],
+                          sample_rate=w["sample_rate"], delta=0.001, seed=0)
+        plain = knnm.Server(X0, G0, p32, slots=1, capacity_rows=total, max_batch_rows=64000,
+                            use_graphs=False)
     del X0, G0
     off = n0
     next_id = [1]
@@ -332,15 +341,39 @@ def run_serving(args, torch, knnm, ctx):
             off += int(b)
         return out
 
-    def closed(batch_list):
+    def closed(batch_list, server=None):
+        server = server or srv
         t0 = time.perf_counter()
         for rid, B in batch_list:
-            srv.submit(B, rid)
-        infos = [srv.wait(rid, out=False)[2] for rid, _ in batch_list]
+            server.submit(B, rid)
+        infos = [server.wait(rid, out=False)[2] for rid, _ in batch_list]
         return time.perf_counter() - t0, infos
 
-    closed(cut("warm"))
-    wall, infos_c = closed(cut("closed"))
+    warm = cut("warm")
+    closed(warm)
+    closed_list = cut("closed")
+    wall, infos_c = closed(closed_list)
+    recall_closed = None
+    if fp32_arm:  # the serving graph after the same batches the FP32 arm merges
+        Xc, idc, _ = srv.resident(device="cuda")
+        qc = datagen.sample_nodes(Xc.shape[0], args.recall_queries, seed=1)
+        recall_closed = exact_recall(torch, Xc, idc, qc, K=10)
+        del Xc, idc
+    plain_res = None
+    if plain is not None:
+        closed(warm, plain)
+        wall_p, infos_p = closed(closed_list, plain)
+        Xp, idp, _ = plain.resident(device="cuda")
+        plain.close()
+        qp = datagen.sample_nodes(Xp.shape[0], args.recall_queries, seed=1)
+        rows_p = int(sizes["closed"].sum())
+        plain_res = {"server": "FP32, one slot, no CUDA graphs (batches merged one at a time)",
+                     "batches": nb, "rows": rows_p, "wall_s": wall_p,
+                     "rows_per_s": rows_p / wall_p,
+                     "mean_request_ms": float(np.mean([i["run_ms"] for i in infos_p])),
+                     "recall_at_10_end": exact_recall(torch, Xp, idp, qp, K=10),
+                     "resident_rows_end": int(Xp.shape[0])}
+        del Xp, idp
     rows_c = int(sizes["closed"].sum())
     sat_rate = nb / wall
     lam = 0.8 * sat_rate
@@ -380,13 +413,19 @@ def run_serving(args, torch, knnm, ctx):
     queries = datagen.sample_nodes(Xr.shape[0], args.recall_queries, seed=1)
     recall = exact_recall(torch, Xr, idr, queries, K=10)
     rows_o = int(sizes["open"].sum())
-    return {
+
+    def breakdown(infos):
+        return {k: float(np.mean([i[k] for i in infos]))
+                for k in ("queue_ms", "run_ms", "merge_ms", "init_ms", "rounds_ms", "final_ms",
+                          "commit_ms")}
+    out = {
         "workload": SERVE, "resident_rows_start": n0, "resident_rows_end": int(Xr.shape[0]),
         "d": d, "k": K, "metric": "l2", "precision": "bf16_rerank", "graphs": True,
         "slots": slots, "batch_sizes": "lognormal, median 8000, sigma 1.0, clipped 1000-64000",
         "closed_loop": {"batches": nb, "rows": rows_c, "wall_s": wall,
                         "rows_per_s": rows_c / wall, "batches_per_s": sat_rate,
-                        "mean_rounds": float(np.mean([i["rounds"] for i in infos_c]))},
+                        "mean_rounds": float(np.mean([i["rounds"] for i in infos_c])),
+                        "recall_at_10_after": recall_closed},
         "open_loop": {"batches": nb, "rows": rows_o, "arrival_rate_per_s": lam,
                       "arrivals": "Poisson, 0.8 x closed-loop batches/s", "wall_s": wall_o,
                       "rows_per_s": rows_o / wall_o, "p50_ms": nearest_rank(lat, 0.50),
@@ -395,7 +434,39 @@ def run_serving(args, torch, knnm, ctx):
                       "clocks": clocks},
         "max_concurrent": stats["max_concurrent"], "failed": stats["failed"],
         "recall_at_10_end": recall,
+        "request_breakdown_ms": {"closed_loop": breakdown(infos_c),
+                                 "open_loop": breakdown(infos_o)},
     }
+    if plain_res is not None:
+        out["fp32_plain_closed_loop"] = plain_res
+        out["closed_loop_speedup_over_fp32_plain"] = (rows_c / wall) / plain_res["rows_per_s"]
+    return out
+
+
+def run_serve_workload(args):
+    """One JSON line for the serving workload: closed- and open-loop runs of the
+    BF16 serving loop and the plain FP32 server on the same batches."""
+    import torch
+    from paper_1908_00814_gb300 import build as kbuild, knnm
+    kbuild.build()
+    torch.cuda.set_device(0)
+    ctx = knnm.Context(0)
+    res = run_serving(args, torch, knnm, ctx, fp32_arm=not args.no_fp32)
+    ctx.close()
+    cl = res["closed_loop"]
+    line = {"metric": "serving rows merged/sec (closed loop) with p50/p99 batch latency "
+                      "(open loop)",
+            "value": cl["rows_per_s"], "unit": "rows/s", "n_gpus": 1,
+            "steps": cl["batches"], "warmup": args.serve_slots,
+            "ms_per_step": 1000.0 * cl["wall_s"] / cl["batches"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16+f32", "data": "synthetic",
+            "config": {"workload": SERVE, "resident_rows": res["resident_rows_start"],
+                       "batches_per_phase": cl["batches"], "slots": res["slots"],
+                       "batch_sizes": res["batch_sizes"]},
+            "serving": res}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def join_traffic():
@@ -733,8 +804,11 @@ def run_other(args, name):
         merge = "joint (Alg. 2)"
     else:
         for metric, precs in (("l1", ("fp32",)), ("l2", ("fp32", "fp16", "bf16"))):
-            bp = knnm.params(k=K, metric=metric, precision="fp32", max_iters=10, delta=0.001,
-                             seed=11)
+            # input graphs: 10-round NN-Descent builds of each half at sample
+            # rate 0.75 (at 0.5 the inputs capped the merged graph at recall
+            # 0.956 for L2 and 0.92 for L1)
+            bp = knnm.params(k=K, metric=metric, precision="fp32", max_iters=10,
+                             sample_rate=BUILD_RATE_960, delta=0.001, seed=11)
             G1, _, _ = ctx.build(S1, bp)
             bp.seed = 12
             G2, _, _ = ctx.build(S2, bp)
@@ -768,6 +842,10 @@ def run_other(args, name):
         print(f"# tree: {ms:.1f} ms", file=sys.stderr, flush=True)
         head = runs["l2_fp32"]
         merge = "symmetric (Alg. 1) + merge tree"
+    inputs = {"symmetric": f"NN-Descent builds of each half, 10 rounds, sample rate "
+                           f"{BUILD_RATE_960}",
+              "symmetric_chi2": "NN-Descent builds of each half, 10 rounds",
+              "joint": "NN-Descent build of the first half, 10 rounds"}.get(w["kind"])
     line = {"metric": METRIC, "value": head["points_per_s"], "unit": UNIT, "n_gpus": 1,
             "steps": steps, "warmup": warmup, "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -775,7 +853,7 @@ def run_other(args, name):
             "config": {"workload": name, "merge": merge, "n": n, "d": d, "k": K,
                        "metric": w["metric"], "max_rounds": w["rounds"],
                        "sample_rate": w["sample_rate"], "delta": 0.001,
-                       "recall_queries": len(queries),
+                       "recall_queries": len(queries), "inputs": inputs,
                        "l2_flush": "inputs larger than L2"},
             "runs": runs}
     print(json.dumps(line), flush=True)
@@ -990,7 +1068,7 @@ def main():
                     choices=[WORKLOAD, "jmerge_gmm_2m_d96_k16_cos", "smerge_gist_1m_d960_k20",
                              "hmerge_sift_1m_d128_k20", "hsearch_sift_1m_d128_k20",
                              "smerge_nuswide_260k_d500_k20_chi2",
-                             "smerge_kosarak_75k_k20_jaccard"],
+                             "smerge_kosarak_75k_k20_jaccard", "serve_sift_2m_d128_k16"],
                     help="another merge workload (one JSON line of its own)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-batches", type=int, default=16)
@@ -1011,6 +1089,8 @@ def main():
         return run_search(args, args.workload)
     if args.workload == "smerge_kosarak_75k_k20_jaccard":
         return run_sets(args, args.workload)
+    if args.workload == SERVE:
+        return run_serve_workload(args)
     if args.workload != WORKLOAD:
         return run_other(args, args.workload)
     return run_ours(args, w)

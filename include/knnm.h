@@ -381,6 +381,15 @@ typedef struct {
   double queue_ms;        /* submit -> admission */
   double run_ms;          /* admission -> commit done */
   double latency_ms;      /* submit -> commit done */
+  /* where run_ms goes: the J-Merge call (host clock; it waits for the
+   * snapshot copy, copies the batch in and runs init, rounds and final merge),
+   * its device times of init (Divide / Append / Initialize over the snapshot
+   * and batch rows), rounds and final merge, and the commit (host clock from
+   * queuing the commit to its completion, including the wait for the commit
+   * stream) */
+  double merge_ms;
+  float init_ms, rounds_ms, final_ms;
+  double commit_ms;
 } knnm_request_info;
 
 typedef struct {

@@ -223,10 +223,15 @@ int run_batch(knnm_server* S, Slot* sl, Request* r) {
   knnm_params p = S->params;
   p.seed = hash5(S->params.seed, 0, STREAM_SERVE, r->id, 0);
   knnm_stats st;
+  const auto t_merge = Clock::now();
   rc = knnm_merge_joint(sl->ctx, S->X, n_snap, sl->snap_ids, sl->batch, r->rows, S->d, &p,
                         sl->out_ids, reinterpret_cast<float*>(sl->out_dists), &st);
   if (rc) return sfail(S, rc, "request %llu: %s", (unsigned long long)r->id,
                        knnm_last_error(sl->ctx));
+  r->info.merge_ms = ms_between(t_merge, Clock::now());
+  r->info.init_ms = st.ms_init;
+  r->info.rounds_ms = st.ms_rounds;
+  r->info.final_ms = st.ms_final;
   r->info.rounds = st.rounds;
   int64_t evals = 0;
   for (int t = 0; t < st.rounds; ++t) evals += st.dist_evals[t];
@@ -238,6 +243,7 @@ int run_batch(knnm_server* S, Slot* sl, Request* r) {
   SRV_CUDA(cudaMemcpyAsync(r->dists.data(), sl->out_dists + (size_t)n_snap * S->K,
                            r->dists.size() * 4, cudaMemcpyDeviceToHost, sl->stream));
   SRV_CUDA(cudaStreamSynchronize(sl->stream));
+  const auto t_commit = Clock::now();
   {
     std::lock_guard<std::mutex> g(S->mu);
     const int64_t base = S->n_committed;
@@ -253,6 +259,7 @@ int run_batch(knnm_server* S, Slot* sl, Request* r) {
     S->inflight_rows -= r->rows;
   }
   SRV_CUDA(cudaEventSynchronize(sl->ev_commit));
+  r->info.commit_ms = ms_between(t_commit, Clock::now());
   return KNNM_OK;
 }
 

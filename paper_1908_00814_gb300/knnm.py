@@ -72,7 +72,10 @@ class RequestInfo(ctypes.Structure):
                 ("snapshot_commits", ctypes.c_int64), ("commit_seq", ctypes.c_int64),
                 ("commit_base", ctypes.c_int64), ("dist_evals", ctypes.c_int64),
                 ("slot", ctypes.c_int), ("queue_ms", ctypes.c_double),
-                ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+                ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double),
+                ("merge_ms", ctypes.c_double), ("init_ms", ctypes.c_float),
+                ("rounds_ms", ctypes.c_float), ("final_ms", ctypes.c_float),
+                ("commit_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
