@@ -581,7 +581,6 @@ struct PipeArgs {
   int nstages;               // unused by the ring kernel
   int cw;                    // warps per block
   int ring_rows;             // rows in each warp's ring
-  unsigned long long cpr_inv;  // ceil(2^32 / (row_bytes / 16)): chunk -> row by multiply-shift
   int warp_bytes;            // shared memory per warp
   int row_bytes;             // bytes copied per candidate row
   int row_stride;            // bytes between staged rows

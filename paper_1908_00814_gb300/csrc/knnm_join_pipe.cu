@@ -5,10 +5,11 @@
 // shared memory holds a ring of candidate rows, three candidate-record slots
 // (ids, round-start k-th keys, norms; written by the sampler) and a pair list.
 // While it computes node j it already has the rows of node j+1 and the record
-// of node j+2 in flight: 16-byte asynchronous copies (cp.async, LSU path)
-// issued by all 32 lanes, so each node costs a few warp instructions of copy
-// issue instead of one TMA request per row.  Node j+1's rows go right after
-// node j's in the ring when both fit, else after node j is done.
+// of node j+2 in flight: 1-D bulk copies on the TMA engine (cp.async.bulk, one
+// per row, issued by one lane per row, completion counted in bytes on the
+// slot's mbarrier), so staging a node's rows costs one or two warp
+// instructions.  Node j+1's rows go right after node j's in the ring when both
+// fit, else after node j is done.
 //   * FP32: the allowed pairs (set masks of Alg. 1 / Alg. 2, from 64-bit
 //     candidate masks) are listed, then each lane computes one or two pairs at
 //     a time, canonical in-order FP32 from the ring.
@@ -124,12 +125,6 @@ __device__ __forceinline__ void emit_many(const JoinArgs& a, Sink& sink, const b
 }
 
 
-__device__ __forceinline__ void cp16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
-               : "memory");
-}
-// Every cp.async of this lane has landed (committed or not).
-__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Bounded wait of the whole warp: true only when every lane saw the phase
 // complete, so that a timeout sends all lanes down the same path.
@@ -185,12 +180,6 @@ __device__ __forceinline__ int list_pairs(const JoinArgs& a, const Rec& rc, uint
   }
   __syncwarp();
   return np;
-}
-
-// cp.async completions of this lane arrive on `bar` (counted in its 32 arrivals).
-__device__ __forceinline__ void cp_arrive(uint64_t* bar) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -385,8 +374,8 @@ __device__ __forceinline__ void node_tc(const JoinArgs& a, const Rec& rc, int np
 
 // ---------------------------------------------------------------------------
 // The kernel.  Per warp: NREC record slots, each with two mbarriers (record
-// landed, rows landed) completed by the lanes' cp.async arrivals; a FIFO ring
-// of R rows.  Rows of up to AHEAD nodes beyond the current one are in flight
+// landed, rows landed) armed by lane 0 with the bytes to expect and completed
+// by the bulk copies; a FIFO ring of R rows.  Rows of up to AHEAD nodes beyond the current one are in flight
 // whenever the ring has room.
 // ---------------------------------------------------------------------------
 constexpr int NREC = 3;
@@ -413,15 +402,14 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) k_join_ring(JoinArgs a, Pip
   unsigned long long* red = (unsigned long long*)(smem + (size_t)W * P.warp_bytes);
   if (lane == 0) {
     for (int x = 0; x < NREC; ++x) {
-      mbar_init(recbar + x, 32);
-      mbar_init(rowbar + x, 32);
+      mbar_init(recbar + x, 1);
+      mbar_init(rowbar + x, 1);
     }
     fence_mbar_init();
   }
   if (threadIdx.x < 8) red[threadIdx.x] = 0ull;
   __syncthreads();
 
-  const int cpr = P.row_bytes >> 4;  // 16-byte chunks per row
   const int64_t GW = (int64_t)gridDim.x * W;
   const int64_t g0 = (int64_t)blockIdx.x * W + warp;
   const int64_t count = a.N > g0 ? (a.N - 1 - g0) / GW + 1 : 0;  // nodes of this warp
@@ -444,27 +432,27 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) k_join_ring(JoinArgs a, Pip
   auto fetch_rec = [&](int64_t j) {
     const unsigned char* src = P.rec + (size_t)(g0 + j * GW) * RB;
     unsigned char* dst = rec_at(j);
-    for (int c = lane; c < (RB >> 4); c += 32) cp16(dst + c * 16, src + c * 16);
-    cp_arrive(recbar + slot_of(j));
+    if (lane == 0) {
+      mbar_arrive_expect_tx(recbar + slot_of(j), (uint32_t)RB);
+      bulk_g2s(dst, src, (uint32_t)RB, recbar + slot_of(j));
+    }
     arm(rec_pend, rec_parb, j);
   };
   auto fetch_rows = [&](int64_t j, int base, int M, bool staged) {
+    if (lane == 0) mbar_arrive_expect_tx(rowbar + slot_of(j), staged ? (uint32_t)(M * P.row_bytes) : 0u);
+    __syncwarp();
     if (staged) {
       const int32_t* cid = (const int32_t*)(rec_at(j) + 16);
-      const int total = M * cpr;
-      for (int c = lane; c < total; c += 32) {
-        const int r = (int)(((unsigned long long)c * P.cpr_inv) >> 32);
-        const int o = c - r * cpr;
+      for (int r = lane; r < M; r += 32) {
         int32_t id = cid[r];
         if (id < 0 || id >= a.N) id = 0;
         const unsigned char* src = TC ? (const unsigned char*)(P.Xe + (size_t)id * P.dx)
                                       : (const unsigned char*)a.rows.row(id);
         int slot = base + r;
         if (slot >= R) slot -= R;
-        cp16(ring + (size_t)slot * stride + o * 16, src + o * 16);
+        bulk_g2s(ring + (size_t)slot * stride, src, (uint32_t)P.row_bytes, rowbar + slot_of(j));
       }
     }
-    cp_arrive(rowbar + slot_of(j));
     arm(row_pend, row_parb, j);
   };
 
@@ -541,10 +529,10 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) k_join_ring(JoinArgs a, Pip
   }
   sink.finish(a.bucket, a.bcap, a.live_keys, a.K);
   unsigned long long nprop = sink.nprop, ndirect = sink.ndirect;
-  cp_wait_all();
   if (failed) {
     if (lane == 0) atomicOr(&a.ctr->err, (unsigned long long)DERR_WAIT_TIMEOUT);
-    // the copies have landed; let their arrivals land too (bounded as well)
+    // let the copies of every armed phase land before the warp leaves
+    // (bounded as well)
 #pragma unroll
     for (int x = 0; x < NREC; ++x) {
       if ((rec_pend >> x) & 1u) warp_wait(recbar + x, (rec_parb >> x) & 1u, WAIT_LIMIT);
@@ -761,8 +749,6 @@ cudaError_t plan_pipe(int precision, int metric, int cap_new, int cap_old, int d
     P->row_stride = d * 4 + 16;
   }
   P->ring_rows = ring;
-  const int cpr = P->row_bytes / 16;
-  P->cpr_inv = (0x100000000ull + cpr - 1) / cpr;
   // pairs (i, j) with i < nn <= cap_new, i < j < M <= cap_new + cap_old
   P->pair_cap = cap_new * (cap_new + cap_old) - cap_new * (cap_new + 1) / 2;
   size_t wb = (size_t)ring * P->row_stride + (size_t)NREC * RB + 2 * NREC * 8 +
