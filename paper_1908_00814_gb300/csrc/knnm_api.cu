@@ -505,11 +505,13 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     KNNM_CUDA(cudaMemsetAsync(P.ctr, 0, sizeof(DevCounters), rs));
     KNNM_CUDA(cudaMemsetAsync(&P.ctr->err_row, 0xFF, 8, rs));
     sa.t = t;
+    const bool alt = adaptive && !use_tc;  // a tensor-core precision taking the FP32 join
+    const JoinPath& j = alt ? jp32 : jp;
+    // the ring join reads its candidates from the records alone
+    sa.records_only = (P.rec && j.pipe) ? 1 : 0;
     if (timed) KNNM_CUDA(cudaEventRecord(ctx->rev[0], rs));
     KNNM_CUDA(launch_sample(sa, rs));
     if (timed) KNNM_CUDA(cudaEventRecord(ctx->rev[1], rs));
-    const bool alt = adaptive && !use_tc;  // a tensor-core precision taking the FP32 join
-    const JoinPath& j = alt ? jp32 : jp;
     const int jprec = alt ? KNNM_FP32 : precision;
     if (j.pipe)
       KNNM_CUDA(launch_pipe(jprec, ja, j.pa, j.smem, j.grid, rs));

@@ -508,6 +508,10 @@ struct SampleArgs {
   // new(u) is not empty, the only ones the join pairs from; the others get
   // empty candidate sets.  The step entry point keeps it off (full outputs).
   int active_only = 0;
+  // Only the candidate records are read after the sampler (the join of this
+  // round takes its candidates from them): the reverse samples need not be in
+  // key order and new_ids / old_ids keep the forward sets only.
+  int records_only = 0;
 };
 cudaError_t launch_sample(const SampleArgs& a, cudaStream_t st);
 // Context internals used by the serving loop (knnm_api.cu): grow the

@@ -464,6 +464,26 @@ __device__ __forceinline__ uint64_t warp_smallest(const uint64_t* bucket, uint64
   return best;
 }
 
+// The s smallest keys of bucket [b0, b1) in lanes 0.. (KEY_EMPTY beyond), in
+// no particular order: every key when there are at most s, else the keys of
+// rank below s.  Buckets above 32 keys take warp_smallest.
+__device__ __forceinline__ uint64_t warp_smallest_any(const uint64_t* bucket, uint64_t b0,
+                                                      uint64_t b1, int s, uint64_t* stage) {
+  if (b1 - b0 > 32) return warp_smallest(bucket, b0, b1, s, stage);
+  const int lane = threadIdx.x & 31;
+  const int c = (int)(b1 - b0);
+  const uint64_t x = lane < c ? bucket[b0 + lane] : KEY_EMPTY;
+  if (c <= s) return x;
+  const unsigned live = __ballot_sync(FULL, x != KEY_EMPTY);
+  int rank = 0;
+  for (unsigned m = live; m; m &= m - 1u)
+    rank += (__shfl_sync(FULL, x, __ffs(m) - 1) < x) ? 1 : 0;
+  const unsigned sel = __ballot_sync(FULL, x != KEY_EMPTY && rank < s);
+  const int src = lane < __popc(sel) ? (int)__fns(sel, 0, lane + 1) : lane;
+  const uint64_t y = __shfl_sync(FULL, x, src);
+  return lane < __popc(sel) ? y : KEY_EMPTY;
+}
+
 // new(u) = fwd_new u rev_new;  old(u) = (fwd_old u rev_old) \ new(u).
 __global__ void __launch_bounds__(BLOCK) k_sample_rev(SampleArgs a) {
   __shared__ uint64_t stage[WARPS_PER_BLOCK][32];
@@ -488,7 +508,11 @@ __global__ void __launch_bounds__(BLOCK) k_sample_rev(SampleArgs a) {
     const int32_t fn = lane < nf ? a.new_ids[(size_t)u * a.cap_new + lane] : -1;
     const int32_t fo = lane < of ? a.old_ids[(size_t)u * a.cap_old + lane] : -2;
     uint64_t rk, ok;
-    if (a.rcnt) {
+    if (a.rcnt && a.records_only) {
+      uint64_t* st = stage[threadIdx.x >> 5];
+      rk = warp_smallest_any(a.rbucket, a.roffs[2 * u], a.roffs[2 * u + 1], s, st);
+      ok = warp_smallest_any(a.rbucket, a.roffs[2 * u + 1], a.roffs[2 * u + 2], s, st);
+    } else if (a.rcnt) {
       uint64_t* st = stage[threadIdx.x >> 5];
       rk = warp_smallest(a.rbucket, a.roffs[2 * u], a.roffs[2 * u + 1], s, st);
       ok = warp_smallest(a.rbucket, a.roffs[2 * u + 1], a.roffs[2 * u + 2], s, st);
@@ -517,9 +541,11 @@ __global__ void __launch_bounds__(BLOCK) k_sample_rev(SampleArgs a) {
                    b3 = __ballot_sync(FULL, keep_ro);
     const int nn = nf + __popc(b1), no = __popc(b2) + __popc(b3);
     __syncwarp();
-    if (add_rn) a.new_ids[(size_t)u * a.cap_new + nf + __popc(b1 & lanemask_lt())] = rn;
-    if (keep_fo) a.old_ids[(size_t)u * a.cap_old + __popc(b2 & lanemask_lt())] = fo;
-    if (keep_ro) a.old_ids[(size_t)u * a.cap_old + __popc(b2) + __popc(b3 & lanemask_lt())] = ro;
+    if (!a.records_only) {
+      if (add_rn) a.new_ids[(size_t)u * a.cap_new + nf + __popc(b1 & lanemask_lt())] = rn;
+      if (keep_fo) a.old_ids[(size_t)u * a.cap_old + __popc(b2 & lanemask_lt())] = fo;
+      if (keep_ro) a.old_ids[(size_t)u * a.cap_old + __popc(b2) + __popc(b3 & lanemask_lt())] = ro;
+    }
     if (lane == 0) {
       a.new_cnt[u] = nn;
       a.old_cnt[u] = no;
