@@ -417,6 +417,17 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   ia.flags = P.flags;
   ia.rear = P.rear;
   ia.ctr = P.ctr;
+  if (P.Xe) {
+    // every row exact in its 16-bit copy: init reads the 16-bit rows
+    KNNM_CUDA(cudaMemcpyAsync(ctx->host_ctr, P.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost,
+                              st));
+    KNNM_CUDA(cudaStreamSynchronize(st));
+    if (ctx->host_ctr->inexact == 0) {
+      ia.Xe = P.Xe;
+      ia.dx = jp.pa.dx;
+      ia.half = precision == KNNM_FP16_RERANK ? 1 : 0;
+    }
+  }
   KNNM_CUDA(launch_init(ia, st));
   KNNM_CUDA(cudaMemcpyAsync(ctx->host_ctr, P.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
   KNNM_CUDA(cudaEventRecord(ctx->ev[1], st));

@@ -469,6 +469,12 @@ struct InitArgs {
   uint8_t* flags;      // [N][K]
   uint64_t* rear;      // [N][Kr]
   DevCounters* ctr;
+  // When every row is exact in its 16-bit copy (small non-negative integers),
+  // the distances are taken from the 16-bit extended rows [N][dx] instead of
+  // the FP32 rows: the same values in the same order, half the bytes.
+  const __nv_bfloat16* Xe = nullptr;
+  int dx = 0;
+  int half = 0;  // the 16-bit rows are FP16 (else BF16)
 };
 cudaError_t launch_init(const InitArgs& a, cudaStream_t st);
 

@@ -189,7 +189,70 @@ __device__ __forceinline__ float staged_dist(const Rows& R, int64_t i, int32_t g
   }
 }
 
-template <int METRIC>
+// staged_dist from the 16-bit extended rows (SRC 1: BF16, 2: FP16) of rows
+// that hold their FP32 values exactly: each element converts back to the very
+// FP32 value, and the accumulation is the same in-order canonical one.  128
+// dimensions (256 bytes of a row) are staged per pass; d % 8 == 0.
+template <int SRC>
+__device__ __forceinline__ float e16_to_f32(uint32_t bits) {
+  if (SRC == 1) return __uint_as_float(bits << 16);
+  return __half2float(__ushort_as_half((unsigned short)bits));
+}
+
+template <int METRIC, int SRC>
+__device__ __forceinline__ float staged_dist16(const InitArgs& a, int64_t i, int32_t g, int rows,
+                                               float* bufF) {
+  const int lane = threadIdx.x & 31, d = a.rows.d;
+  constexpr int RS = INIT_STRIDE * 2;  // 16-bit elements between staged rows (272 bytes)
+  uint16_t* buf = reinterpret_cast<uint16_t*>(bufF);
+  const uint16_t* X = reinterpret_cast<const uint16_t*>(a.Xe);
+  const uint4* xi = reinterpret_cast<const uint4*>(X + (size_t)i * a.dx);
+  const uint16_t* yj = buf + lane * RS;
+  float acc = 0.0f;
+  for (int c = 0; c < d; c += 128) {
+    const int q8 = min(128, d - c) >> 3;  // 16-byte chunks per row this pass
+    for (int s0 = 0; s0 < rows; s0 += 2) {
+      const int slot = s0 + (lane >> 4), o = lane & 15;
+      const int32_t gs = __shfl_sync(FULL, g, slot & 31);
+      if (slot < rows && gs >= 0 && o < q8)
+        init_cp16(buf + slot * RS + o * 8, X + (size_t)gs * a.dx + c + o * 8);
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncwarp();
+    if (g >= 0) {
+      for (int t = 0; t < q8; ++t) {
+        const uint4 xv = __ldg(xi + (c >> 3) + t);
+        const uint4 yv = *reinterpret_cast<const uint4*>(yj + 8 * t);
+        const uint32_t xw[4] = {xv.x, xv.y, xv.z, xv.w}, yw[4] = {yv.x, yv.y, yv.z, yv.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          acc = Canon<METRIC>::step(acc, e16_to_f32<SRC>(xw[q] & 0xFFFFu),
+                                    e16_to_f32<SRC>(yw[q] & 0xFFFFu));
+          acc = Canon<METRIC>::step(acc, e16_to_f32<SRC>(xw[q] >> 16),
+                                    e16_to_f32<SRC>(yw[q] >> 16));
+        }
+      }
+    }
+    __syncwarp();
+  }
+  float na = 0.f, nb = 0.f;
+  if (METRIC == COS) {
+    na = a.norms[i];
+    nb = g >= 0 ? a.norms[g] : 0.f;
+  }
+  return canon_finish<METRIC>(acc, na, nb);
+}
+
+template <int METRIC, int SRC>
+__device__ __forceinline__ float staged_dist_src(const InitArgs& a, int64_t i, int32_t g, int rows,
+                                                 float* buf) {
+  if constexpr (SRC == 0 || METRIC == JACCARD || METRIC == L1 || METRIC == CHI2)
+    return staged_dist<METRIC>(a.rows, i, g, rows, a.norms, buf);
+  else
+    return staged_dist16<METRIC, SRC>(a, i, g, rows, buf);
+}
+
+template <int METRIC, int SRC>
 __global__ void __launch_bounds__(BLOCK) k_init(InitArgs a) {
   extern __shared__ __align__(16) float init_buf[];  // [warps][32][INIT_STRIDE] when staged
   float* wbuf = init_buf + (threadIdx.x >> 5) * 32 * INIT_STRIDE;
@@ -237,7 +300,7 @@ __global__ void __launch_bounds__(BLOCK) k_init(InitArgs a) {
         int32_t g = -1;
         if (lane < K) g = !bad ? (int32_t)(own_base + loc) : -1;
         else if (lane < K + want) g = dsh;
-        const float dist = staged_dist<METRIC>(a.rows, i, g, K + want, a.norms, wbuf);
+        const float dist = staged_dist_src<METRIC, SRC>(a, i, g, K + want, wbuf);
         const uint64_t kk = g >= 0 ? make_key(dist, g) : KEY_EMPTY;
         key = lane < K ? kk : KEY_EMPTY;
         const uint64_t dk = __shfl_sync(FULL, kk, (lane + K) & 31);
@@ -245,7 +308,7 @@ __global__ void __launch_bounds__(BLOCK) k_init(InitArgs a) {
         have_dkey = true;
       } else if (a.vec4) {
         const int32_t g = (lane < K && !bad) ? (int32_t)(own_base + loc) : -1;
-        const float dist = staged_dist<METRIC>(a.rows, i, g, K, a.norms, wbuf);
+        const float dist = staged_dist_src<METRIC, SRC>(a, i, g, K, wbuf);
         if (g >= 0) key = make_key(dist, g);
       } else if (lane < K && !bad) {
         int64_t g = own_base + loc;
@@ -266,7 +329,7 @@ __global__ void __launch_bounds__(BLOCK) k_init(InitArgs a) {
       const int32_t drawn = draw_random(a.seed, i, base, n_src, want, K);
       if (a.vec4) {
         const int32_t g = lane < want ? drawn : -1;
-        const float dist = staged_dist<METRIC>(a.rows, i, g, want, a.norms, wbuf);
+        const float dist = staged_dist_src<METRIC, SRC>(a, i, g, want, wbuf);
         if (g >= 0) dkey = make_key(dist, g);
       } else if (lane < want) {
         dkey = make_key(dist_rows<METRIC>(a.rows, i, drawn, a.norms, a.vec4), drawn);
@@ -1122,27 +1185,35 @@ __global__ void k_bf16_prep(Rows R, int64_t N, __nv_bfloat16* Xb, float4* aux, f
 // Launchers
 // ---------------------------------------------------------------------------
 
-template <int METRIC>
+template <int METRIC, int SRC>
 cudaError_t launch_init_m(const InitArgs& a, int grid, cudaStream_t st) {
   const size_t smem = a.vec4 ? (size_t)WARPS_PER_BLOCK * 32 * INIT_STRIDE * 4 : 0;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_init<METRIC>,
+    cudaError_t e = cudaFuncSetAttribute(k_init<METRIC, SRC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_init<METRIC><<<grid, BLOCK, smem, st>>>(a);
+  k_init<METRIC, SRC><<<grid, BLOCK, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+template <int METRIC>
+cudaError_t launch_init_src(const InitArgs& a, int grid, cudaStream_t st) {
+  // 16-bit rows only for aligned rows (vec4) of a tensor-core metric, d % 8 == 0
+  if (a.Xe && a.vec4 && a.rows.d % 8 == 0)
+    return a.half ? launch_init_m<METRIC, 2>(a, grid, st) : launch_init_m<METRIC, 1>(a, grid, st);
+  return launch_init_m<METRIC, 0>(a, grid, st);
 }
 
 cudaError_t launch_init(const InitArgs& a, cudaStream_t st) {
   int grid = grid_for_warps(a.N);
   switch (a.metric) {
-    case L2: return launch_init_m<L2>(a, grid, st);
-    case IP: return launch_init_m<IP>(a, grid, st);
-    case COS: return launch_init_m<COS>(a, grid, st);
-    case L1: return launch_init_m<L1>(a, grid, st);
-    case JACCARD: return launch_init_m<JACCARD>(a, grid, st);
-    default: return launch_init_m<CHI2>(a, grid, st);
+    case L2: return launch_init_src<L2>(a, grid, st);
+    case IP: return launch_init_src<IP>(a, grid, st);
+    case COS: return launch_init_src<COS>(a, grid, st);
+    case L1: return launch_init_m<L1, 0>(a, grid, st);
+    case JACCARD: return launch_init_m<JACCARD, 0>(a, grid, st);
+    default: return launch_init_m<CHI2, 0>(a, grid, st);
   }
 }
 
