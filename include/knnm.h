@@ -406,7 +406,10 @@ typedef struct {
  * canonically and sorted.  params->k, metric, precision, max_iters,
  * sample_rate, keep_ratio, delta and seed apply to every batch.  The server
  * allocates the resident arrays for cfg->capacity_rows rows up front and
- * starts cfg->slots worker threads.  n >= K+1. */
+ * starts cfg->slots worker threads.  n >= K+1.  It takes a device, not a
+ * context: each worker slot owns a context of its own (stream, scratch), so
+ * that batches run concurrently, and a caller's context could not be shared
+ * by the slots (calls on one context must not overlap). */
 int knnm_server_create(int device, const float* S, int64_t n, const int32_t* G, int d,
                        const knnm_params* params, const knnm_server_config* cfg,
                        knnm_server** out);
