@@ -147,12 +147,17 @@ int knnm_set_stream(knnm_ctx* ctx, void* cuda_stream);
  *   KNNM_OPT_FAIL_ALLOC (default 0, >= 0): the next `value` scratch
  *     reservations of the context fail with KNNM_ERR_NOMEM as if the device
  *     were out of memory (host-side fault injection for tests); the context
- *     and its existing scratch stay usable. */
+ *     and its existing scratch stay usable.
+ *   KNNM_OPT_TC_JOIN (default 0, 0..2): with a tensor-core precision, which
+ *     join each round runs: 0 chooses per round (the tensor-core join while
+ *     its re-rank share stays low, else the FP32 join), 1 always the
+ *     tensor-core join, 2 always the FP32 join.  Results do not depend on it. */
 enum {
   KNNM_OPT_GRAPHS = 1,
   KNNM_OPT_BUCKET_CAP = 2,
   KNNM_OPT_WAIT_POLLS = 3,
-  KNNM_OPT_FAIL_ALLOC = 4
+  KNNM_OPT_FAIL_ALLOC = 4,
+  KNNM_OPT_TC_JOIN = 5
 };
 int knnm_set_option(knnm_ctx* ctx, int option, int value);
 /* Message of the context's last failure ("" if none).  Owned by the context. */

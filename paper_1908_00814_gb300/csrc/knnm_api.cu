@@ -25,6 +25,7 @@ struct knnm_ctx {
   int bucket_cap = 0;         // proposal slots per target and round (0: from K)
   uint32_t wait_polls = WAIT_LIMIT;  // polls before a device wait of the join gives up
   int fail_alloc = 0;         // scratch reservations still to fail (host-side injection)
+  int tc_choice = 0;          // tensor-core precisions: 0 per-round choice, 1 always TC, 2 never
   cudaStream_t cap_stream = nullptr;  // private stream the round graph is captured on
   char err[512] = {0};
 };
@@ -267,6 +268,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   const bool adaptive = tc && choose_join(ctx, KNNM_FP32, params->metric, D.cap_new, D.cap_old,
                                           d, rows_aligned, &jp32) == KNNM_OK;
   if (tc && !adaptive) ctx->err[0] = 0;
+
   const int bcap = proposal_slots(ctx, K);
   // Carve the scratch (two passes: size, then pointers).
   struct Ptrs {
@@ -542,6 +544,8 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   // join predicts the re-rank share from its proposal share.
   const bool all_exact = tc && ctx->host_ctr->inexact == 0;
   bool use_tc = tc && (!adaptive || all_exact);
+  if (adaptive && ctx->tc_choice == 1) use_tc = true;
+  if (adaptive && ctx->tc_choice == 2) use_tc = false;
   // In graph mode each join gets its own captured round, made when first used.
   cudaGraphExec_t round_exec[2] = {nullptr, nullptr};
   auto drop_graphs = [&]() {
@@ -625,7 +629,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     cudaGetLastError();  // a timing query that failed leaves no error behind
     local.rounds = t;
     if ((double)h.updates <= stop_at) break;
-    if (adaptive && !all_exact) {
+    if (adaptive && !all_exact && ctx->tc_choice == 0) {
       const double ev = h.dist_evals > 0 ? (double)h.dist_evals : 1.0;
       use_tc = use_tc ? (double)h.reranked / ev < 0.10
                       : (double)h.proposals / (2.0 * ev) < 0.03;
@@ -736,6 +740,10 @@ extern "C" int knnm_set_option(knnm_ctx* c, int option, int value) {
   }
   if (option == KNNM_OPT_FAIL_ALLOC && value >= 0) {
     c->fail_alloc = value;
+    return KNNM_OK;
+  }
+  if (option == KNNM_OPT_TC_JOIN && value >= 0 && value <= 2) {
+    c->tc_choice = value;
     return KNNM_OK;
   }
   return KNNM_ERR_INVALID;

@@ -19,7 +19,7 @@ _LIB_PATH = Path(__file__).resolve().parent / "libknnm.so"
 L2, IP, COS, L1, CHI2, JACCARD = 0, 1, 2, 3, 4, 5
 FP32, BF16_RERANK, FP16_RERANK = 0, 1, 2
 SYMMETRIC, JOINT = 0, 1
-OPT_GRAPHS, OPT_BUCKET_CAP, OPT_WAIT_POLLS, OPT_FAIL_ALLOC = 1, 2, 3, 4
+OPT_GRAPHS, OPT_BUCKET_CAP, OPT_WAIT_POLLS, OPT_FAIL_ALLOC, OPT_TC_JOIN = 1, 2, 3, 4, 5
 MAX_ROUNDS = 64
 METRICS = {"l2": L2, "ip": IP, "cos": COS, "l1": L1, "chi2": CHI2, "jaccard": JACCARD}
 

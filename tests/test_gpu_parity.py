@@ -487,3 +487,41 @@ def test_hmerge_parity(torch, km, ctx, orc, precision):
         assert_same(layers[m], layers_r[m], f"layer {m}")
     assert_same(ids, ids_r, "bottom ids")
     assert_same(dists, dists_r, "bottom dists")
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+@pytest.mark.parametrize("metric,d", [(0, 32), (1, 48), (2, 40), (0, 96)])
+def test_tensor_core_join_on_float_rows_every_round(torch, km, orc, precision, metric, d):
+    """Float rows (not small integers): the tensor-core join (estimates on the
+    tensor cores, canonical FP32 re-ranks wherever the bound cannot rule a pair
+    out) forced on every round, and the FP32 join forced on every round: S-Merge
+    and J-Merge equal the oracle bit for bit either way, and the estimates rule
+    some pairs out without a re-rank."""
+    X = datagen.gaussian_mixture(2200, d, n_comp=8, seed=70 + d + metric,
+                                 normalize=(metric == 2))
+    n1, K, rounds = 1100, 10, 6
+    G1, _ = orc.bruteforce_knn(X[:n1], K, metric=metric)
+    G2, _ = orc.bruteforce_knn(X[n1:], K, metric=metric)
+    ref_i, ref_d, ref_st = orc.merge_symmetric(X[:n1], G1, X[n1:], G2, K, metric=metric,
+                                               max_iters=rounds, seed=3)
+    jref_i, jref_d, jref_st = orc.merge_joint(X[:n1], G1, X[n1:], K, metric=metric,
+                                              max_iters=rounds, seed=4)
+    for choice in (1, 2):
+        ctx = km.Context(0)
+        ctx.set_option(km.OPT_TC_JOIN, choice)
+        p = km.params(k=K, metric=METRIC_NAMES[metric], precision=precision, max_iters=rounds,
+                      delta=0.0, seed=3)
+        gi, gd, st = ctx.merge_symmetric(cuda(torch, X[:n1]), cuda(torch, G1),
+                                         cuda(torch, X[n1:]), cuda(torch, G2), p)
+        assert all(st["tc_rounds"]) if choice == 1 else not any(st["tc_rounds"])
+        if choice == 1:
+            assert 0 < sum(st["reranked"]) < sum(st["dist_evals"])
+        assert st["updates"] == ref_st["updates"] and st["dist_evals"] == ref_st["dist_evals"]
+        assert_same(host(gi), ref_i, f"ids {precision} choice {choice}")
+        assert_same(host(gd), ref_d, f"dists {precision} choice {choice}")
+        p.seed = 4
+        gi, gd, st = ctx.merge_joint(cuda(torch, X[:n1]), cuda(torch, G1), cuda(torch, X[n1:]), p)
+        assert st["updates"] == jref_st["updates"]
+        assert_same(host(gi), jref_i, f"jmerge ids {precision} choice {choice}")
+        assert_same(host(gd), jref_d, f"jmerge dists {precision} choice {choice}")
+        ctx.close()
