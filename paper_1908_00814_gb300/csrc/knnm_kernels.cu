@@ -381,7 +381,26 @@ __global__ void k_norms(Rows R, int64_t N, float* norms) {
 // ---------------------------------------------------------------------------
 
 // Forward sets of each node u and the pushes into the reverse slot arrays.
+// Rank of every lane's key among the first n (even) of the warp's 32 keys
+// (KEY_EMPTY never counts), read two keys at a time from a broadcast copy in
+// `stage` (32 keys of the warp's shared memory).  Keys other than KEY_EMPTY are
+// distinct.  All 32 lanes must call it together.
+__device__ __forceinline__ int warp_rank(uint64_t x, int n, uint64_t* stage) {
+  const int lane = threadIdx.x & 31;
+  stage[lane] = x;
+  __syncwarp();
+  int rank = 0;
+  const ulonglong2* st2 = (const ulonglong2*)stage;
+  for (int m = 0; m < n; m += 2) {
+    const ulonglong2 y = st2[m >> 1];
+    rank += (y.x < x ? 1 : 0) + (y.y < x ? 1 : 0);
+  }
+  __syncwarp();
+  return rank;
+}
+
 __global__ void __launch_bounds__(BLOCK) k_sample_fwd(SampleArgs a) {
+  __shared__ __align__(16) uint64_t stage[WARPS_PER_BLOCK][32];
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
   const int K = a.K, s = a.s;
@@ -395,12 +414,15 @@ __global__ void __launch_bounds__(BLOCK) k_sample_fwd(SampleArgs a) {
     const int32_t v = key_id(key);
     const bool isnew = lane < K && f == FLAG_NEW;
     const bool isold = lane < K && f != FLAG_NEW;
-    const uint64_t pre = hash_prefix(a.seed, t, STREAM_FWD_NEW, (uint64_t)u);
-    const uint64_t sk = isnew ? sampling_key(pre, v) : KEY_EMPTY;
-    int rank = 0;
-    for (unsigned nb = __ballot_sync(FULL, isnew); nb; nb &= nb - 1u)
-      rank += (__shfl_sync(FULL, sk, __ffs(nb) - 1) < sk) ? 1 : 0;
-    const bool sel = isnew && rank < s;
+    // at most s new entries: every one is drawn, whatever the keys
+    bool sel = isnew;
+    if (__popc(__ballot_sync(FULL, isnew)) > s) {
+      const uint64_t pre = hash_prefix(a.seed, t, STREAM_FWD_NEW, (uint64_t)u);
+      const uint64_t sk = isnew ? sampling_key(pre, v) : KEY_EMPTY;
+      // every lane takes part: warp_rank writes the stage and syncs the warp
+      const int rank = warp_rank(sk, (K + 1) & ~1, stage[threadIdx.x >> 5]);
+      sel = isnew && rank < s;
+    }
     if (sel) a.flags[(size_t)u * K + lane] = FLAG_OLD;
     const unsigned bs = __ballot_sync(FULL, sel), bo = __ballot_sync(FULL, isold);
     if (sel) a.new_ids[(size_t)u * a.cap_new + __popc(bs & lanemask_lt())] = v;
@@ -455,28 +477,57 @@ __global__ void __launch_bounds__(BLOCK) k_sample_count_old(SampleArgs a) {
 
 // Moves each reverse edge's sampling key into its (target, stream) bucket;
 // the counts are consumed back to zero.
+// Two nodes per warp and pass: each step's loads (counts, ids, bucket starts)
+// and slot claims of both are in flight together, since every step waits
+// on the one before.
+constexpr int SCATTER_NODES = 2;
+
 __global__ void __launch_bounds__(BLOCK) k_sample_scatter(SampleArgs a) {
+  constexpr int U = SCATTER_NODES;
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
   const uint64_t t = (uint64_t)(a.t_dev ? *a.t_dev : a.t);
-  for (int64_t u = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5); u < a.N;
-       u += nwarps) {
-    const int nf = a.new_cnt[u], of = a.old_cnt[u];
-    const bool hn = lane < nf;
-    const int32_t vn = hn ? a.new_ids[(size_t)u * a.cap_new + lane] : 0;
-    const int32_t vo = lane < of ? a.old_ids[(size_t)u * a.cap_old + lane] : 0;
-    const bool ho = lane < of && (!a.active_only || active_by_bucket(a, vo));
-    // bucket starts, keys and both slot claims in flight before either store
-    const unsigned long long bn = hn ? a.roffs[2 * (size_t)vn] : 0ull;
-    const unsigned long long bo = ho ? a.roffs[2 * (size_t)vo + 1] : 0ull;
-    const int pn = hn ? atomicSub(&a.rcnt[2 * (size_t)vn], 1) - 1 : 0;
-    const int po = ho ? atomicSub(&a.rcnt[2 * (size_t)vo + 1], 1) - 1 : 0;
-    if (hn)
-      a.rbucket[bn + (uint64_t)pn] =
-          sampling_key(hash_prefix(a.seed, t, STREAM_REV_NEW, (uint64_t)vn), (int32_t)u);
-    if (ho)
-      a.rbucket[bo + (uint64_t)po] =
-          sampling_key(hash_prefix(a.seed, t, STREAM_REV_OLD, (uint64_t)vo), (int32_t)u);
+  for (int64_t u0 = ((int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5)) * U; u0 < a.N;
+       u0 += nwarps * U) {
+    int nf[U], of[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const bool in = u0 + j < a.N;
+      nf[j] = in ? a.new_cnt[u0 + j] : 0;
+      of[j] = in ? a.old_cnt[u0 + j] : 0;
+    }
+    int32_t vn[U], vo[U];
+    bool hn[U], ho[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      hn[j] = lane < nf[j];
+      vn[j] = hn[j] ? a.new_ids[(size_t)(u0 + j) * a.cap_new + lane] : 0;
+      vo[j] = lane < of[j] ? a.old_ids[(size_t)(u0 + j) * a.cap_old + lane] : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < U; ++j)
+      ho[j] = lane < of[j] && (!a.active_only || active_by_bucket(a, vo[j]));
+    unsigned long long bn[U], bo[U];
+    int pn[U], po[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      bn[j] = hn[j] ? a.roffs[2 * (size_t)vn[j]] : 0ull;
+      bo[j] = ho[j] ? a.roffs[2 * (size_t)vo[j] + 1] : 0ull;
+    }
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      pn[j] = hn[j] ? atomicSub(&a.rcnt[2 * (size_t)vn[j]], 1) - 1 : 0;
+      po[j] = ho[j] ? atomicSub(&a.rcnt[2 * (size_t)vo[j] + 1], 1) - 1 : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      if (hn[j])
+        a.rbucket[bn[j] + (uint64_t)pn[j]] = sampling_key(
+            hash_prefix(a.seed, t, STREAM_REV_NEW, (uint64_t)vn[j]), (int32_t)(u0 + j));
+      if (ho[j])
+        a.rbucket[bo[j] + (uint64_t)po[j]] = sampling_key(
+            hash_prefix(a.seed, t, STREAM_REV_OLD, (uint64_t)vo[j]), (int32_t)(u0 + j));
+    }
   }
 }
 
@@ -490,10 +541,7 @@ __device__ __forceinline__ uint64_t warp_smallest(const uint64_t* bucket, uint64
   if (b1 - b0 <= 32) {
     // one chunk: each key's rank among the chunk is its place
     const uint64_t x = b0 + lane < b1 ? bucket[b0 + lane] : KEY_EMPTY;
-    const unsigned live = __ballot_sync(FULL, x != KEY_EMPTY);
-    int rank = 0;
-    for (unsigned m = live; m; m &= m - 1u)
-      rank += (__shfl_sync(FULL, x, __ffs(m) - 1) < x) ? 1 : 0;
+    const int rank = warp_rank(x, (int)((b1 - b0 + 1) & ~1ull), stage);
     stage[lane] = KEY_EMPTY;
     __syncwarp();
     if (x != KEY_EMPTY && rank < s) stage[rank] = x;
@@ -537,10 +585,7 @@ __device__ __forceinline__ uint64_t warp_smallest_any(const uint64_t* bucket, ui
   const int c = (int)(b1 - b0);
   const uint64_t x = lane < c ? bucket[b0 + lane] : KEY_EMPTY;
   if (c <= s) return x;
-  const unsigned live = __ballot_sync(FULL, x != KEY_EMPTY);
-  int rank = 0;
-  for (unsigned m = live; m; m &= m - 1u)
-    rank += (__shfl_sync(FULL, x, __ffs(m) - 1) < x) ? 1 : 0;
+  const int rank = warp_rank(x, (c + 1) & ~1, stage);
   const unsigned sel = __ballot_sync(FULL, x != KEY_EMPTY && rank < s);
   const int src = lane < __popc(sel) ? (int)__fns(sel, 0, lane + 1) : lane;
   const uint64_t y = __shfl_sync(FULL, x, src);
@@ -549,7 +594,8 @@ __device__ __forceinline__ uint64_t warp_smallest_any(const uint64_t* bucket, ui
 
 // new(u) = fwd_new u rev_new;  old(u) = (fwd_old u rev_old) \ new(u).
 __global__ void __launch_bounds__(BLOCK) k_sample_rev(SampleArgs a) {
-  __shared__ uint64_t stage[WARPS_PER_BLOCK][32];
+  __shared__ __align__(16) uint64_t stage[WARPS_PER_BLOCK][32];
+  __shared__ __align__(16) int32_t sets[WARPS_PER_BLOCK][3][32];
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
   const int s = a.s;
@@ -585,18 +631,29 @@ __global__ void __launch_bounds__(BLOCK) k_sample_rev(SampleArgs a) {
     }
     const int32_t rn = rk != KEY_EMPTY ? key_id(rk) : -3;
     const int32_t ro = ok != KEY_EMPTY ? key_id(ok) : -4;
+    // membership tests against broadcast copies of the three sets, four ids
+    // a load; the markers of absent entries (-1, -2, -3, -4) never match
+    int32_t(*sw)[32] = sets[threadIdx.x >> 5];
+    sw[0][lane] = fn;
+    sw[1][lane] = rn;
+    sw[2][lane] = fo;
+    __syncwarp();
+    const int nr = 32 - __clz((int)__ballot_sync(FULL, rn >= 0));
     bool rn_dup = false, fo_in_rn = false, ro_drop = false;
-    for (int m = 0; m < nf; ++m) {
-      int32_t x = __shfl_sync(FULL, fn, m);
-      rn_dup |= (rn == x);
-      ro_drop |= (ro == x);
+    for (int m = 0; m < nf; m += 4) {
+      const int4 x = *(const int4*)&sw[0][m];
+      rn_dup |= (rn == x.x) | (rn == x.y) | (rn == x.z) | (rn == x.w);
+      ro_drop |= (ro == x.x) | (ro == x.y) | (ro == x.z) | (ro == x.w);
     }
-    for (int m = 0; m < s; ++m) {
-      int32_t x = __shfl_sync(FULL, rn, m);
-      fo_in_rn |= (fo == x);
-      ro_drop |= (ro == x);
+    for (int m = 0; m < nr; m += 4) {
+      const int4 x = *(const int4*)&sw[1][m];
+      fo_in_rn |= (fo == x.x) | (fo == x.y) | (fo == x.z) | (fo == x.w);
+      ro_drop |= (ro == x.x) | (ro == x.y) | (ro == x.z) | (ro == x.w);
     }
-    for (int m = 0; m < of; ++m) ro_drop |= (ro == __shfl_sync(FULL, fo, m));
+    for (int m = 0; m < of; m += 4) {
+      const int4 x = *(const int4*)&sw[2][m];
+      ro_drop |= (ro == x.x) | (ro == x.y) | (ro == x.z) | (ro == x.w);
+    }
     const bool add_rn = rn >= 0 && !rn_dup;
     const bool keep_fo = fo >= 0 && !fo_in_rn;
     const bool keep_ro = ro >= 0 && !ro_drop;
