@@ -531,25 +531,39 @@ __global__ void __launch_bounds__(BLOCK) k_sample_scatter(SampleArgs a) {
   }
 }
 
-// The s smallest keys of bucket [b0, b1), ascending, lane j holding the j-th
-// (KEY_EMPTY beyond).  Keys in a bucket are distinct.  `stage` is 32 keys of
-// the warp's shared memory.
-__device__ __forceinline__ uint64_t warp_smallest(const uint64_t* bucket, uint64_t b0, uint64_t b1,
-                                                  int s, uint64_t* stage) {
+// The s smallest of the c <= 32 keys x (lane j holding the j-th of a
+// bucket, KEY_EMPTY beyond), ascending in lanes 0.. (KEY_EMPTY beyond).  Keys
+// are distinct.  `stage` is 32 keys of the warp's shared memory.
+__device__ __forceinline__ uint64_t select_sorted32(uint64_t x, int c, int s, uint64_t* stage) {
+  const int lane = threadIdx.x & 31;
+  const int rank = warp_rank(x, (c + 1) & ~1, stage);
+  stage[lane] = KEY_EMPTY;
+  __syncwarp();
+  if (x != KEY_EMPTY && rank < s) stage[rank] = x;
+  __syncwarp();
+  const uint64_t best = stage[lane];
+  __syncwarp();
+  return best;
+}
+
+// As select_sorted32, in no particular order: every key when c <= s, else the
+// keys of rank below s, packed into lanes 0..
+__device__ __forceinline__ uint64_t select_any32(uint64_t x, int c, int s, uint64_t* stage) {
+  if (c <= s) return x;
+  const int lane = threadIdx.x & 31;
+  const int rank = warp_rank(x, (c + 1) & ~1, stage);
+  const unsigned sel = __ballot_sync(FULL, x != KEY_EMPTY && rank < s);
+  const int src = lane < __popc(sel) ? (int)__fns(sel, 0, lane + 1) : lane;
+  const uint64_t y = __shfl_sync(FULL, x, src);
+  return lane < __popc(sel) ? y : KEY_EMPTY;
+}
+
+// The s smallest keys of bucket [b0, b1) with b1 - b0 > 32, ascending, lane j
+// holding the j-th (KEY_EMPTY beyond).  Keys in a bucket are distinct.
+__device__ __forceinline__ uint64_t warp_smallest_long(const uint64_t* bucket, uint64_t b0,
+                                                       uint64_t b1, int s) {
   const int lane = threadIdx.x & 31;
   uint64_t best = KEY_EMPTY;
-  if (b1 - b0 <= 32) {
-    // one chunk: each key's rank among the chunk is its place
-    const uint64_t x = b0 + lane < b1 ? bucket[b0 + lane] : KEY_EMPTY;
-    const int rank = warp_rank(x, (int)((b1 - b0 + 1) & ~1ull), stage);
-    stage[lane] = KEY_EMPTY;
-    __syncwarp();
-    if (x != KEY_EMPTY && rank < s) stage[rank] = x;
-    __syncwarp();
-    best = stage[lane];
-    __syncwarp();
-    return best;
-  }
   for (uint64_t c = b0; c < b1; c += 32) {
     uint64_t x = c + lane < b1 ? bucket[c + lane] : KEY_EMPTY;
     const uint64_t kth = __shfl_sync(FULL, best, s - 1);
@@ -575,34 +589,45 @@ __device__ __forceinline__ uint64_t warp_smallest(const uint64_t* bucket, uint64
   return best;
 }
 
-// The s smallest keys of bucket [b0, b1) in lanes 0.. (KEY_EMPTY beyond), in
-// no particular order: every key when there are at most s, else the keys of
-// rank below s.  Buckets above 32 keys take warp_smallest.
-__device__ __forceinline__ uint64_t warp_smallest_any(const uint64_t* bucket, uint64_t b0,
-                                                      uint64_t b1, int s, uint64_t* stage) {
-  if (b1 - b0 > 32) return warp_smallest(bucket, b0, b1, s, stage);
-  const int lane = threadIdx.x & 31;
-  const int c = (int)(b1 - b0);
-  const uint64_t x = lane < c ? bucket[b0 + lane] : KEY_EMPTY;
-  if (c <= s) return x;
-  const int rank = warp_rank(x, (c + 1) & ~1, stage);
-  const unsigned sel = __ballot_sync(FULL, x != KEY_EMPTY && rank < s);
-  const int src = lane < __popc(sel) ? (int)__fns(sel, 0, lane + 1) : lane;
-  const uint64_t y = __shfl_sync(FULL, x, src);
-  return lane < __popc(sel) ? y : KEY_EMPTY;
-}
-
 // new(u) = fwd_new u rev_new;  old(u) = (fwd_old u rev_old) \ new(u).
+// Each node's loads come in two waves, all of a wave in flight together: its
+// ids and bucket keys, then (once the sets are known) the records' gathers.
+// The counts and bucket bounds they need are loaded one node ahead.
 __global__ void __launch_bounds__(BLOCK) k_sample_rev(SampleArgs a) {
   __shared__ __align__(16) uint64_t stage[WARPS_PER_BLOCK][32];
   __shared__ __align__(16) int32_t sets[WARPS_PER_BLOCK][3][32];
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
   const int s = a.s;
-  for (int64_t u = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5); u < a.N;
-       u += nwarps) {
-    const int nf = a.new_cnt[u], of = a.old_cnt[u];
-    if (a.active_only && nf == 0 && a.roffs[2 * u] == a.roffs[2 * u + 1]) {
+  const bool buckets = a.rcnt != nullptr;
+  uint64_t* st = stage[threadIdx.x >> 5];
+  int32_t(*sw)[32] = sets[threadIdx.x >> 5];
+  int64_t u = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
+  int nf_next = 0, of_next = 0;
+  unsigned long long q0 = 0, q1 = 0, q2 = 0;
+  if (u < a.N) {
+    nf_next = a.new_cnt[u];
+    of_next = a.old_cnt[u];
+    if (buckets) {
+      q0 = a.roffs[2 * u];
+      q1 = a.roffs[2 * u + 1];
+      q2 = a.roffs[2 * u + 2];
+    }
+  }
+  for (; u < a.N; u += nwarps) {
+    const int nf = nf_next, of = of_next;
+    const unsigned long long r0 = q0, r1 = q1, r2 = q2;
+    const int64_t un = u + nwarps;
+    if (un < a.N) {
+      nf_next = a.new_cnt[un];
+      of_next = a.old_cnt[un];
+      if (buckets) {
+        q0 = a.roffs[2 * un];
+        q1 = a.roffs[2 * un + 1];
+        q2 = a.roffs[2 * un + 2];
+      }
+    }
+    if (a.active_only && buckets && nf == 0 && r0 == r1) {
       // new(u) is empty: no pair of the join starts here
       if (lane == 0) {
         a.new_cnt[u] = 0;
@@ -614,26 +639,34 @@ __global__ void __launch_bounds__(BLOCK) k_sample_rev(SampleArgs a) {
       }
       continue;
     }
+    // first wave: forward ids and the first 32 keys of both buckets
     const int32_t fn = lane < nf ? a.new_ids[(size_t)u * a.cap_new + lane] : -1;
     const int32_t fo = lane < of ? a.old_ids[(size_t)u * a.cap_old + lane] : -2;
-    uint64_t rk, ok;
-    if (a.rcnt && a.records_only) {
-      uint64_t* st = stage[threadIdx.x >> 5];
-      rk = warp_smallest_any(a.rbucket, a.roffs[2 * u], a.roffs[2 * u + 1], s, st);
-      ok = warp_smallest_any(a.rbucket, a.roffs[2 * u + 1], a.roffs[2 * u + 2], s, st);
-    } else if (a.rcnt) {
-      uint64_t* st = stage[threadIdx.x >> 5];
-      rk = warp_smallest(a.rbucket, a.roffs[2 * u], a.roffs[2 * u + 1], s, st);
-      ok = warp_smallest(a.rbucket, a.roffs[2 * u + 1], a.roffs[2 * u + 2], s, st);
+    uint64_t xn, xo;
+    if (buckets) {
+      xn = r0 + lane < r1 ? a.rbucket[r0 + lane] : KEY_EMPTY;
+      xo = r1 + lane < r2 ? a.rbucket[r1 + lane] : KEY_EMPTY;
     } else {
-      rk = lane < s ? a.rev_new[(size_t)u * s + lane] : KEY_EMPTY;
-      ok = lane < s ? a.rev_old[(size_t)u * s + lane] : KEY_EMPTY;
+      xn = lane < s ? a.rev_new[(size_t)u * s + lane] : KEY_EMPTY;
+      xo = lane < s ? a.rev_old[(size_t)u * s + lane] : KEY_EMPTY;
+    }
+    uint64_t rk = xn, ok = xo;
+    if (buckets) {
+      const uint64_t cn = r1 - r0, co = r2 - r1;
+      if (a.records_only) {
+        rk = cn > 32 ? warp_smallest_long(a.rbucket, r0, r1, s) : select_any32(xn, (int)cn, s, st);
+        ok = co > 32 ? warp_smallest_long(a.rbucket, r1, r2, s) : select_any32(xo, (int)co, s, st);
+      } else {
+        rk = cn > 32 ? warp_smallest_long(a.rbucket, r0, r1, s)
+                     : select_sorted32(xn, (int)cn, s, st);
+        ok = co > 32 ? warp_smallest_long(a.rbucket, r1, r2, s)
+                     : select_sorted32(xo, (int)co, s, st);
+      }
     }
     const int32_t rn = rk != KEY_EMPTY ? key_id(rk) : -3;
     const int32_t ro = ok != KEY_EMPTY ? key_id(ok) : -4;
     // membership tests against broadcast copies of the three sets, four ids
     // a load; the markers of absent entries (-1, -2, -3, -4) never match
-    int32_t(*sw)[32] = sets[threadIdx.x >> 5];
     sw[0][lane] = fn;
     sw[1][lane] = rn;
     sw[2][lane] = fo;
@@ -654,36 +687,53 @@ __global__ void __launch_bounds__(BLOCK) k_sample_rev(SampleArgs a) {
       const int4 x = *(const int4*)&sw[2][m];
       ro_drop |= (ro == x.x) | (ro == x.y) | (ro == x.z) | (ro == x.w);
     }
+    const bool has_fn = lane < nf;
     const bool add_rn = rn >= 0 && !rn_dup;
     const bool keep_fo = fo >= 0 && !fo_in_rn;
     const bool keep_ro = ro >= 0 && !ro_drop;
     const unsigned b1 = __ballot_sync(FULL, add_rn), b2 = __ballot_sync(FULL, keep_fo),
                    b3 = __ballot_sync(FULL, keep_ro);
     const int nn = nf + __popc(b1), no = __popc(b2) + __popc(b3);
+    const int p_rn = nf + __popc(b1 & lanemask_lt());
+    const int p_fo = __popc(b2 & lanemask_lt());
+    const int p_ro = __popc(b2) + __popc(b3 & lanemask_lt());
     __syncwarp();
     if (!a.records_only) {
-      if (add_rn) a.new_ids[(size_t)u * a.cap_new + nf + __popc(b1 & lanemask_lt())] = rn;
-      if (keep_fo) a.old_ids[(size_t)u * a.cap_old + __popc(b2 & lanemask_lt())] = fo;
-      if (keep_ro) a.old_ids[(size_t)u * a.cap_old + __popc(b2) + __popc(b3 & lanemask_lt())] = ro;
+      if (add_rn) a.new_ids[(size_t)u * a.cap_new + p_rn] = rn;
+      if (keep_fo) a.old_ids[(size_t)u * a.cap_old + p_fo] = fo;
+      if (keep_ro) a.old_ids[(size_t)u * a.cap_old + p_ro] = ro;
     }
     if (lane == 0) {
       a.new_cnt[u] = nn;
       a.old_cnt[u] = no;
     }
     if (a.rec) {
+      // second wave: every k-th key and norm, then the stores
+      auto kth_of = [&](int32_t id) -> uint64_t {
+        return a.kth ? __ldg(&a.kth[id]) : __ldg(&a.keys[(size_t)id * a.K_list + (a.K_list - 1)]);
+      };
+      const uint64_t k_fn = has_fn ? kth_of(fn) : 0, k_rn = add_rn ? kth_of(rn) : 0,
+                     k_fo = keep_fo ? kth_of(fo) : 0, k_ro = keep_ro ? kth_of(ro) : 0;
+      float c_fn = 0.f, c_rn = 0.f, c_fo = 0.f, c_ro = 0.f;
+      if (a.norms) {
+        if (has_fn) c_fn = __ldg(&a.norms[fn]);
+        if (add_rn) c_rn = __ldg(&a.norms[rn]);
+        if (keep_fo) c_fo = __ldg(&a.norms[fo]);
+        if (keep_ro) c_ro = __ldg(&a.norms[ro]);
+      }
       unsigned char* R = a.rec + (size_t)u * rec_bytes(a.rec_cap);
       int32_t* rid = (int32_t*)(R + 16);
       uint64_t* rkth = (uint64_t*)(R + 16 + 4 * a.rec_cap);
       float* rcn = (float*)(R + 16 + 12 * a.rec_cap);
-      auto put = [&](int pos, int32_t id) {
+      auto put = [&](int pos, int32_t id, uint64_t k, float c) {
         rid[pos] = id;
-        rkth[pos] = a.kth ? a.kth[id] : a.keys[(size_t)id * a.K_list + (a.K_list - 1)];
-        if (a.norms) rcn[pos] = a.norms[id];
+        rkth[pos] = k;
+        if (a.norms) rcn[pos] = c;
       };
-      if (lane < nf) put(lane, fn);
-      if (add_rn) put(nf + __popc(b1 & lanemask_lt()), rn);
-      if (keep_fo) put(nn + __popc(b2 & lanemask_lt()), fo);
-      if (keep_ro) put(nn + __popc(b2) + __popc(b3 & lanemask_lt()), ro);
+      if (has_fn) put(lane, fn, k_fn, c_fn);
+      if (add_rn) put(p_rn, rn, k_rn, c_rn);
+      if (keep_fo) put(nn + p_fo, fo, k_fo, c_fo);
+      if (keep_ro) put(nn + p_ro, ro, k_ro, c_ro);
       if (lane == 0) {
         int32_t* h = (int32_t*)R;
         h[0] = nn;
