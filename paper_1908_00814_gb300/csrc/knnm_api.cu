@@ -283,6 +283,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     float4* aux;
     float* rmax;
     __nv_bfloat16* Xe;
+    float* wx;
     unsigned char* rec;
     DevCounters* ctr;
     int32_t* pcnt;
@@ -319,6 +320,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     P.aux = tc && !jp.pipe ? c.take<float4>((size_t)N) : nullptr;
     P.rmax = tc && !jp.pipe ? c.take<float>((size_t)N) : nullptr;
     P.Xe = tc && jp.pipe ? c.take<__nv_bfloat16>((size_t)N * jp.pa.dx) : nullptr;
+    P.wx = tc && jp.pipe ? c.take<float>((size_t)N) : nullptr;
     P.rec = (jp.pipe || (adaptive && jp32.pipe))
                 ? c.take<unsigned char>((size_t)N * rec_bytes(jp.pipe ? jp.pa.cap : jp32.pa.cap))
                 : nullptr;
@@ -397,7 +399,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     ++launches;
   }
   if (P.Xe) {
-    KNNM_CUDA(launch_bf16_ext(rows, N, jp.pa.dx, P.Xe, precision == KNNM_FP16_RERANK,
+    KNNM_CUDA(launch_bf16_ext(rows, N, jp.pa.dx, P.Xe, P.wx, precision == KNNM_FP16_RERANK,
                               &P.ctr->inexact, st));
     ++launches;
   }
@@ -520,8 +522,11 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     sa.t = t;
     const bool alt = adaptive && !use_tc;  // a tensor-core precision taking the FP32 join
     const JoinPath& j = alt ? jp32 : jp;
-    // the ring join reads its candidates from the records alone
+    // the ring join reads its candidates from the records alone; their third
+    // column is the rows' exactness width for the tensor-core ring join and
+    // the cosine norm (or nothing) for the FP32 one
     sa.records_only = (P.rec && j.pipe) ? 1 : 0;
+    sa.norms = (tc && !alt && jp.pipe) ? P.wx : P.norms;
     if (timed) KNNM_CUDA(cudaEventRecord(ctx->rev[0], rs));
     KNNM_CUDA(launch_sample(sa, rs));
     if (timed) KNNM_CUDA(cudaEventRecord(ctx->rev[1], rs));
@@ -1385,6 +1390,7 @@ int step_join_rows(knnm_ctx* ctx, int mode, const float* X1, int64_t nx1, const 
   float4* aux;
   float* rmax;
   __nv_bfloat16* Xe;
+  float* wx;
   unsigned char* rec;
   DevCounters* ctr;
   auto carve = [&](Carver& c) {
@@ -1402,6 +1408,7 @@ int step_join_rows(knnm_ctx* ctx, int mode, const float* X1, int64_t nx1, const 
       mold = c.take<int32_t>((size_t)N);
     }
     Xe = tc && jp.pipe ? c.take<__nv_bfloat16>((size_t)N * jp.pa.dx) : nullptr;
+    wx = tc && jp.pipe ? c.take<float>((size_t)N) : nullptr;
     rec = jp.pipe ? c.take<unsigned char>((size_t)N * rec_bytes(jp.pa.cap)) : nullptr;
   };
   Carver c0;
@@ -1427,7 +1434,7 @@ int step_join_rows(knnm_ctx* ctx, int mode, const float* X1, int64_t nx1, const 
   if (Xb)
     KNNM_CUDA(launch_bf16_prep(rows, N, Xb, aux, rmax, precision == KNNM_FP16_RERANK, nullptr, st));
   if (Xe)
-    KNNM_CUDA(launch_bf16_ext(rows, N, jp.pa.dx, Xe, precision == KNNM_FP16_RERANK, nullptr, st));
+    KNNM_CUDA(launch_bf16_ext(rows, N, jp.pa.dx, Xe, wx, precision == KNNM_FP16_RERANK, nullptr, st));
   JoinArgs ja;
   ja.mode = mode;
   ja.rows = rows;
@@ -1455,7 +1462,9 @@ int step_join_rows(knnm_ctx* ctx, int mode, const float* X1, int64_t nx1, const 
   ja.wait_polls = ctx->wait_polls;
   KNNM_CUDA(cudaMemsetAsync(pcnt, 0, (size_t)N * 4, st));
   if (jp.pipe) {
-    KNNM_CUDA(launch_build_records(N, K, keys, params->metric == KNNM_COS ? norms : nullptr,
+    // third record column: exactness widths (tensor-core join), cosine norms
+    KNNM_CUDA(launch_build_records(N, K, keys,
+                                   tc ? wx : (params->metric == KNNM_COS ? norms : nullptr),
                                    cap_new, cap_old, new_ids, new_cnt, old_ids, old_cnt, rec,
                                    jp.pa.cap, st));
     jp.pa.rec = rec;
@@ -1599,7 +1608,7 @@ extern "C" int knnm_step_tc_estimate(knnm_ctx* ctx, const float* X, int64_t n, i
   c1.base = (char*)ctx->arena;
   carve(c1);
   Rows rows{X, X, n, d};
-  KNNM_CUDA(launch_bf16_ext(rows, n, dx, Xe, precision == KNNM_FP16_RERANK, nullptr, st));
+  KNNM_CUDA(launch_bf16_ext(rows, n, dx, Xe, nullptr, precision == KNNM_FP16_RERANK, nullptr, st));
   KNNM_CUDA(launch_tc_estimate(precision, metric, Xe, dx, rows, pi, pj, P, est, bound, canon, st));
   KNNM_CUDA(cudaStreamSynchronize(st));
   return KNNM_OK;

@@ -592,10 +592,11 @@ struct PipeArgs {
   int cw;                    // warps per block
   int ring_rows;             // rows in each warp's ring
   int warp_bytes;            // shared memory per warp
-  int row_bytes;             // bytes copied per candidate row
+  int row_bytes;             // bytes staged per candidate row
   int row_stride;            // bytes between staged rows
   int stage_bytes;           // record + rows of one stage
   int pair_cap;              // cap_new * (cap_new + cap_old)
+  int gstr;                  // floats per row of the staged Gram block
 };
 // Fills the layout fields of P (not rec / Xe), the dynamic shared memory and
 // the persistent grid; fails when the shapes do not fit the pipeline.
@@ -609,8 +610,9 @@ cudaError_t launch_tc_estimate(int precision, int metric, const __nv_bfloat16* X
                                Rows rows, const int32_t* pi, const int32_t* pj, int64_t P,
                                float* est, float* bound, float* canon, cudaStream_t st);
 // 16-bit rows (BF16, or FP16 when half != 0; stored through __nv_bfloat16
-// pointers as raw 16-bit elements) with their error-data tails.
-cudaError_t launch_bf16_ext(Rows rows, int64_t N, int dx, __nv_bfloat16* Xe, int half,
+// pointers as raw 16-bit elements) with their error-data tails; wx (optional)
+// receives each row's exactness width, the tail's fifth float.
+cudaError_t launch_bf16_ext(Rows rows, int64_t N, int dx, __nv_bfloat16* Xe, float* wx, int half,
                             unsigned long long* inexact, cudaStream_t st);
 
 // Persistent join kernels: `grid` blocks loop over the nodes.

@@ -25,7 +25,6 @@ namespace knnm {
 
 namespace {
 
-constexpr int GSTR = 68;  // floats per row of the staged Gram block
 
 
 __device__ __forceinline__ void ldm_x4(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3,
@@ -251,12 +250,16 @@ __device__ __forceinline__ void node_fp32(const JoinArgs& a, const Rec& rc, int 
 }
 
 // BF16: the Gram block is computed one 16-row tile of new candidates at a time
-// into a 16 x GSTR buffer; pairs come sorted by their first index, so tile mt
-// serves the pairs [split(mt), split(mt + 1)).
+// into a 16 x gstr buffer (gstr >= every candidate count; columns beyond it are
+// not stored); pairs come sorted by their first index, so tile mt serves the
+// pairs [split(mt), split(mt + 1)).  Each record's third column holds the
+// rows' exactness widths (the fifth float of the extended row's tail, which
+// the ring does not stage).
 template <int METRIC, bool HALF, typename RowPtr>
 __device__ __forceinline__ void node_tc(const JoinArgs& a, const Rec& rc, int np,
                                         uint16_t* pairs, int np0, RowPtr row_ptr, float* G,
-                                        Sink& sink, unsigned long long& reranked) {
+                                        const int gstr, Sink& sink,
+                                        unsigned long long& reranked) {
   const int lane = threadIdx.x & 31;
   const int d = a.rows.d;
   const int dpad = (d + 15) & ~15;
@@ -289,12 +292,12 @@ __device__ __forceinline__ void node_tc(const JoinArgs& a, const Rec& rc, int np
       const int r0 = lane >> 2;
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        if (nt + t < ntiles) {
-          const int col = (nt + t) * 8 + 2 * (lane & 3);
-          G[r0 * GSTR + col] = c[t][0];
-          G[r0 * GSTR + col + 1] = c[t][1];
-          G[(r0 + 8) * GSTR + col] = c[t][2];
-          G[(r0 + 8) * GSTR + col + 1] = c[t][3];
+        const int col = (nt + t) * 8 + 2 * (lane & 3);
+        if (nt + t < ntiles && col < gstr) {  // gstr % 4 == 0: col + 1 < gstr too
+          G[r0 * gstr + col] = c[t][0];
+          G[r0 * gstr + col + 1] = c[t][1];
+          G[(r0 + 8) * gstr + col] = c[t][2];
+          G[(r0 + 8) * gstr + col + 1] = c[t][3];
         }
       }
     }
@@ -313,12 +316,10 @@ __device__ __forceinline__ void node_tc(const JoinArgs& a, const Rec& rc, int np
         if (q < q_hi) {
           pr[u] = pairs[q];
           const int i = pr[u] >> 8, jj = pr[u] & 0xFF;
-          const float g = G[(i & 15) * GSTR + jj];
-          const unsigned char* ti = row_ptr(i) + dpad * 2;
-          const unsigned char* tj = row_ptr(jj) + dpad * 2;
-          const float4 ai = *(const float4*)ti;
-          const float4 aj = *(const float4*)tj;
-          const float ri = *(const float*)(ti + 16), rj = *(const float*)(tj + 16);
+          const float g = G[(i & 15) * gstr + jj];
+          const float4 ai = *(const float4*)(row_ptr(i) + dpad * 2);
+          const float4 aj = *(const float4*)(row_ptr(jj) + dpad * 2);
+          const float ri = rc.cn[i], rj = rc.cn[jj];
           tgt[2 * u] = rc.cid[i];
           tgt[2 * u + 1] = rc.cid[jj];
           if (exact_rows(ri, rj)) {
@@ -382,7 +383,6 @@ constexpr int NREC = 3;
 constexpr int AHEAD = 1;
 constexpr int MAX_WARPS = 12;  // warps per block (one block per SM)
 constexpr int MIN_WARPS = 4;
-constexpr int RING_EXTRA = 4;  // ring rows beyond the largest candidate set
 
 template <int METRIC, bool TC, bool HALF>
 __global__ void __launch_bounds__(MAX_WARPS * 32, 1) k_join_ring(JoinArgs a, PipeArgs P) {
@@ -519,7 +519,7 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) k_join_ring(JoinArgs a, Pip
       const int np = list_pairs(a, rc, pairs, &np0);
       if (lane == 0) evals += (unsigned long long)np;
       if (TC) {
-        node_tc<METRIC, HALF>(a, rc, np, pairs, np0, row_ptr, G, sink, reranked);
+        node_tc<METRIC, HALF>(a, rc, np, pairs, np0, row_ptr, G, P.gstr, sink, reranked);
       } else {
         node_fp32<METRIC>(a, rc, np, pairs, row_ptr, sink);
       }
@@ -574,7 +574,7 @@ constexpr int EXT_WARPS = 8;
 
 template <bool HALF>
 __global__ void __launch_bounds__(EXT_WARPS * 32) k_bf16_ext(Rows R, int64_t N, int dx,
-                                                            __nv_bfloat16* Xe,
+                                                            __nv_bfloat16* Xe, float* wx,
                                                             unsigned long long* inexact) {
   __shared__ float tile[EXT_WARPS][32][33];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -640,6 +640,7 @@ __global__ void __launch_bounds__(EXT_WARPS * 32) k_bf16_ext(Rows R, int64_t N, 
   tail[2] = __fsqrt_ru(nb2 * grow) * 1.000001f;
   tail[3] = __fsqrt_rn(nx2);
   tail[4] = exact ? __double2float_ru((double)d * (double)mx * (double)mx) : -1.0f;
+  if (wx) wx[i] = tail[4];
   if (!exact && inexact) atomicAdd(inexact, 1ull);
   tail[5] = tail[6] = tail[7] = 0.0f;
 }
@@ -736,13 +737,20 @@ cudaError_t plan_pipe(int precision, int metric, int cap_new, int cap_old, int d
   if (!tc && d % 4 != 0) return cudaErrorInvalidValue;
   P->cap = cap;
   const int RB = rec_bytes(cap);
-  int ring = ((cap + RING_EXTRA) + 7) & ~7;
+  // Ring rows: the largest candidate set (the rows of the next node come in
+  // when both fit).  Every byte per warp counts: the kernel is latency-bound
+  // and the warps per SM are set by the shared memory each one holds.
+  int ring = (cap_new + cap_old + 1) & ~1;
+  P->gstr = (cap_new + cap_old + 3) & ~3;
   if (tc) {
     const int dpad = (d + 15) & ~15;
     P->dx = dpad + 16;
-    P->row_bytes = P->dx * 2;
-    P->row_stride = P->row_bytes + 16;  // 16-byte skew: conflict-free ldmatrix
-    if (ring < 32) ring = 32;           // the 16-row A tiles reach row 31
+    // staged: the 16-bit elements and the tail's first four floats (the fifth,
+    // the exactness width, travels in the record); a stride of 16 mod 32
+    // bytes keeps the 8-row ldmatrix reads free of bank conflicts
+    P->row_bytes = dpad * 2 + 16;
+    P->row_stride = P->row_bytes;
+    if (ring < 32) ring = 32;  // the 16-row A tiles reach row 31
   } else {
     P->dx = 0;
     P->row_bytes = d * 4;
@@ -753,7 +761,7 @@ cudaError_t plan_pipe(int precision, int metric, int cap_new, int cap_old, int d
   P->pair_cap = cap_new * (cap_new + cap_old) - cap_new * (cap_new + 1) / 2;
   size_t wb = (size_t)ring * P->row_stride + (size_t)NREC * RB + 2 * NREC * 8 +
               (((size_t)P->pair_cap * 2 + 15) & ~(size_t)15);
-  if (tc) wb += (size_t)16 * GSTR * 4;
+  if (tc) wb += (size_t)16 * P->gstr * 4;
   wb = (wb + 127) & ~(size_t)127;
   P->warp_bytes = (int)wb;
   // warps per block: as many as fit the 227 KB a block may hold (at most
@@ -825,14 +833,14 @@ cudaError_t launch_pipe(int precision, const JoinArgs& a, const PipeArgs& P, siz
   return cudaGetLastError();
 }
 
-cudaError_t launch_bf16_ext(Rows rows, int64_t N, int dx, __nv_bfloat16* Xe, int half,
+cudaError_t launch_bf16_ext(Rows rows, int64_t N, int dx, __nv_bfloat16* Xe, float* wx, int half,
                             unsigned long long* inexact, cudaStream_t st) {
   if (N == 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((N + EXT_WARPS * 32 - 1) / (EXT_WARPS * 32));
   if (half)
-    k_bf16_ext<true><<<blocks, EXT_WARPS * 32, 0, st>>>(rows, N, dx, Xe, inexact);
+    k_bf16_ext<true><<<blocks, EXT_WARPS * 32, 0, st>>>(rows, N, dx, Xe, wx, inexact);
   else
-    k_bf16_ext<false><<<blocks, EXT_WARPS * 32, 0, st>>>(rows, N, dx, Xe, inexact);
+    k_bf16_ext<false><<<blocks, EXT_WARPS * 32, 0, st>>>(rows, N, dx, Xe, wx, inexact);
   return cudaGetLastError();
 }
 
