@@ -953,13 +953,14 @@ def run_ours(args, w):
             # sampler: lists and flags read, snapshot written, k-th keys; per
             # list entry its forward id (written, read back), reverse key
             # (written, read back) and in-edge count; per staged candidate
-            # its record entry (id, k-th key); per node the record header
-            # and the four set counts
-            nbytes["sample"] += N * K * (9 + 8 + 8 + 16 + 4) + N * (8 + 16 + 16) + G * 12
-            # join: per staged row the 16-bit row with its error data, its id
-            # and k-th key; per re-ranked pair both FP32 rows; per proposal its
-            # key and its target's count; per node the candidate counts
-            nbytes["join"] += (G * (d * 2 + 4 + 8 + 16) + st["reranked"][r] * 2 * d * 4
+            # its record entry (id, k-th key, exactness width); per node the
+            # record header and the four set counts
+            nbytes["sample"] += N * K * (9 + 8 + 8 + 16 + 4) + N * (8 + 16 + 16) + G * 16
+            # join: per staged row the 16-bit row with its 16 bytes of error
+            # data, its id, k-th key and exactness width; per re-ranked pair
+            # both FP32 rows; per proposal its key and its target's count; per
+            # node the candidate counts
+            nbytes["join"] += (G * (d * 2 + 16 + 4 + 8 + 4) + st["reranked"][r] * 2 * d * 4
                                + P * 12 + N * 8)
             # update: per proposal its key; per node the list, the round-start
             # snapshot and flags read, list and flags written, its count
