@@ -306,7 +306,8 @@ __device__ __forceinline__ void slots_insert(uint64_t* slots, int m, uint64_t x)
 // slots_insert for a key that is usually no improvement: one read of the m-th
 // slot rejects it (slots only decrease, so a key not below the current m-th
 // can never be among the m smallest, and an equal key is already held).
-__device__ __forceinline__ void slots_insert_checked(uint64_t* slots, int m, uint64_t x) {
+// Out of line: the rare overflow path stays out of the join kernels' hot code.
+static __device__ __noinline__ void slots_insert_checked(uint64_t* slots, int m, uint64_t x) {
   if (x >= *((volatile uint64_t*)(slots + m - 1))) return;
   slots_insert(slots, m, x);
 }

@@ -150,8 +150,11 @@ __device__ __forceinline__ Rec read_rec(const JoinArgs& a, const unsigned char* 
 }
 
 // Lists the allowed pairs (i < nn, i < j < M, set test) into `pairs`, sorted by
-// first index: the whole warp expands one row's partner mask at a time.  *np0
-// receives the number of pairs whose first index is below 16.
+// first index, then second.  *np0 receives the number of pairs whose first
+// index is below 16.  Two ways to the same list: with many new candidates each
+// lane walks half a row's partner mask (the cost follows the longest half-row),
+// with few the warp expands one row at a time (the cost follows the rows).
+constexpr int LIST_LANES_FROM = 8;
 __device__ __forceinline__ int list_pairs(const JoinArgs& a, const Rec& rc, uint16_t* pairs,
                                           int* np0) {
   const int lane = threadIdx.x & 31;
@@ -169,13 +172,37 @@ __device__ __forceinline__ int list_pairs(const JoinArgs& a, const Rec& rc, uint
   const int np = __shfl_sync(FULL, incl, 31);
   *np0 = __shfl_sync(FULL, incl, 15);
   const int excl = incl - cnt;
-  const unsigned lt = (1u << lane) - 1u;
-  for (int i = 0; i < rc.nn; ++i) {
-    const uint32_t m0 = (uint32_t)__shfl_sync(FULL, (unsigned)pm, i);
-    const uint32_t m1 = (uint32_t)__shfl_sync(FULL, (unsigned)(pm >> 32), i);
-    const int b = __shfl_sync(FULL, excl, i);
-    if ((m0 >> lane) & 1u) pairs[b + __popc(m0 & lt)] = (uint16_t)((i << 8) | lane);
-    if ((m1 >> lane) & 1u) pairs[b + __popc(m0) + __popc(m1 & lt)] = (uint16_t)((i << 8) | (lane + 32));
+  if (rc.nn >= LIST_LANES_FROM) {
+    // Sixteen rows a pass: lane r < 16 writes the pairs of row rb + r with
+    // partners below 32, lane r + 16 those with partners from 32 on, each in
+    // ascending order from the row's offset; the loop runs as long as the
+    // largest half-row.
+    for (int rb = 0; rb < rc.nn; rb += 16) {
+      const int row = rb + (lane & 15);
+      const uint32_t m0 = (uint32_t)__shfl_sync(FULL, (unsigned)pm, row);
+      const uint32_t m1 = (uint32_t)__shfl_sync(FULL, (unsigned)(pm >> 32), row);
+      const int b = __shfl_sync(FULL, excl, row);
+      uint32_t m = row < rc.nn ? (lane < 16 ? m0 : m1) : 0u;
+      int pos = lane < 16 ? b : b + __popc(m0);
+      const int tag = (row << 8) | (lane < 16 ? 0 : 32);
+      while (m) {
+        const int j = __ffs(m) - 1;
+        m &= m - 1u;
+        pairs[pos++] = (uint16_t)(tag | j);
+      }
+    }
+  } else {
+    // few rows: the warp writes one row at a time, lane j its partner j and
+    // j + 32 (ranks within the row from the mask)
+    const unsigned lt = (1u << lane) - 1u;
+    for (int i = 0; i < rc.nn; ++i) {
+      const uint32_t m0 = (uint32_t)__shfl_sync(FULL, (unsigned)pm, i);
+      const uint32_t m1 = (uint32_t)__shfl_sync(FULL, (unsigned)(pm >> 32), i);
+      const int b = __shfl_sync(FULL, excl, i);
+      if ((m0 >> lane) & 1u) pairs[b + __popc(m0 & lt)] = (uint16_t)((i << 8) | lane);
+      if ((m1 >> lane) & 1u)
+        pairs[b + __popc(m0) + __popc(m1 & lt)] = (uint16_t)((i << 8) | (lane + 32));
+    }
   }
   __syncwarp();
   return np;
