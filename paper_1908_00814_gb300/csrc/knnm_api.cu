@@ -536,6 +536,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     else
       KNNM_CUDA(launch_join(jprec, ja, j.plan, rs));
     if (timed) KNNM_CUDA(cudaEventRecord(ctx->rev[2], rs));
+    ma.prefetch = sa.active_only;  // few proposals: the update waits on loads
     KNNM_CUDA(launch_bucket_update(ma, rs));
     if (timed) KNNM_CUDA(cudaEventRecord(ctx->rev[3], rs));
     if (sa.t_dev) KNNM_CUDA(launch_bump_int(P.tdev, rs));

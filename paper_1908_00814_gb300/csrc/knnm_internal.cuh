@@ -635,6 +635,8 @@ struct MergeArgs {
   int bcap;                   // bucket slots per target
   const uint64_t* bucket;     // [N][bcap] proposal keys per target
   DevCounters* ctr;
+  int prefetch = 0;           // load each node's data one node ahead (rounds of
+                              // few proposals: latency-bound, not issue-bound)
 };
 // The per-node merge of list and bucket (UpdateNN of the whole round) with
 // flags and c_t.

@@ -405,10 +405,18 @@ __global__ void __launch_bounds__(BLOCK) k_sample_fwd(SampleArgs a) {
   const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
   const int K = a.K, s = a.s;
   const uint64_t t = (uint64_t)(a.t_dev ? *a.t_dev : a.t);
-  for (int64_t u = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5); u < a.N;
-       u += nwarps) {
-    uint64_t key = lane < K ? a.keys[(size_t)u * K + lane] : KEY_EMPTY;
-    uint8_t f = lane < K ? a.flags[(size_t)u * K + lane] : FLAG_OLD;
+  // each node's list and flags are loaded one node ahead
+  int64_t u = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
+  uint64_t key_next = u < a.N && lane < K ? a.keys[(size_t)u * K + lane] : KEY_EMPTY;
+  uint8_t f_next = u < a.N && lane < K ? a.flags[(size_t)u * K + lane] : FLAG_OLD;
+  for (; u < a.N; u += nwarps) {
+    const uint64_t key = key_next;
+    const uint8_t f = f_next;
+    const int64_t un = u + nwarps;
+    if (un < a.N && lane < K) {
+      key_next = a.keys[(size_t)un * K + lane];
+      f_next = a.flags[(size_t)un * K + lane];
+    }
     if (a.prev_keys && lane < K) a.prev_keys[(size_t)u * K + lane] = key;
     if (a.kth && lane == K - 1) a.kth[u] = key;
     const int32_t v = key_id(key);
@@ -496,14 +504,18 @@ __global__ void __launch_bounds__(BLOCK) k_sample_scatter(SampleArgs a) {
       nf[j] = in ? a.new_cnt[u0 + j] : 0;
       of[j] = in ? a.old_cnt[u0 + j] : 0;
     }
+    // the id rows are read whole, beside the counts (entries past a count are
+    // stale and unused)
     int32_t vn[U], vo[U];
     bool hn[U], ho[U];
 #pragma unroll
     for (int j = 0; j < U; ++j) {
-      hn[j] = lane < nf[j];
-      vn[j] = hn[j] ? a.new_ids[(size_t)(u0 + j) * a.cap_new + lane] : 0;
-      vo[j] = lane < of[j] ? a.old_ids[(size_t)(u0 + j) * a.cap_old + lane] : 0;
+      const bool in = u0 + j < a.N;
+      vn[j] = in && lane < a.cap_new ? a.new_ids[(size_t)(u0 + j) * a.cap_new + lane] : 0;
+      vo[j] = in && lane < a.cap_old ? a.old_ids[(size_t)(u0 + j) * a.cap_old + lane] : 0;
     }
+#pragma unroll
+    for (int j = 0; j < U; ++j) hn[j] = lane < nf[j];
 #pragma unroll
     for (int j = 0; j < U; ++j)
       ho[j] = lane < of[j] && (!a.active_only || active_by_bucket(a, vo[j]));
@@ -947,6 +959,7 @@ __device__ __forceinline__ uint64_t offer_chunk(uint64_t cur, uint64_t x, int K,
   return cur;
 }
 
+template <bool PF>
 __global__ void __launch_bounds__(BLOCK) k_merge_lists(MergeArgs a) {
   __shared__ unsigned long long red[WARPS_PER_BLOCK];
   __shared__ uint64_t stage[WARPS_PER_BLOCK][32];
@@ -956,11 +969,29 @@ __global__ void __launch_bounds__(BLOCK) k_merge_lists(MergeArgs a) {
   unsigned long long cnt = 0;
   const int64_t passes = (a.N + nwarps - 1) / nwarps;
   const int64_t w0 = (int64_t)blockIdx.x * WARPS_PER_BLOCK + w;
+  // With PF a node's list, count, snapshot, flags and first bucket chunk are
+  // loaded one node ahead (more registers, fewer warps); without, each load
+  // comes where it is first needed.
+  uint64_t cur_n = KEY_EMPTY, pk_n = KEY_EMPTY, x0_n = KEY_EMPTY;
+  uint8_t pf_n = FLAG_NEW;
+  int cv_n = 0;
+  const int first = min(a.bcap, 32);
+  auto load = [&](int64_t v) {
+    cur_n = lane < K ? a.keys[(size_t)v * K + lane] : KEY_EMPTY;
+    cv_n = a.cnt[v];
+    pk_n = lane < K ? a.prev_keys[(size_t)v * K + lane] : KEY_EMPTY;
+    pf_n = lane < K ? a.flags[(size_t)v * K + lane] : (uint8_t)FLAG_NEW;
+    x0_n = lane < first ? a.bucket[(size_t)v * a.bcap + lane] : KEY_EMPTY;
+  };
+  if (PF && w0 < a.N) load(w0);
   for (int64_t p = 0; p < passes; ++p) {
     const int64_t v = w0 + p * nwarps;
     if (v >= a.N) continue;
-    uint64_t cur = lane < K ? a.keys[(size_t)v * K + lane] : KEY_EMPTY;
-    const int cv = a.cnt[v];
+    uint64_t cur = PF ? cur_n : (lane < K ? a.keys[(size_t)v * K + lane] : KEY_EMPTY);
+    const int cv = PF ? cv_n : a.cnt[v];
+    const uint64_t x0 = x0_n, pk_ahead = pk_n;  // this node's, before the next load
+    const uint8_t pf_ahead = pf_n;
+    if (PF && v + nwarps < a.N) load(v + nwarps);
     const uint64_t b0 = (uint64_t)v * a.bcap, b1 = b0 + (uint64_t)min(cv, a.bcap);
     if (lane == 0 && cv) a.cnt[v] = 0;  // the next round's join starts from zero
     // The bucket in groups of four 32-key chunks: each lane's smallest key of
@@ -968,7 +999,8 @@ __global__ void __launch_bounds__(BLOCK) k_merge_lists(MergeArgs a) {
     // K-th key before the other three chunks are offered, so that most of
     // their keys are rejected by one compare.
     if (b1 - b0 <= 32) {
-      cur = offer_chunk(cur, b0 + lane < b1 ? a.bucket[b0 + lane] : KEY_EMPTY, K, stage[w]);
+      cur = offer_chunk(cur, b0 + lane < b1 ? (PF ? x0 : a.bucket[b0 + lane]) : KEY_EMPTY, K,
+                        stage[w]);
     } else for (uint64_t g = b0; g < b1; g += 128) {
       uint64_t x[4];
 #pragma unroll
@@ -991,11 +1023,13 @@ __global__ void __launch_bounds__(BLOCK) k_merge_lists(MergeArgs a) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) cur = offer_chunk(cur, x[q], K, stage[w]);
     }
+    const uint64_t pk =
+        PF ? pk_ahead : (lane < K ? a.prev_keys[(size_t)v * K + lane] : KEY_EMPTY);
+    const uint8_t pf =
+        PF ? pf_ahead : (lane < K ? a.flags[(size_t)v * K + lane] : (uint8_t)FLAG_NEW);
     // flags against the round-start snapshot: an entry is old when the same key
     // was in the list at round start.  The snapshot is sorted ascending (empty
     // places last), so each entry finds its place by a five-step binary search.
-    const uint64_t pk = lane < K ? a.prev_keys[(size_t)v * K + lane] : KEY_EMPTY;
-    const uint8_t pf = lane < K ? a.flags[(size_t)v * K + lane] : FLAG_NEW;
     int at = 0;  // number of snapshot keys <= cur among places 0..30
 #pragma unroll
     for (int step = 16; step > 0; step >>= 1) {
@@ -1405,7 +1439,10 @@ cudaError_t launch_build_records(int64_t N, int K, const uint64_t* keys, const f
 }
 
 cudaError_t launch_bucket_update(const MergeArgs& a, cudaStream_t st) {
-  k_merge_lists<<<grid_for_warps(a.N), BLOCK, 0, st>>>(a);
+  if (a.prefetch)
+    k_merge_lists<true><<<grid_for_warps(a.N), BLOCK, 0, st>>>(a);
+  else
+    k_merge_lists<false><<<grid_for_warps(a.N), BLOCK, 0, st>>>(a);
   return cudaGetLastError();
 }
 
