@@ -544,11 +544,17 @@ cudaError_t launch_set_int(int* p, int v, cudaStream_t st);
 cudaError_t launch_bump_int(int* p, cudaStream_t st);
 
 // Candidate record of one node, read by the pipelined join with one bulk copy:
-//   int32 {nn, no, 0, 0} | int32 ids[cap] (new first) | uint64 kth[cap] | float cn[cap]
-// kth[r] is the k-th key of candidate r's list at round start; cn[r] its
-// canonical norm (COS only).  cap is a multiple of 4, so the record is a
-// multiple of 16 bytes.
+//   int32 {nn, no, 0, 0} | cap entries of 16 bytes {int32 id, float c, uint64 kth}
+// (new candidates first).  kth is the k-th key of the candidate's list at round
+// start; c its exactness width (tensor-core join) or canonical norm (FP32 join,
+// COS).  One 16-byte load gives all three.
 __host__ __device__ __forceinline__ int rec_bytes(int cap) { return 16 + 16 * cap; }
+__device__ __forceinline__ uint4 rec_entry(int32_t id, float c, uint64_t kth) {
+  return make_uint4((uint32_t)id, __float_as_uint(c), (uint32_t)kth, (uint32_t)(kth >> 32));
+}
+__device__ __forceinline__ int32_t rec_id(uint4 e) { return (int32_t)e.x; }
+__device__ __forceinline__ float rec_c(uint4 e) { return __uint_as_float(e.y); }
+__device__ __forceinline__ uint64_t rec_kth(uint4 e) { return ((uint64_t)e.w << 32) | e.z; }
 __host__ __device__ __forceinline__ int round_up4(int x) { return (x + 3) & ~3; }
 
 // Builds records from public candidate lists (the step-API path).
@@ -582,8 +588,8 @@ struct JoinArgs {
   int use_bulk;             // rows may be fetched with bulk async copies
   uint32_t wait_polls = WAIT_LIMIT;  // polls before an mbarrier wait gives up
 };
-// Pipelined join (knnm_join_pipe.cu): per-node candidate records and rows are
-// staged by a producer warp through NS shared-memory stages.
+// Ring join (knnm_join_pipe.cu): per-node candidate records and rows are
+// staged by bulk copies into each warp's own shared-memory ring.
 struct PipeArgs {
   const unsigned char* rec;  // [N][rec_bytes(cap)] candidate records
   int cap;                   // ids per record

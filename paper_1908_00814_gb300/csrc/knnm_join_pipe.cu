@@ -132,20 +132,17 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, uint32
 }
 
 struct Rec {
-  const int32_t* cid;
-  const uint64_t* kth;
-  const float* cn;
+  const uint4* e;  // per candidate {id, width or norm, k-th key}: one 16-byte load
   int nn, M;
+  __device__ __forceinline__ int32_t id(int r) const { return rec_id(e[r]); }
 };
 
-__device__ __forceinline__ Rec read_rec(const JoinArgs& a, const unsigned char* R, int cap) {
+__device__ __forceinline__ Rec read_rec(const JoinArgs& a, const unsigned char* R) {
   Rec r;
   const int32_t* h = (const int32_t*)R;
   r.nn = min(max(h[0], 0), a.cap_new);
   r.M = r.nn + min(max(h[1], 0), a.cap_old);
-  r.cid = (const int32_t*)(R + 16);
-  r.kth = (const uint64_t*)(R + 16 + 4 * cap);
-  r.cn = (const float*)(R + 16 + 12 * cap);
+  r.e = (const uint4*)(R + 16);
   return r;
 }
 
@@ -158,8 +155,8 @@ constexpr int LIST_LANES_FROM = 8;
 __device__ __forceinline__ int list_pairs(const JoinArgs& a, const Rec& rc, uint16_t* pairs,
                                           int* np0) {
   const int lane = threadIdx.x & 31;
-  const bool lo = lane < rc.M && rc.cid[lane] < a.n1;
-  const bool hi = lane + 32 < rc.M && rc.cid[lane + 32] < a.n1;
+  const bool lo = lane < rc.M && rc.id(lane) < a.n1;
+  const bool hi = lane + 32 < rc.M && rc.id(lane + 32) < a.n1;
   const uint64_t s1 = (uint64_t)__ballot_sync(FULL, lo) | ((uint64_t)__ballot_sync(FULL, hi) << 32);
   const uint64_t pm = lane < rc.nn ? partner_mask(a.mode, lane, rc.M, s1) : 0ull;
   const int cnt = __popcll(pm);
@@ -261,15 +258,16 @@ __device__ __forceinline__ void node_fp32(const JoinArgs& a, const Rec& rc, int 
       const int q = q0 + t * 32 + lane;
       const bool live = t < pl && q < np;
       const int i = pi[t], jj = pj[t];
-      const float dist = canon_finish<METRIC>(acc[t], METRIC == COS ? rc.cn[i] : 0.f,
-                                              METRIC == COS ? rc.cn[jj] : 0.f);
-      const int32_t ci = rc.cid[i], cj = rc.cid[jj];
+      const uint4 ei = rc.e[i], ej = rc.e[jj];
+      const float dist = canon_finish<METRIC>(acc[t], METRIC == COS ? rec_c(ei) : 0.f,
+                                              METRIC == COS ? rec_c(ej) : 0.f);
+      const int32_t ci = rec_id(ei), cj = rec_id(ej);
       key[2 * t] = make_key(dist, cj);
       key[2 * t + 1] = make_key(dist, ci);
       tgt[2 * t] = ci;
       tgt[2 * t + 1] = cj;
-      has[2 * t] = live && key[2 * t] < rc.kth[i];
-      has[2 * t + 1] = live && key[2 * t + 1] < rc.kth[jj];
+      has[2 * t] = live && key[2 * t] < rec_kth(ei);
+      has[2 * t + 1] = live && key[2 * t + 1] < rec_kth(ej);
     }
     emit_many(a, sink, has, tgt, key);
     q0 += 32 * pl;
@@ -346,19 +344,19 @@ __device__ __forceinline__ void node_tc(const JoinArgs& a, const Rec& rc, int np
           const float g = G[(i & 15) * gstr + jj];
           const float4 ai = *(const float4*)(row_ptr(i) + dpad * 2);
           const float4 aj = *(const float4*)(row_ptr(jj) + dpad * 2);
-          const float ri = rc.cn[i], rj = rc.cn[jj];
-          tgt[2 * u] = rc.cid[i];
-          tgt[2 * u + 1] = rc.cid[jj];
-          if (exact_rows(ri, rj)) {
+          const uint4 ei = rc.e[i], ej = rc.e[jj];
+          tgt[2 * u] = rec_id(ei);
+          tgt[2 * u + 1] = rec_id(ej);
+          if (exact_rows(rec_c(ei), rec_c(ej))) {
             const float dist = exact_value<METRIC>(g, ai, aj);
             key[2 * u] = make_key(dist, tgt[2 * u + 1]);
             key[2 * u + 1] = make_key(dist, tgt[2 * u]);
-            has[2 * u] = key[2 * u] < rc.kth[i];
-            has[2 * u + 1] = key[2 * u + 1] < rc.kth[jj];
+            has[2 * u] = key[2 * u] < rec_kth(ei);
+            has[2 * u + 1] = key[2 * u + 1] < rec_kth(ej);
           } else {
             float est;
             const float E = bound_tc<METRIC>(g, ai, aj, d, &est);
-            mark[u] = est - E <= fmaxf(key_dist(rc.kth[i]), key_dist(rc.kth[jj]));
+            mark[u] = est - E <= fmaxf(key_dist(rec_kth(ei)), key_dist(rec_kth(ej)));
           }
         }
       }
@@ -383,7 +381,8 @@ __device__ __forceinline__ void node_tc(const JoinArgs& a, const Rec& rc, int np
     if (q < nr) {
       const uint16_t pr = pairs[q];
       const int i = pr >> 8, jj = pr & 0xFF;
-      const int32_t tp = rc.cid[i], tq = rc.cid[jj];
+      const uint4 ei = rc.e[i], ej = rc.e[jj];
+      const int32_t tp = rec_id(ei), tq = rec_id(ej);
       const float4 ai = *(const float4*)(row_ptr(i) + dpad * 2);
       const float4 aj = *(const float4*)(row_ptr(jj) + dpad * 2);
       const float dist =
@@ -393,8 +392,8 @@ __device__ __forceinline__ void node_tc(const JoinArgs& a, const Rec& rc, int np
       tgt[1] = tq;
       key[0] = make_key(dist, tq);
       key[1] = make_key(dist, tp);
-      has[0] = key[0] < rc.kth[i];
-      has[1] = key[1] < rc.kth[jj];
+      has[0] = key[0] < rec_kth(ei);
+      has[1] = key[1] < rec_kth(ej);
     }
     emit_many(a, sink, has, tgt, key);
   }
@@ -469,9 +468,9 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) k_join_ring(JoinArgs a, Pip
     if (lane == 0) mbar_arrive_expect_tx(rowbar + slot_of(j), staged ? (uint32_t)(M * P.row_bytes) : 0u);
     __syncwarp();
     if (staged) {
-      const int32_t* cid = (const int32_t*)(rec_at(j) + 16);
+      const uint4* ent = (const uint4*)(rec_at(j) + 16);
       for (int r = lane; r < M; r += 32) {
-        int32_t id = cid[r];
+        int32_t id = rec_id(ent[r]);
         if (id < 0 || id >= a.N) id = 0;
         const unsigned char* src = TC ? (const unsigned char*)(P.Xe + (size_t)id * P.dx)
                                       : (const unsigned char*)a.rows.row(id);
@@ -502,7 +501,7 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) k_join_ring(JoinArgs a, Pip
       }
       rec_pend &= ~(1u << sl);
       __syncwarp();
-      const Rec rn = read_rec(a, rec_at(next_rows), P.cap);
+      const Rec rn = read_rec(a, rec_at(next_rows));
       const bool st = rn.nn > 0 && rn.M > 1;
       const int need = st ? rn.M : 0;
       if (next_rows > j && ring_tail - ring_head + need > R) break;  // no room yet
@@ -527,7 +526,7 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) k_join_ring(JoinArgs a, Pip
     __syncwarp();
     // the record slot of node j - 1 is free: fetch the record of node j + NREC - 1
     if (j + NREC - 1 < count) fetch_rec(j + NREC - 1);
-    const Rec rc = read_rec(a, rec_at(j), P.cap);
+    const Rec rc = read_rec(a, rec_at(j));
     int base = 0, used = 0;
 #pragma unroll
     for (int x = 0; x < NREC; ++x)

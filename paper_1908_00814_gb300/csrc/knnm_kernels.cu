@@ -734,14 +734,8 @@ __global__ void __launch_bounds__(BLOCK) k_sample_rev(SampleArgs a) {
         if (keep_ro) c_ro = __ldg(&a.norms[ro]);
       }
       unsigned char* R = a.rec + (size_t)u * rec_bytes(a.rec_cap);
-      int32_t* rid = (int32_t*)(R + 16);
-      uint64_t* rkth = (uint64_t*)(R + 16 + 4 * a.rec_cap);
-      float* rcn = (float*)(R + 16 + 12 * a.rec_cap);
-      auto put = [&](int pos, int32_t id, uint64_t k, float c) {
-        rid[pos] = id;
-        rkth[pos] = k;
-        if (a.norms) rcn[pos] = c;
-      };
+      uint4* ent = (uint4*)(R + 16);
+      auto put = [&](int pos, int32_t id, uint64_t k, float c) { ent[pos] = rec_entry(id, c, k); };
       if (has_fn) put(lane, fn, k_fn, c_fn);
       if (add_rn) put(p_rn, rn, k_rn, c_rn);
       if (keep_fo) put(nn + p_fo, fo, k_fo, c_fo);
@@ -770,16 +764,12 @@ __global__ void __launch_bounds__(BLOCK) k_build_records(int64_t N, int K, const
        u += nwarps) {
     const int nn = min(new_cnt[u], cap_new), no = min(old_cnt[u], cap_old);
     unsigned char* R = rec + (size_t)u * rec_bytes(rec_cap);
-    int32_t* rid = (int32_t*)(R + 16);
-    uint64_t* rkth = (uint64_t*)(R + 16 + 4 * rec_cap);
-    float* rcn = (float*)(R + 16 + 12 * rec_cap);
+    uint4* ent = (uint4*)(R + 16);
     for (int r = lane; r < nn + no; r += 32) {
       const int32_t id = r < nn ? new_ids[(size_t)u * cap_new + r]
                                 : old_ids[(size_t)u * cap_old + (r - nn)];
       const int32_t safe = (id < 0 || id >= N) ? 0 : id;
-      rid[r] = id;
-      rkth[r] = keys[(size_t)safe * K + (K - 1)];
-      if (norms) rcn[r] = norms[safe];
+      ent[r] = rec_entry(id, norms ? norms[safe] : 0.0f, keys[(size_t)safe * K + (K - 1)]);
     }
     if (lane == 0) {
       int32_t* h = (int32_t*)R;
