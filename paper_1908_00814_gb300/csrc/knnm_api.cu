@@ -290,7 +290,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     uint64_t* bucket;
     int32_t* rcnt;
     unsigned long long *roffs, *rtile, *rtotal;
-    uint64_t* rbucket;
+    int32_t* rbucket;
     int* tdev;
     uint64_t* kth;
   } P;
@@ -305,7 +305,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     P.rear = c.take<uint64_t>((size_t)N * (D.Kr > 0 ? D.Kr : 1));
     P.rcnt = c.take<int32_t>((size_t)2 * N);
     P.roffs = c.take<unsigned long long>((size_t)2 * N + 1);
-    P.rbucket = c.take<uint64_t>((size_t)N * K);
+    P.rbucket = c.take<int32_t>((size_t)N * K);
     P.rtile = c.take<unsigned long long>((size_t)(2 * N + 1023) / 1024 + 1);
     P.rtotal = c.take<unsigned long long>(1);
     P.tdev = c.take<int>(1);
@@ -1295,7 +1295,8 @@ extern "C" int knnm_step_sample(knnm_ctx* ctx, int64_t N, int K, const int32_t* 
     return fail(ctx, KNNM_ERR_INVALID, "bad sampling arguments");
   cudaStream_t st = ctx->stream;
   KNNM_CUDA(cudaSetDevice(ctx->device));
-  uint64_t *keys, *rbucket;
+  uint64_t* keys;
+  int32_t* rbucket;
   int32_t* rcnt;
   unsigned long long *roffs, *rtile, *rtotal;
   DevCounters* ctr;
@@ -1303,7 +1304,7 @@ extern "C" int knnm_step_sample(knnm_ctx* ctx, int64_t N, int K, const int32_t* 
     keys = c.take<uint64_t>((size_t)N * K);
     rcnt = c.take<int32_t>((size_t)2 * N);
     roffs = c.take<unsigned long long>((size_t)2 * N + 1);
-    rbucket = c.take<uint64_t>((size_t)N * K);
+    rbucket = c.take<int32_t>((size_t)N * K);
     rtile = c.take<unsigned long long>((size_t)(2 * N + 1023) / 1024 + 1);
     rtotal = c.take<unsigned long long>(1);
     ctr = c.take<DevCounters>(1);

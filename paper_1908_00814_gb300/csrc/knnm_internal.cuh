@@ -508,7 +508,7 @@ struct SampleArgs {
   // Bucketed reverse sampling (used when rcnt is set; rev_new/rev_old unused):
   int32_t* rcnt = nullptr;             // [2N] in-edges per (target, stream); zero on entry and exit
   unsigned long long* roffs = nullptr;  // [2N+1] bucket offsets
-  uint64_t* rbucket = nullptr;         // [N*K] reverse sampling keys grouped by (target, stream)
+  int32_t* rbucket = nullptr;          // [N*K] reverse in-edges' source ids grouped by (target, stream)
   unsigned long long* tile_sum = nullptr;  // [ceil(2N/1024)+1] scan scratch
   unsigned long long* total = nullptr;     // scan total
   // Join-only sampling (bucketed path): old(u) is built only for nodes whose

@@ -483,8 +483,9 @@ __global__ void __launch_bounds__(BLOCK) k_sample_count_old(SampleArgs a) {
   }
 }
 
-// Moves each reverse edge's sampling key into its (target, stream) bucket;
-// the counts are consumed back to zero.
+// Moves each reverse edge's source id into its (target, stream) bucket (the
+// reverse pass derives the sampling keys from the ids); the counts are
+// consumed back to zero.
 // Two nodes per warp and pass: each step's loads (counts, ids, bucket starts)
 // and slot claims of both are in flight together, since every step waits
 // on the one before.
@@ -494,7 +495,6 @@ __global__ void __launch_bounds__(BLOCK) k_sample_scatter(SampleArgs a) {
   constexpr int U = SCATTER_NODES;
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
-  const uint64_t t = (uint64_t)(a.t_dev ? *a.t_dev : a.t);
   for (int64_t u0 = ((int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5)) * U; u0 < a.N;
        u0 += nwarps * U) {
     int nf[U], of[U];
@@ -533,12 +533,8 @@ __global__ void __launch_bounds__(BLOCK) k_sample_scatter(SampleArgs a) {
     }
 #pragma unroll
     for (int j = 0; j < U; ++j) {
-      if (hn[j])
-        a.rbucket[bn[j] + (uint64_t)pn[j]] = sampling_key(
-            hash_prefix(a.seed, t, STREAM_REV_NEW, (uint64_t)vn[j]), (int32_t)(u0 + j));
-      if (ho[j])
-        a.rbucket[bo[j] + (uint64_t)po[j]] = sampling_key(
-            hash_prefix(a.seed, t, STREAM_REV_OLD, (uint64_t)vo[j]), (int32_t)(u0 + j));
+      if (hn[j]) a.rbucket[bn[j] + (uint64_t)pn[j]] = (int32_t)(u0 + j);
+      if (ho[j]) a.rbucket[bo[j] + (uint64_t)po[j]] = (int32_t)(u0 + j);
     }
   }
 }
@@ -570,14 +566,15 @@ __device__ __forceinline__ uint64_t select_any32(uint64_t x, int c, int s, uint6
   return lane < __popc(sel) ? y : KEY_EMPTY;
 }
 
-// The s smallest keys of bucket [b0, b1) with b1 - b0 > 32, ascending, lane j
-// holding the j-th (KEY_EMPTY beyond).  Keys in a bucket are distinct.
-__device__ __forceinline__ uint64_t warp_smallest_long(const uint64_t* bucket, uint64_t b0,
-                                                       uint64_t b1, int s) {
+// The s smallest sampling keys of the source ids in bucket [b0, b1) with
+// b1 - b0 > 32 (keys from the bucket owner's hash prefix), ascending, lane j
+// holding the j-th (KEY_EMPTY beyond).  Ids in a bucket are distinct.
+__device__ __forceinline__ uint64_t warp_smallest_long(const int32_t* bucket, uint64_t b0,
+                                                       uint64_t b1, int s, uint64_t prefix) {
   const int lane = threadIdx.x & 31;
   uint64_t best = KEY_EMPTY;
   for (uint64_t c = b0; c < b1; c += 32) {
-    uint64_t x = c + lane < b1 ? bucket[c + lane] : KEY_EMPTY;
+    uint64_t x = c + lane < b1 ? sampling_key(prefix, bucket[c + lane]) : KEY_EMPTY;
     const uint64_t kth = __shfl_sync(FULL, best, s - 1);
     if (x >= kth) x = KEY_EMPTY;
     unsigned live = __ballot_sync(FULL, x != KEY_EMPTY);
@@ -612,6 +609,11 @@ __global__ void __launch_bounds__(BLOCK) k_sample_rev(SampleArgs a) {
   const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
   const int s = a.s;
   const bool buckets = a.rcnt != nullptr;
+  // hash prefixes of the two reverse streams up to the owner (the same for
+  // every node of the round); each node's own is one more mixing step
+  const uint64_t t = (uint64_t)(a.t_dev ? *a.t_dev : a.t);
+  const uint64_t h_new = mix_step(mix_step(mix_step(a.seed) ^ t) ^ STREAM_REV_NEW);
+  const uint64_t h_old = mix_step(mix_step(mix_step(a.seed) ^ t) ^ STREAM_REV_OLD);
   uint64_t* st = stage[threadIdx.x >> 5];
   int32_t(*sw)[32] = sets[threadIdx.x >> 5];
   int64_t u = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
@@ -654,10 +656,14 @@ __global__ void __launch_bounds__(BLOCK) k_sample_rev(SampleArgs a) {
     // first wave: forward ids and the first 32 keys of both buckets
     const int32_t fn = lane < nf ? a.new_ids[(size_t)u * a.cap_new + lane] : -1;
     const int32_t fo = lane < of ? a.old_ids[(size_t)u * a.cap_old + lane] : -2;
-    uint64_t xn, xo;
+    uint64_t xn, xo, pre_n = 0, pre_o = 0;
     if (buckets) {
-      xn = r0 + lane < r1 ? a.rbucket[r0 + lane] : KEY_EMPTY;
-      xo = r1 + lane < r2 ? a.rbucket[r1 + lane] : KEY_EMPTY;
+      const int32_t yn = r0 + lane < r1 ? a.rbucket[r0 + lane] : -1;
+      const int32_t yo = r1 + lane < r2 ? a.rbucket[r1 + lane] : -1;
+      pre_n = mix_step(h_new ^ (uint64_t)u);  // = hash_prefix(seed, t, STREAM_REV_NEW, u)
+      pre_o = mix_step(h_old ^ (uint64_t)u);
+      xn = yn >= 0 ? sampling_key(pre_n, yn) : KEY_EMPTY;
+      xo = yo >= 0 ? sampling_key(pre_o, yo) : KEY_EMPTY;
     } else {
       xn = lane < s ? a.rev_new[(size_t)u * s + lane] : KEY_EMPTY;
       xo = lane < s ? a.rev_old[(size_t)u * s + lane] : KEY_EMPTY;
@@ -666,12 +672,14 @@ __global__ void __launch_bounds__(BLOCK) k_sample_rev(SampleArgs a) {
     if (buckets) {
       const uint64_t cn = r1 - r0, co = r2 - r1;
       if (a.records_only) {
-        rk = cn > 32 ? warp_smallest_long(a.rbucket, r0, r1, s) : select_any32(xn, (int)cn, s, st);
-        ok = co > 32 ? warp_smallest_long(a.rbucket, r1, r2, s) : select_any32(xo, (int)co, s, st);
+        rk = cn > 32 ? warp_smallest_long(a.rbucket, r0, r1, s, pre_n)
+                     : select_any32(xn, (int)cn, s, st);
+        ok = co > 32 ? warp_smallest_long(a.rbucket, r1, r2, s, pre_o)
+                     : select_any32(xo, (int)co, s, st);
       } else {
-        rk = cn > 32 ? warp_smallest_long(a.rbucket, r0, r1, s)
+        rk = cn > 32 ? warp_smallest_long(a.rbucket, r0, r1, s, pre_n)
                      : select_sorted32(xn, (int)cn, s, st);
-        ok = co > 32 ? warp_smallest_long(a.rbucket, r1, r2, s)
+        ok = co > 32 ? warp_smallest_long(a.rbucket, r1, r2, s, pre_o)
                      : select_sorted32(xo, (int)co, s, st);
       }
     }
