@@ -270,6 +270,8 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   if (tc && !adaptive) ctx->err[0] = 0;
 
   const int bcap = proposal_slots(ctx, K);
+  // candidate records (and the per-node entry fields) whenever a ring join runs
+  const bool with_rec = jp.pipe || (adaptive && jp32.pipe);
   // Carve the scratch (two passes: size, then pointers).
   struct Ptrs {
     float* X;
@@ -292,7 +294,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     unsigned long long *roffs, *rtile, *rtotal;
     int32_t* rbucket;
     int* tdev;
-    uint64_t* kth;
+    uint4* info;
   } P;
   auto carve = [&](Carver& c) {
     P.X = (!s1_dev || !s2_dev) ? c.take<float>((size_t)N * d) : nullptr;
@@ -309,7 +311,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     P.rtile = c.take<unsigned long long>((size_t)(2 * N + 1023) / 1024 + 1);
     P.rtotal = c.take<unsigned long long>(1);
     P.tdev = c.take<int>(1);
-    P.kth = P.rec ? c.take<uint64_t>((size_t)N) : nullptr;
+    P.info = with_rec ? c.take<uint4>((size_t)N) : nullptr;
     P.flags = c.take<uint8_t>((size_t)N * K);
     P.new_ids = c.take<int32_t>((size_t)N * D.cap_new);
     P.new_cnt = c.take<int32_t>((size_t)N);
@@ -321,7 +323,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     P.rmax = tc && !jp.pipe ? c.take<float>((size_t)N) : nullptr;
     P.Xe = tc && jp.pipe ? c.take<__nv_bfloat16>((size_t)N * jp.pa.dx) : nullptr;
     P.wx = tc && jp.pipe ? c.take<float>((size_t)N) : nullptr;
-    P.rec = (jp.pipe || (adaptive && jp32.pipe))
+    P.rec = with_rec
                 ? c.take<unsigned char>((size_t)N * rec_bytes(jp.pipe ? jp.pa.cap : jp32.pa.cap))
                 : nullptr;
     P.ctr = c.take<DevCounters>(1);
@@ -403,6 +405,12 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
                               &P.ctr->inexact, st));
     ++launches;
   }
+  // the per-node entry fields: widths and norms into their words of P.info
+  // (the sampler writes the k-th keys each round)
+  if (P.info) {
+    KNNM_CUDA(launch_fill_info(N, P.wx, P.norms, P.info, st));
+    ++launches;
+  }
 
   InitArgs ia;
   ia.mode = in.mode;
@@ -475,7 +483,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     sa.rec_cap = jp.pipe ? jp.pa.cap : jp32.pa.cap;
     sa.norms = P.norms;
     sa.K_list = K;
-    sa.kth = P.kth;
+    sa.info = P.info;
     jp.pa.rec = P.rec;
     jp.pa.Xe = P.Xe;
     jp32.pa.rec = P.rec;
@@ -526,7 +534,8 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
     // column is the rows' exactness width for the tensor-core ring join and
     // the cosine norm (or nothing) for the FP32 one
     sa.records_only = (P.rec && j.pipe) ? 1 : 0;
-    sa.norms = (tc && !alt && jp.pipe) ? P.wx : P.norms;
+    sa.info_c = (tc && !alt && jp.pipe) ? 0 : (P.norms ? 1 : -1);
+    sa.norms = (tc && !alt && jp.pipe) ? P.wx : P.norms;  // the same column without info
     if (timed) KNNM_CUDA(cudaEventRecord(ctx->rev[0], rs));
     KNNM_CUDA(launch_sample(sa, rs));
     if (timed) KNNM_CUDA(cudaEventRecord(ctx->rev[1], rs));

@@ -503,7 +503,13 @@ struct SampleArgs {
   int rec_cap = 0;               // ids per record (multiple of 4)
   const float* norms = nullptr;  // canonical norms (COS) copied into the records, else null
   int K_list = 0;                // list length, for the k-th key of each candidate
-  uint64_t* kth = nullptr;       // [N] round-start k-th key of every list (small: stays in L2)
+  // [N] per node {exactness width, canonical norm, round-start k-th key}: a
+  // record entry's fields from one 16-byte gather (16 MB per 1M nodes: stays
+  // in L2).  The sampler writes the k-th keys; info_c picks the word that goes
+  // into the records' third column (0 the width, 1 the norm, -1 none).  When
+  // null, the k-th keys come from the lists and the norms from `norms`.
+  uint4* info = nullptr;
+  int info_c = -1;
   // Bucketed reverse sampling (used when rcnt is set; rev_new/rev_old unused):
   // Bucketed reverse sampling (used when rcnt is set; rev_new/rev_old unused):
   int32_t* rcnt = nullptr;             // [2N] in-edges per (target, stream); zero on entry and exit
@@ -556,6 +562,10 @@ __device__ __forceinline__ int32_t rec_id(uint4 e) { return (int32_t)e.x; }
 __device__ __forceinline__ float rec_c(uint4 e) { return __uint_as_float(e.y); }
 __device__ __forceinline__ uint64_t rec_kth(uint4 e) { return ((uint64_t)e.w << 32) | e.z; }
 __host__ __device__ __forceinline__ int round_up4(int x) { return (x + 3) & ~3; }
+
+// Fills the width and norm words of every node's entry fields (SampleArgs::info).
+cudaError_t launch_fill_info(int64_t N, const float* wx, const float* norms, uint4* info,
+                             cudaStream_t st);
 
 // Builds records from public candidate lists (the step-API path).
 cudaError_t launch_build_records(int64_t N, int K, const uint64_t* keys, const float* norms,

@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(BLOCK) k_sample_fwd(SampleArgs a) {
       f_next = a.flags[(size_t)un * K + lane];
     }
     if (a.prev_keys && lane < K) a.prev_keys[(size_t)u * K + lane] = key;
-    if (a.kth && lane == K - 1) a.kth[u] = key;
+    if (a.info && lane == K - 1) reinterpret_cast<uint64_t*>(a.info + u)[1] = key;
     const int32_t v = key_id(key);
     const bool isnew = lane < K && f == FLAG_NEW;
     const bool isold = lane < K && f != FLAG_NEW;
@@ -728,26 +728,26 @@ __global__ void __launch_bounds__(BLOCK) k_sample_rev(SampleArgs a) {
       a.old_cnt[u] = no;
     }
     if (a.rec) {
-      // second wave: every k-th key and norm, then the stores
-      auto kth_of = [&](int32_t id) -> uint64_t {
-        return a.kth ? __ldg(&a.kth[id]) : __ldg(&a.keys[(size_t)id * a.K_list + (a.K_list - 1)]);
+      // second wave: every candidate's entry fields (one 16-byte gather each),
+      // then the stores
+      auto entry_of = [&](int32_t id) -> uint4 {
+        if (a.info) {
+          const uint4 f = __ldg(&a.info[id]);
+          const uint32_t c = a.info_c == 0 ? f.x : (a.info_c == 1 ? f.y : 0u);
+          return make_uint4((uint32_t)id, c, f.z, f.w);
+        }
+        return rec_entry(id, a.norms ? __ldg(&a.norms[id]) : 0.0f,
+                         __ldg(&a.keys[(size_t)id * a.K_list + (a.K_list - 1)]));
       };
-      const uint64_t k_fn = has_fn ? kth_of(fn) : 0, k_rn = add_rn ? kth_of(rn) : 0,
-                     k_fo = keep_fo ? kth_of(fo) : 0, k_ro = keep_ro ? kth_of(ro) : 0;
-      float c_fn = 0.f, c_rn = 0.f, c_fo = 0.f, c_ro = 0.f;
-      if (a.norms) {
-        if (has_fn) c_fn = __ldg(&a.norms[fn]);
-        if (add_rn) c_rn = __ldg(&a.norms[rn]);
-        if (keep_fo) c_fo = __ldg(&a.norms[fo]);
-        if (keep_ro) c_ro = __ldg(&a.norms[ro]);
-      }
+      const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+      const uint4 e_fn = has_fn ? entry_of(fn) : zero, e_rn = add_rn ? entry_of(rn) : zero,
+                  e_fo = keep_fo ? entry_of(fo) : zero, e_ro = keep_ro ? entry_of(ro) : zero;
       unsigned char* R = a.rec + (size_t)u * rec_bytes(a.rec_cap);
       uint4* ent = (uint4*)(R + 16);
-      auto put = [&](int pos, int32_t id, uint64_t k, float c) { ent[pos] = rec_entry(id, c, k); };
-      if (has_fn) put(lane, fn, k_fn, c_fn);
-      if (add_rn) put(p_rn, rn, k_rn, c_rn);
-      if (keep_fo) put(nn + p_fo, fo, k_fo, c_fo);
-      if (keep_ro) put(nn + p_ro, ro, k_ro, c_ro);
+      if (has_fn) ent[lane] = e_fn;
+      if (add_rn) ent[p_rn] = e_rn;
+      if (keep_fo) ent[nn + p_fo] = e_fo;
+      if (keep_ro) ent[nn + p_ro] = e_ro;
       if (lane == 0) {
         int32_t* h = (int32_t*)R;
         h[0] = nn;
@@ -1441,6 +1441,22 @@ cudaError_t launch_bucket_update(const MergeArgs& a, cudaStream_t st) {
     k_merge_lists<true><<<grid_for_warps(a.N), BLOCK, 0, st>>>(a);
   else
     k_merge_lists<false><<<grid_for_warps(a.N), BLOCK, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// First two words of each node's entry fields: exactness width and norm (0
+// where absent).
+__global__ void k_fill_info(int64_t N, const float* wx, const float* norms, uint4* info) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  reinterpret_cast<uint2*>(info + i)[0] =
+      make_uint2(__float_as_uint(wx ? wx[i] : 0.0f), __float_as_uint(norms ? norms[i] : 0.0f));
+}
+
+cudaError_t launch_fill_info(int64_t N, const float* wx, const float* norms, uint4* info,
+                             cudaStream_t st) {
+  if (N == 0) return cudaSuccess;
+  k_fill_info<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, wx, norms, info);
   return cudaGetLastError();
 }
 
