@@ -951,11 +951,11 @@ def run_ours(args, w):
         for r in range(st["rounds"]):
             G, P = st["gathered"][r], st["proposals"][r]
             # sampler: lists and flags read, snapshot written, k-th keys; per
-            # list entry its forward id (written, read back), reverse key
-            # (written, read back) and in-edge count; per staged candidate
-            # its record entry (id, k-th key, exactness width); per node the
-            # record header and the four set counts
-            nbytes["sample"] += N * K * (9 + 8 + 8 + 16 + 4) + N * (8 + 16 + 16) + G * 16
+            # list entry its forward id (written, read back), reverse source
+            # id (written, read back) and in-edge count; per staged candidate
+            # its 16-byte record entry (id, width or norm, k-th key); per node
+            # the record header and the four set counts
+            nbytes["sample"] += N * K * (9 + 8 + 8 + 8 + 4) + N * (8 + 16 + 16) + G * 16
             # join: per staged row the 16-bit row with its 16 bytes of error
             # data, its id, k-th key and exactness width; per re-ranked pair
             # both FP32 rows; per proposal its key and its target's count; per
