@@ -301,7 +301,10 @@ __device__ __forceinline__ void node_tc(const JoinArgs& a, const Rec& rc, int np
       for (int t = 0; t < 4; ++t) {
         c[t][0] = c[t][1] = c[t][2] = c[t][3] = 0.f;
         const int tile = nt + t < ntiles ? nt + t : ntiles - 1;
-        pb[t] = row_ptr(tile * 8 + (lane & 7)) + ((lane >> 3) & 1) * 16;
+        // rows past the last candidate (padding of the last 8-column tile)
+        // read the last candidate instead: every read stays inside the ring,
+        // and those columns are never used
+        pb[t] = row_ptr(min(tile * 8 + (lane & 7), rc.M - 1)) + ((lane >> 3) & 1) * 16;
       }
 #pragma unroll 4
       for (int k0 = 0; k0 < dpad; k0 += 16) {
