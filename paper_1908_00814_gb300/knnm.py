@@ -295,7 +295,20 @@ class Context:
             raise KnnmError(rc, lib().knnm_last_error(self.h).decode())
 
     # ------------------------------------------------------------ whole merges
-    def _outputs(self, like, n, k):
+    def _outputs(self, like, n, k, out=None):
+        """Output ids [n, k] int32 and distances [n, k] float32: the caller's `out`
+        pair (for example pinned host buffers, so that the library's copy back
+        runs at full speed), checked, else new arrays where `like` lives."""
+        if out is not None:
+            ids, dists = out
+            for a, dt, name in ((ids, "int32", "ids"), (dists, "float32", "dists")):
+                shape = tuple(a.shape)
+                dtype = str(a.dtype).replace("torch.", "")
+                contiguous = a.is_contiguous() if _is_torch(a) else a.flags["C_CONTIGUOUS"]
+                if shape != (n, k) or dtype != dt or not contiguous:
+                    raise ValueError(f"out {name}: need a contiguous {dt} array of shape "
+                                     f"({n}, {k}), got {dtype} {shape}")
+            return ids, dists
         if _is_torch(like):
             import torch
             dev = like.device if like.is_cuda else "cpu"
@@ -303,10 +316,10 @@ class Context:
                     torch.empty((n, k), dtype=torch.float32, device=dev))
         return np.empty((n, k), np.int32), np.empty((n, k), np.float32)
 
-    def merge_symmetric(self, S1, G1, S2, G2, p: Params):
+    def merge_symmetric(self, S1, G1, S2, G2, p: Params, out=None):
         n1, d = S1.shape
         n2 = S2.shape[0]
-        ids, dists = self._outputs(S1, n1 + n2, p.k)
+        ids, dists = self._outputs(S1, n1 + n2, p.k, out)
         st = Stats()
         self._sync_stream()
         self._check(lib().knnm_merge_symmetric(self.h, _ptr(S1), n1, _ptr(G1), _ptr(S2), n2,
@@ -314,10 +327,10 @@ class Context:
                                                _ptr(dists), ctypes.byref(st)))
         return ids, dists, st.as_dict()
 
-    def merge_joint(self, S1, G1, S_new, p: Params):
+    def merge_joint(self, S1, G1, S_new, p: Params, out=None):
         n1, d = S1.shape
         n2 = S_new.shape[0]
-        ids, dists = self._outputs(S_new, n1 + n2, p.k)
+        ids, dists = self._outputs(S_new, n1 + n2, p.k, out)
         st = Stats()
         self._sync_stream()
         self._check(lib().knnm_merge_joint(self.h, _ptr(S1), n1, _ptr(G1), _ptr(S_new), n2, d,
@@ -471,9 +484,9 @@ class Context:
                                                    ctypes.byref(out)))
         return int(out.value)
 
-    def build(self, S, p: Params):
+    def build(self, S, p: Params, out=None):
         n, d = S.shape
-        ids, dists = self._outputs(S, n, p.k)
+        ids, dists = self._outputs(S, n, p.k, out)
         st = Stats()
         self._sync_stream()
         self._check(lib().knnm_build(self.h, _ptr(S), n, d, ctypes.byref(p), _ptr(ids),

@@ -79,3 +79,24 @@ def test_list_widths_match_the_oracle(built_lib, orc, K, r, rho):
     assert knnm.list_widths(p, knnm.JOINT, 0)[:2] == (K, 0)
     with pytest.raises(knnm.KnnmError):
         knnm.list_widths(knnm.params(k=33), knnm.SYMMETRIC, 100)
+
+
+def test_caller_output_buffers_are_checked():
+    """Output buffers passed by the caller (pinned host memory, say) come back
+    as given when they are contiguous [n, k] int32 / float32, and are refused
+    before any library call otherwise."""
+    import numpy as np
+    import torch
+    from paper_1908_00814_gb300 import knnm
+    outputs = knnm.Context._outputs
+    n, k = 7, 5
+    for make in (lambda s, dt: np.zeros(s, dt), lambda s, dt: torch.zeros(s, dtype=getattr(torch, dt))):
+        ids, dists = make((n, k), "int32"), make((n, k), "float32")
+        got = outputs(None, None, n, k, (ids, dists))
+        assert got[0] is ids and got[1] is dists
+        with pytest.raises(ValueError):
+            outputs(None, None, n, k, (make((n, k), "int64"), dists))
+        with pytest.raises(ValueError):
+            outputs(None, None, n, k, (ids, make((n, k + 1), "float32")))
+        with pytest.raises(ValueError):
+            outputs(None, None, n, k, (make((k, n), "int32").T, dists))
