@@ -142,6 +142,9 @@ __device__ int32_t draw_random(uint64_t seed, int64_t i, int64_t base, int64_t n
 // canon_dist_global4, with all rows' loads in flight at once.
 constexpr int INIT_CH = 64;              // dimensions staged per pass
 constexpr int INIT_STRIDE = INIT_CH + 4;  // floats per staged row (conflict-free float4 reads)
+// Staged rows per warp: up to 32 listed rows, then the node's own row (read
+// by every lane from shared memory: its loads never wait inside the chain).
+constexpr int INIT_ROWS = 33;
 
 __device__ __forceinline__ void init_cp16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
@@ -155,7 +158,7 @@ __device__ __forceinline__ float staged_dist(const Rows& R, int64_t i, int32_t g
     return g >= 0 ? jaccard_rows(R, i, g) : 0.0f;
   } else {
   const int lane = threadIdx.x & 31, d = R.d;
-  const float4* xi = reinterpret_cast<const float4*>(R.row(i));
+  float* own = buf + 32 * INIT_STRIDE;
   const float* yj = buf + lane * INIT_STRIDE;
   float acc = 0.0f;
   for (int c = 0; c < d; c += INIT_CH) {
@@ -166,11 +169,12 @@ __device__ __forceinline__ float staged_dist(const Rows& R, int64_t i, int32_t g
       if (slot < rows && gs >= 0 && o < q4)
         init_cp16(buf + slot * INIT_STRIDE + o * 4, R.row(gs) + c + o * 4);
     }
+    if (lane < q4) init_cp16(own + lane * 4, R.row(i) + c + lane * 4);
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncwarp();
     if (g >= 0) {
       for (int t = 0; t < q4; ++t) {
-        const float4 x = __ldg(xi + (c >> 2) + t);
+        const float4 x = *reinterpret_cast<const float4*>(own + 4 * t);
         const float4 y = *reinterpret_cast<const float4*>(yj + 4 * t);
         acc = Canon<METRIC>::step(acc, x.x, y.x);
         acc = Canon<METRIC>::step(acc, x.y, y.y);
@@ -206,7 +210,7 @@ __device__ __forceinline__ float staged_dist16(const InitArgs& a, int64_t i, int
   constexpr int RS = INIT_STRIDE * 2;  // 16-bit elements between staged rows (272 bytes)
   uint16_t* buf = reinterpret_cast<uint16_t*>(bufF);
   const uint16_t* X = reinterpret_cast<const uint16_t*>(a.Xe);
-  const uint4* xi = reinterpret_cast<const uint4*>(X + (size_t)i * a.dx);
+  uint16_t* own = buf + 32 * RS;
   const uint16_t* yj = buf + lane * RS;
   float acc = 0.0f;
   for (int c = 0; c < d; c += 128) {
@@ -217,11 +221,12 @@ __device__ __forceinline__ float staged_dist16(const InitArgs& a, int64_t i, int
       if (slot < rows && gs >= 0 && o < q8)
         init_cp16(buf + slot * RS + o * 8, X + (size_t)gs * a.dx + c + o * 8);
     }
+    if (lane < q8) init_cp16(own + lane * 8, X + (size_t)i * a.dx + c + lane * 8);
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncwarp();
     if (g >= 0) {
       for (int t = 0; t < q8; ++t) {
-        const uint4 xv = __ldg(xi + (c >> 3) + t);
+        const uint4 xv = *reinterpret_cast<const uint4*>(own + 8 * t);
         const uint4 yv = *reinterpret_cast<const uint4*>(yj + 8 * t);
         const uint32_t xw[4] = {xv.x, xv.y, xv.z, xv.w}, yw[4] = {yv.x, yv.y, yv.z, yv.w};
 #pragma unroll
@@ -254,8 +259,8 @@ __device__ __forceinline__ float staged_dist_src(const InitArgs& a, int64_t i, i
 
 template <int METRIC, int SRC>
 __global__ void __launch_bounds__(BLOCK) k_init(InitArgs a) {
-  extern __shared__ __align__(16) float init_buf[];  // [warps][32][INIT_STRIDE] when staged
-  float* wbuf = init_buf + (threadIdx.x >> 5) * 32 * INIT_STRIDE;
+  extern __shared__ __align__(16) float init_buf[];  // [warps][INIT_ROWS][INIT_STRIDE] when staged
+  float* wbuf = init_buf + (threadIdx.x >> 5) * INIT_ROWS * INIT_STRIDE;
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
   const int K = a.K, Kk = a.K_keep, Kr = a.K - a.K_keep;
@@ -1326,7 +1331,7 @@ __global__ void k_bf16_prep(Rows R, int64_t N, __nv_bfloat16* Xb, float4* aux, f
 
 template <int METRIC, int SRC>
 cudaError_t launch_init_m(const InitArgs& a, int grid, cudaStream_t st) {
-  const size_t smem = a.vec4 ? (size_t)WARPS_PER_BLOCK * 32 * INIT_STRIDE * 4 : 0;
+  const size_t smem = a.vec4 ? (size_t)WARPS_PER_BLOCK * INIT_ROWS * INIT_STRIDE * 4 : 0;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_init<METRIC, SRC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
