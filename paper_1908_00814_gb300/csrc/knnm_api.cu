@@ -654,7 +654,7 @@ int run_merge(knnm_ctx* ctx, const MergeIn& in, const knnm_params* params, int32
   KNNM_CUDA(cudaEventRecord(ctx->ev[2], st));
   int32_t* oi = P.oi ? P.oi : out_ids;
   float* od = P.od ? P.od : out_dists;
-  KNNM_CUDA(launch_final(N, K, P.keys, D.Kr, P.rear, oi, od, st));
+  KNNM_CUDA(launch_final(N, K, P.keys, D.Kr, P.rear, oi, od, true, st));
   ++launches;
   KNNM_CUDA(cudaEventRecord(ctx->ev[3], st));
   if (P.oi)
@@ -1578,7 +1578,7 @@ extern "C" int knnm_step_final(knnm_ctx* ctx, int64_t N, int K, const int32_t* i
   carve(c1);
   KNNM_CUDA(launch_pack((int64_t)N * K, ids, dists, keys, st));
   if (Kr > 0) KNNM_CUDA(launch_pack((int64_t)N * Kr, rear_ids, rear_dists, rear, st));
-  KNNM_CUDA(launch_final(N, K, keys, Kr, rear, out_ids, out_dists, st));
+  KNNM_CUDA(launch_final(N, K, keys, Kr, rear, out_ids, out_dists, false, st));
   KNNM_CUDA(cudaStreamSynchronize(st));
   return KNNM_OK;
 }

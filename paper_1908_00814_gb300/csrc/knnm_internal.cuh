@@ -658,8 +658,10 @@ struct MergeArgs {
 // flags and c_t.
 cudaError_t launch_bucket_update(const MergeArgs& a, cudaStream_t st);
 
+// sorted: every list and every rear list is ascending (the merge driver's own
+// arrays), so the two are merged rather than sorted together.
 cudaError_t launch_final(int64_t N, int K, const uint64_t* keys, int Kr, const uint64_t* rear,
-                         int32_t* out_ids, float* out_dists, cudaStream_t st);
+                         int32_t* out_ids, float* out_dists, bool sorted, cudaStream_t st);
 
 // Candidate counts with every node outside [lo, hi) set to 0.
 cudaError_t launch_mask_counts(int64_t N, int64_t lo, int64_t hi, const int32_t* in_new,

@@ -1148,14 +1148,21 @@ __global__ void __launch_bounds__(BLOCK) k_union(int64_t n, int K, int parts,
 
 __global__ void __launch_bounds__(BLOCK) k_final(int64_t N, int K, const uint64_t* keys, int Kr,
                                                  const uint64_t* rear, int32_t* out_ids,
-                                                 float* out_dists) {
+                                                 float* out_dists, int sorted) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
   for (int64_t v = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5); v < N;
        v += nwarps) {
     uint64_t e0 = lane < K ? keys[(size_t)v * K + lane] : KEY_EMPTY;
     uint64_t e1 = lane < Kr ? rear[(size_t)v * Kr + lane] : KEY_EMPTY;
-    warp_sort64(e0, e1);
+    if (sorted && K + Kr <= 32) {
+      // both ascending (the list, and the rear keys as init wrote them): one
+      // bitonic merge keeps all K + Kr keys in order
+      e0 = warp_merge_lo32(e0, e1);
+      e1 = KEY_EMPTY;
+    } else {
+      warp_sort64(e0, e1);
+    }
     uint64_t p0 = __shfl_up_sync(FULL, e0, 1);
     uint64_t p1 = __shfl_up_sync(FULL, e1, 1);
     uint64_t last0 = __shfl_sync(FULL, e0, 31);
@@ -1486,8 +1493,9 @@ cudaError_t launch_union(int64_t n, int K, int parts, const int32_t* part_ids,
 }
 
 cudaError_t launch_final(int64_t N, int K, const uint64_t* keys, int Kr, const uint64_t* rear,
-                         int32_t* out_ids, float* out_dists, cudaStream_t st) {
-  k_final<<<grid_for_warps(N), BLOCK, 0, st>>>(N, K, keys, Kr, rear, out_ids, out_dists);
+                         int32_t* out_ids, float* out_dists, bool sorted, cudaStream_t st) {
+  k_final<<<grid_for_warps(N), BLOCK, 0, st>>>(N, K, keys, Kr, rear, out_ids, out_dists,
+                                               sorted ? 1 : 0);
   return cudaGetLastError();
 }
 
