@@ -665,10 +665,14 @@ __global__ void __launch_bounds__(BLOCK) k_sample_rev(SampleArgs a) {
     if (buckets) {
       const int32_t yn = r0 + lane < r1 ? a.rbucket[r0 + lane] : -1;
       const int32_t yo = r1 + lane < r2 ? a.rbucket[r1 + lane] : -1;
-      pre_n = mix_step(h_new ^ (uint64_t)u);  // = hash_prefix(seed, t, STREAM_REV_NEW, u)
-      pre_o = mix_step(h_old ^ (uint64_t)u);
-      xn = yn >= 0 ? sampling_key(pre_n, yn) : KEY_EMPTY;
-      xo = yo >= 0 ? sampling_key(pre_o, yo) : KEY_EMPTY;
+      // a bucket the records take whole (at most s ids) is never ranked: its
+      // ids travel as keys with an empty hash half
+      const bool whole_n = a.records_only && r1 - r0 <= (uint64_t)s;
+      const bool whole_o = a.records_only && r2 - r1 <= (uint64_t)s;
+      if (!whole_n) pre_n = mix_step(h_new ^ (uint64_t)u);  // = hash_prefix(seed, t, STREAM_REV_NEW, u)
+      if (!whole_o) pre_o = mix_step(h_old ^ (uint64_t)u);
+      xn = yn < 0 ? KEY_EMPTY : (whole_n ? (uint64_t)(uint32_t)yn : sampling_key(pre_n, yn));
+      xo = yo < 0 ? KEY_EMPTY : (whole_o ? (uint64_t)(uint32_t)yo : sampling_key(pre_o, yo));
     } else {
       xn = lane < s ? a.rev_new[(size_t)u * s + lane] : KEY_EMPTY;
       xo = lane < s ? a.rev_old[(size_t)u * s + lane] : KEY_EMPTY;
