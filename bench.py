@@ -55,11 +55,13 @@ def load_peaks():
     return PEAKS_FALLBACK, "fallback"
 
 
-def workload_config(w, precision):
+def workload_config(w):
+    """The workload both arms run (the reference arm on a bounded sample of it, stated in
+    its cpu_baseline); each line names its own arithmetic in a top-level "precision"."""
     return {"workload": WORKLOAD, "merge": "symmetric (Alg. 1)", "n1": w["n"] // 2,
             "n2": w["n"] - w["n"] // 2, "d": w["d"], "k": w["k"], "metric": w["metric"],
             "max_rounds": w["rounds"], "sample_rate": w["sample_rate"], "keep_ratio": 0.5,
-            "delta": 0.001, "precision": precision,
+            "delta": 0.001,
             "inputs": "NN-Descent builds of each half, 10 rounds, made before timing",
             "l2_flush": "inputs larger than L2 (512 MB vectors + 0.5 GB list state per step)",
             "parallelism": "replicas"}
@@ -189,7 +191,7 @@ def run_reference(args, w):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": workload_config(w, "fp32 (CPU oracle)"),
+            "data": "synthetic", "config": workload_config(w), "precision": "fp32 (CPU oracle)",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"S-Merge of {per_half} rows of each half "
                                        f"({2 * per_half} points) per step, single-threaded",
@@ -1024,7 +1026,8 @@ def run_ours(args, w):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_bf,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16+f32", "data": "synthetic", "config": workload_config(w, "bf16_rerank"),
+            "dtype": "bf16+f32", "data": "synthetic", "config": workload_config(w),
+            "precision": "bf16_rerank",
             "recall_at_10": recall, "recall_queries": len(queries),
             "distance_error": dist_err,
             "rounds": st_bf[-1]["rounds"], "updates_per_round": st_bf[-1]["updates"],
