@@ -22,6 +22,12 @@ def test_reference_arm_prints_one_json_line():
         assert key in line, key
     assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 1
     assert line["config"]["workload"] == "smerge_sift_1m_d128_k20"
+    # the same config dict as the GPU arm's line (the workload, not the arithmetic)
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1908_00814_gb300 import datagen
+    assert line["config"] == bench.workload_config(dict(datagen.WORKLOADS[bench.WORKLOAD]))
+    assert line["precision"] == "fp32 (CPU oracle)" and "precision" not in line["config"]
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
     e2e = line["e2e"]
